@@ -1,0 +1,193 @@
+"""Pins of the oracle's whole-grid step against physics the paper and mathematics fix.
+
+CPU only.  Conservation on closed/periodic boxes, the shear-wave decay rate (viscosity
+nu = cs^2 (1/omega - 1/2), App. A), the advected Gaussian (diffusivity
+D = cs_phi^2 (1/omega - 1/2), Eq. 23), steady conduction (Nu = 1), the cavity's
+centro-symmetry, and the paper's Table 1 at Ra = 1e3.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import formb
+from tests import inputs
+from tests.golden_io import table1
+
+
+def _random_state(p, seed):
+    fs, gs = p.shapes()
+    F = inputs.perturbed_populations(oracle.weights_flow(), fs[1:], seed, rel=0.05)
+    T = inputs.uniform_field(gs[1:], seed + 1, -0.5, 0.5)
+    G = oracle.weights_thermal(p.q_g, p.cs2_phi)[:, None, None, None] * T[None] + \
+        inputs.perturbed_populations(np.full(p.q_g, 0.01), gs[1:], seed + 2, rel=1.0)
+    return F, G
+
+
+@pytest.mark.parametrize("q", [15, 7])
+def test_periodic_box_conservation(q):
+    p = oracle.Problem(6, 5, 4, q_g=q, boundary=oracle.BC_PERIODIC, omega_nu=1.3,
+                       omega_phi=1.6, gbeta=1e-3, ext_force=(1e-4, -2e-4, 3e-4))
+    F, G = _random_state(p, 3)
+    e = oracle.velocities(15).astype(np.float64)
+    mass0, heat0 = F.sum(), G.sum()
+    for _ in range(5):
+        mom0 = np.einsum("azyx,ad->d", F, e)
+        T = G.sum(axis=0)
+        F1, G1 = p.step(F, G)
+        # total force: the uniform one plus g beta (T - T0) on every cell (T0 = 0)
+        Ftot = np.array(p.ext_force) * p.ncell + np.array([0, 0, p.gbeta * T.sum()])
+        # pull streaming is a permutation, so the sums of the post-collision arrays move
+        # exactly as the collision moves them (Eq. 2a: + F per cell)
+        np.testing.assert_allclose(np.einsum("azyx,ad->d", F1, e), mom0 + Ftot, atol=1e-14)
+        F, G = F1, G1
+    assert abs(F.sum() - mass0) < 1e-12 * mass0
+    assert abs(G.sum() - heat0) < 1e-12
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_closed_adiabatic_box_conserves_mass_and_heat(mode):
+    p = oracle.Problem(5, 4, 6, boundary=oracle.BC_ADIABATIC_BOX, omega_nu=1.2,
+                       omega_phi=1.5, gbeta=1e-3, adiabatic_mode=mode)
+    F, G = _random_state(p, 8)
+    F2, G2 = p.run(F, G, 40)
+    assert abs(F2.sum() - F.sum()) < 1e-12 * F.sum()
+    assert abs(G2.sum() - G.sum()) < 1e-12
+
+
+def test_cavity_conserves_mass():
+    p = oracle.Problem.cavity(8, 1e4)
+    F, G = _random_state(p, 9)
+    F2, G2 = p.run(F, G, 30)
+    assert abs(F2.sum() - F.sum()) < 1e-12 * F.sum()
+
+
+def test_shear_wave_decay_gives_viscosity():
+    N, om, A = 64, 1.5, 1e-3
+    p = oracle.Problem(N, 2, 2, boundary=oracle.BC_PERIODIC, omega_nu=om)
+    F = np.zeros((15, 2, 2, N))
+    for i in range(N):
+        F[:, :, :, i] = formb.flow_equilibrium(1.0, [0, A * math.sin(2 * math.pi * i / N), 0])[:, None, None]
+    G = np.zeros((15, 2, 2, N))
+    s = np.sin(2 * np.pi * np.arange(N) / N)
+
+    def amp(F, G):
+        return 2.0 / N * np.sum(p.fields(F, G)["uy"][0, 0] * s)
+
+    F1, G1 = p.run(F, G, 100)
+    F2, G2 = p.run(F1, G1, 500)
+    k = 2 * math.pi / N
+    nu_fit = -math.log(amp(F2, G2) / amp(F1, G1)) / (k * k * 500)
+    nu = (1.0 / 3.0) * (1.0 / om - 0.5)
+    assert abs(nu_fit / nu - 1) < 5e-3, (nu_fit, nu)
+
+
+@pytest.mark.parametrize("q,omphi,cs2", [(15, 1.2, 1 / 3), (15, 1.7, 1 / 3), (7, 1.2, 1 / 3),
+                                         (7, 1.4, 0.25)])
+def test_advected_gaussian_gives_diffusivity(q, omphi, cs2):
+    N, s0, u, t1, t2 = 40, 2.5, (0.05, 0.03, 0.02), 20, 80
+    p = oracle.Problem(N, N, N, q_g=q, boundary=oracle.BC_PERIODIC, omega_phi=omphi, cs2_phi=cs2)
+    F = np.broadcast_to(formb.flow_equilibrium(1.0, u)[:, None, None, None], (15, N, N, N)).copy()
+    c = np.arange(N)
+    X = (c - N / 2) ** 2
+    T0 = np.exp(-(X[None, None, :] + X[None, :, None] + X[:, None, None]) / (2 * s0 * s0))
+    G = formb.thermal_equilibrium(1.0, u, q, cs2)[:, None, None, None] * T0[None]
+
+    def variance(F, G, t):
+        T = p.fields(F, G)["T"]
+        out = []
+        for ax, ud in zip((2, 1, 0), u):
+            d = ((c - (N / 2 + ud * t) + N / 2) % N) - N / 2
+            w = T.sum(axis=tuple(a for a in (0, 1, 2) if a != ax))
+            m = (w * d).sum() / w.sum()
+            out.append((w * d * d).sum() / w.sum() - m * m)
+            assert abs(m) < 1e-3  # the centroid moves with u
+        return np.array(out)
+
+    F1, G1 = p.run(F, G, t1)
+    F2, G2 = p.run(F1, G1, t2 - t1)
+    D_fit = (variance(F2, G2, t2) - variance(F1, G1, t1)) / (2.0 * (t2 - t1))
+    D = cs2 * (1.0 / omphi - 0.5)
+    np.testing.assert_allclose(D_fit, D, rtol=3e-3)
+    assert abs(G2.sum() - G.sum()) < 1e-10
+
+
+def _linear_conduction(p):
+    N = p.nx
+    T = -0.5 + (np.arange(N) + 0.5) / N
+    F, _ = p.init(1, 0.0)
+    G = oracle.weights_thermal(p.q_g, p.cs2_phi)[:, None, None, None] * T[None, None, None, :] \
+        * np.ones((1, p.nz, p.ny, 1))
+    F, G = p.run(F, G, 1500)
+    return T, p.fields(F, G)["T"], p.nusselt(F, G)
+
+
+@pytest.mark.parametrize("q", [15, 7])
+def test_conduction_between_dirichlet_walls_is_exact(q):
+    # x walls by anti-bounce-back, y and z periodic: the linear profile is the steady
+    # state and the one-sided stencil returns Nu = 1
+    p = oracle.Problem(12, 2, 2, q_g=q, boundary=oracle.BC_XWALLS, omega_phi=1.7)
+    T, Tf, nu = _linear_conduction(p)
+    assert np.abs(Tf - T[None, None, :]).max() < 1e-13
+    assert abs(nu["hot_wall_mean"] - 1) < 1e-12 and abs(nu["cold_wall_mean"] - 1) < 1e-12
+
+
+@pytest.mark.parametrize("q", [15, 7])
+def test_conduction_in_the_cavity(q):
+    # gbeta = 0 in the closed cavity; with specular adiabatic walls the profile is exact
+    p = oracle.Problem(10, 10, 10, q_g=q, omega_nu=1.2, omega_phi=1.4, adiabatic_mode=1)
+    T, Tf, nu = _linear_conduction(p)
+    assert np.abs(Tf - T[None, None, :]).max() < 1e-13
+    assert abs(nu["mid_mean"] - 1) < 1e-12 and abs(nu["hot_wall_mean"] - 1) < 1e-12
+
+
+def test_conduction_bounce_back_adiabatic_error_is_first_order():
+    # the bounce-back form of the adiabatic wall reverses the tangential part of the
+    # D3Q15 diagonal links: a wall-layer error in Nu that halves when N doubles
+    errs = []
+    for N in (8, 16):
+        p = oracle.Problem(N, N, N, omega_nu=1.2, omega_phi=1.4, adiabatic_mode=0)
+        _, _, nu = _linear_conduction(p)
+        errs.append(abs(nu["hot_wall_mean"] - 1))
+    assert errs[0] > 1e-2 and 1.6 < errs[0] / errs[1] < 2.4, errs
+
+
+def test_cavity_centro_symmetry():
+    # without noise the cavity is invariant under (x, z) -> (L-x, L-z), T -> -T,
+    # (u_x, u_z) -> -(u_x, u_z), and under y -> L-y, u_y -> -u_y (Sec. 3 geometry)
+    p = oracle.Problem.cavity(12, 2e3)
+    F, G = p.init(1, 0.0)
+    F, G = p.run(F, G, 300)
+    f = p.fields(F, G)
+    rot = lambda a: a[::-1, :, ::-1]  # noqa: E731  (z, y, x) indexing
+    np.testing.assert_allclose(f["T"], -rot(f["T"]), atol=1e-13)
+    np.testing.assert_allclose(f["ux"], -rot(f["ux"]), atol=1e-13)
+    np.testing.assert_allclose(f["uz"], -rot(f["uz"]), atol=1e-13)
+    np.testing.assert_allclose(f["uy"], -f["uy"][:, ::-1, :], atol=1e-13)
+    np.testing.assert_allclose(f["T"], f["T"][:, ::-1, :], atol=1e-13)
+    assert np.abs(f["uz"]).max() > 1e-4  # the flow is actually running
+
+
+@pytest.mark.parametrize("q", [15, 7])
+def test_table1_ra1e3_coarse_grid(q):
+    # Table 1 (Ra = 1e3), on a 20^3 grid after 6000 steps (max |dT| per 500 steps ~2e-6)
+    p = oracle.Problem.cavity(20, 1e3, q_g=q)
+    F, G = p.init(1, 1e-6)
+    F, G = p.run(F, G, 6000)
+    nu = p.nusselt(F, G)
+    ref = {r["quantity"]: r for r in table1() if r["Ra"] == 1e3}
+    assert nu["umax"] == pytest.approx(ref["u_max"]["lbm"], rel=0.01)
+    assert nu["wmax"] == pytest.approx(ref["w_max"]["lbm"], rel=0.01)
+    assert nu["mid_max"] == pytest.approx(ref["Nu_max"]["lbm"], rel=0.015)
+    assert nu["mid_min"] == pytest.approx(ref["Nu_min"]["lbm"], rel=0.015)
+    assert nu["mid_mean"] == pytest.approx(ref["Nu_mean"]["lbm"], rel=0.02)
+    # positions, as distance from the nearest wall, within 1.5 cells
+    near = lambda z: min(z, 1 - z)  # noqa: E731
+    h = 1.5 / 20
+    assert abs(near(nu["umax_z"]) - near(ref["u_max"]["lbm_pos"])) < h
+    assert abs(near(nu["wmax_x"]) - near(ref["w_max"]["lbm_pos"])) < h
+    assert abs(near(nu["mid_max_z"]) - near(ref["Nu_max"]["lbm_pos"])) < h
+    assert abs(near(nu["mid_min_z"]) - near(ref["Nu_min"]["lbm_pos"])) < h
+    # hot and cold walls carry the same heat (centro-symmetry)
+    assert nu["hot_wall_mean"] == pytest.approx(nu["cold_wall_mean"], rel=1e-6)
