@@ -1,0 +1,388 @@
+"""Benchmark of the fused cascaded thermal LBM step on GB300.
+
+Workload: the differentially heated cubic cavity at 128^3, Ra = 1e5, Pr = 0.71,
+U0 = 0.05, FP32 populations, D3Q15 flow + D3Q15 thermal (headline) and D3Q15 flow +
+D3Q7 thermal (variant).  A bench "step" is one time step: one fused stream-and-collide
+kernel over the whole grid, plus the residual / NaN reduction every 100 steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun, one process per GPU) every rank
+advances its own cavity (the method has no exchange between independent cavities) and
+the value is the whole-job throughput over the slowest rank.
+"""
+import argparse
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "coupled MLUPS & % HBM roofline; time-to-steady Nu at Ra=1e5 vs plain FP32"
+N_GRID, RA, PR, U0 = 128, 1e5, 0.71, 0.05
+RESIDUAL_INTERVAL = 100
+# algorithmic bytes per node update: every population read once and written once
+BYTES_PER_NODE = {15: 2 * 30 * 4, 7: 2 * 22 * 4}
+
+
+# ----------------------------------------------------------------------------------
+# distributed helpers (one process per GPU; tested with gloo on CPU)
+# ----------------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value, device=None):
+    """Max of a float over all ranks (the slowest rank sets the job time)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value, device=None):
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return self
+        self.proc = subprocess.Popen(
+            [exe, "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+             "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[4:8]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------
+
+def time_steps(sim, steps, stream):
+    import torch
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    sim.step(steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def run_variant(lbm, q, steps, warmup, dist, device, clocks=None):
+    import torch
+    n3 = N_GRID ** 3
+    stream = torch.cuda.current_stream(device)
+    sim = lbm.LBM((N_GRID,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=lbm.FP32,
+                  residual_interval=RESIDUAL_INTERVAL)
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    barrier(dist)
+    if clocks is not None:
+        clocks.start()
+        time.sleep(0.3)
+    elapsed = time_steps(sim, steps, stream)
+    clk = clocks.stop() if clocks is not None else None
+    barrier(dist)
+    elapsed_max = max_over_ranks(dist, elapsed, device)
+    nu = sim.nusselt()
+    residual = sim.residual()
+
+    # the step kernel alone (no residual launches) for the roofline
+    kern = lbm.LBM((N_GRID,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=lbm.FP32,
+                   residual_interval=0)
+    kern.step(max(10, warmup // 4))
+    ksteps = max(50, min(steps, 2000))
+    t_kernel = time_steps(kern, ksteps, stream) / ksteps
+    kern.close()
+    return dict(sim=sim, elapsed=elapsed_max, mlups=n3 * steps / elapsed_max / 1e6,
+                t_kernel=t_kernel, nu=nu, residual=residual, clocks=clk,
+                launches=steps + steps // RESIDUAL_INTERVAL)
+
+
+def e2e_variant(lbm, q, reps, device):
+    """Through the C ABI with host buffers: upload the state from pinned host memory,
+    advance one residual interval, read Nu and the residual back.  Per repetition."""
+    import torch
+    n = N_GRID
+    sim = lbm.LBM((n,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=lbm.FP32,
+                  residual_interval=RESIDUAL_INTERVAL)
+    f_host = torch.empty((15, n, n, n), dtype=torch.float64, pin_memory=True).numpy()
+    g_host = torch.empty((q, n, n, n), dtype=torch.float64, pin_memory=True).numpy()
+    f, g = sim.get_populations()
+    f_host[...] = f
+    g_host[...] = g
+    sim.set_populations(f_host, g_host)
+    sim.step(RESIDUAL_INTERVAL)
+    sim.nusselt()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        sim.set_populations(f_host, g_host)
+        sim.step(RESIDUAL_INTERVAL)
+        sim.nusselt()
+        sim.residual()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    sim.close()
+    lups = n ** 3 * RESIDUAL_INTERVAL * reps
+    return dict(value=lups / dt / 1e6, unit="MLUPS",
+                h2d_bytes_per_step=(15 + q) * n ** 3 * 8 / RESIDUAL_INTERVAL,
+                d2h_bytes_per_step=(11 * 8) / RESIDUAL_INTERVAL,
+                lbm_steps_per_transfer=RESIDUAL_INTERVAL,
+                note="per step: H2D of the FP64 state (pinned), 100 fused steps, D2H of Nu; "
+                     "bytes amortised per time step")
+
+
+def cpu_baseline(sample_steps=3, q=15):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the same
+    workload (the 128^3 Ra = 1e5 cavity, a few steps from its initial state)."""
+    import oracle
+    p = oracle.Problem.cavity(N_GRID, RA, Pr=PR, Ma=U0 * math.sqrt(3.0), q_g=q)
+    F, G = p.init(seed=1, noise_amp=1e-6)
+    F, G = p.step(F, G)  # first-touch / page-in outside the timing
+    t0 = time.perf_counter()
+    F, G = p.run(F, G, sample_steps)
+    dt = time.perf_counter() - t0
+    return {"value": N_GRID ** 3 * sample_steps / dt / 1e6, "unit": "MLUPS",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{N_GRID}^3 cavity Ra=1e5, D3Q15+D3Q{q}, {sample_steps} FP64 steps"}
+
+
+def gpu_arm(args):
+    import torch
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    import paper_1710_04751_gb300 as lbm
+    lbm.load()
+
+    peak, peak_kind = measured_peak_gbs()
+    clocks = ClockSampler(local)
+    main = run_variant(lbm, 15, args.steps, args.warmup, dist, device, clocks)
+    variant = run_variant(lbm, 7, args.steps, args.warmup, dist, device, None)
+
+    def roof(res, q):
+        achieved = BYTES_PER_NODE[q] * N_GRID ** 3 / res["t_kernel"] / 1e9
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": args.traffic.get(q),
+                "peak_kind": peak_kind, "kernel": f"step_kernel<float,{q}>",
+                "bytes_per_node": BYTES_PER_NODE[q],
+                "kernel_ms": round(res["t_kernel"] * 1e3, 4)}
+
+    total_lups = sum_over_ranks(dist, N_GRID ** 3 * args.steps, device)
+    value = total_lups / main["elapsed"] / 1e6
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(main["elapsed"] / args.steps * 1e3, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: cavity at rest, T = seeded uniform noise +-1e-6",
+        "config": {
+            "workload": "differentially heated cubic cavity 128^3, Ra=1e5, Pr=0.71, U0=0.05, "
+                        "D3Q15 flow + D3Q15 thermal, FP32, to-steady run",
+            "grid": [N_GRID] * 3, "Ra": RA, "Pr": PR, "lattice": "D3Q15+D3Q15",
+            "residual_interval": RESIDUAL_INTERVAL,
+            "l2": "inputs larger than L2: A/B state 503 MB > 129 MB",
+            "parallelism": f"replicas{world}" if world > 1 else "single",
+        },
+        "roofline": roof(main, 15),
+        "clocks": main["clocks"],
+        "gpu_launches": main["launches"],
+        "variants": {
+            "D3Q15+D3Q7": {"value": round(sum_over_ranks(dist, N_GRID ** 3 * args.steps, device)
+                                          / variant["elapsed"] / 1e6, 1),
+                           "unit": "MLUPS", "ms_per_step": round(variant["elapsed"] / args.steps * 1e3, 5),
+                           "roofline": roof(variant, 7)},
+        },
+        "state_after": {"steps": args.warmup + args.steps, "Nu_hot": main["nu"]["hot_wall_mean"],
+                        "residual_per_100": main["residual"]},
+    }
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e_variant(lbm, 15, args.e2e_reps, device)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def reference_arm(args):
+    """The reference arm is the FP64 CPU oracle on the host's cores (rank 0 only).  Each
+    bench step is one oracle time step of a bounded sample of the workload: a
+    128 x 128 x nz slab of the same cavity (same Ra, Pr, U0 and wall rules), nz chosen
+    so that warm-up plus timed steps take about --ref-budget seconds."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    par = oracle.physical_parameters(N_GRID, RA, PR, U0 * math.sqrt(3.0))
+
+    def slab(nz):
+        return oracle.Problem(N_GRID, N_GRID, nz, q_g=15, omega_nu=par["omega_nu"],
+                              omega_phi=par["omega_phi"], gbeta=par["gbeta"], U0=par["U0"])
+
+    cal = slab(8)
+    F, G = cal.init(seed=1, noise_amp=1e-6)
+    t0 = time.perf_counter()
+    cal.step(F, G)
+    rate = cal.ncell / max(time.perf_counter() - t0, 1e-6)  # node updates per second
+    per_step = args.ref_budget / max(1, args.steps + args.warmup)
+    nz = int(max(1, min(N_GRID, per_step * rate / (N_GRID * N_GRID))))
+    p = slab(nz)
+    F, G = p.init(seed=1, noise_amp=1e-6)
+    for _ in range(args.warmup):
+        F, G = p.step(F, G)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        F, G = p.step(F, G)
+    dt = time.perf_counter() - t0
+    value = p.ncell * args.steps / dt / 1e6
+    sample = (f"each step: one FP64 oracle time step of a {N_GRID}x{N_GRID}x{nz} slab of the "
+              f"128^3 Ra=1e5 cavity ({p.ncell} nodes); {args.steps} timed after {args.warmup}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "differentially heated cubic cavity 128^3, Ra=1e5, Pr=0.71, U0=0.05, "
+                               "D3Q15 flow + D3Q15 thermal (FP64 CPU oracle, bounded sample)",
+                   "grid": [N_GRID] * 3, "Ra": RA, "Pr": PR, "lattice": "D3Q15+D3Q15"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-reps", type=int, default=20)
+    ap.add_argument("--ref-budget", type=float, default=90.0,
+                    help="seconds the reference arm spends on warm-up + timed steps")
+    ap.add_argument("--traffic-q15", type=float, default=None,
+                    help="ncu DRAM bytes per launch of the D3Q15 step kernel (reported as-is)")
+    ap.add_argument("--traffic-q7", type=float, default=None)
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        args.steps = 20 if args.steps is None else args.steps
+        args.warmup = 3 if args.warmup is None else args.warmup
+        reference_arm(args)
+        return
+    args.steps = 20000 if args.steps is None else args.steps
+    args.warmup = 300 if args.warmup is None else args.warmup
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    args.traffic = {15: args.traffic_q15, 7: args.traffic_q7}
+    gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

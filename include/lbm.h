@@ -1,0 +1,168 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) library for the cascaded central-moment thermal
+ * lattice Boltzmann method of Hajabdollahi & Premnath, "Central Moments-based Cascaded
+ * Lattice Boltzmann Method for Thermal Convective Flows in Three-Dimensions"
+ * (arXiv:1710.04751).
+ *
+ * One time step (lbm_step) is one fused CUDA kernel over the grid: pull streaming
+ * (Eqs. 2b, 13b), macroscopic variables (Eqs. 3, 25), the Boussinesq force (Sec. 3),
+ * the D3Q15 flow cascade with forcing (Appendix A, Eq. 2a), the D3Q15 (Sec. 2.2,
+ * Eq. 13a) or D3Q7 (Appendix C) thermal cascade, and the cavity wall rules (Sec. 3).
+ *
+ * Conventions shared by every entry point
+ *  - Coordinates: x (index i) is the heated direction, cold face at i = -1/2 (T_cold),
+ *    hot face at i = nx - 1/2 (T_hot); z (index k) is vertical, buoyancy along +z; y is
+ *    spanwise.  Walls lie half-way between the last node and its missing neighbour, so
+ *    the cavity length is L = nx.  (The paper's y is this x; its x is this y.)
+ *  - Host population arrays are FP64, structure-of-arrays, p[a * ncell + cell] with
+ *    cell = (k * ny + j) * nx + i (x fastest) and a the paper's direction order: D3Q15
+ *    rest, +-x, +-y, +-z, then (+,+,+) (-,+,+) (+,-,+) (-,-,+) (+,+,-) (-,+,-) (+,-,-)
+ *    (-,-,-); D3Q7 the first seven.  Stored populations are post-collision: a step is
+ *    pull, then collide.
+ *  - Every host pointer is caller-owned and only read/written during the call.  Device
+ *    memory is library-owned unless the caller passes an arena in lbm_options.
+ *  - Return codes: LBM_OK (0) or a negative LBM_E* code; lbm_last_error(ctx) then holds a
+ *    message (lbm_last_error(NULL) for failures without a context).
+ *  - A context is not thread-safe.  All work runs on the context's CUDA stream; calls
+ *    that return host data synchronise that stream with a bounded wait.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_EINVAL (-1)    /* invalid argument: sizes, lattice, precision, rates out of (0,2) */
+#define LBM_ENOMEM (-2)    /* device or host allocation failed, or arena too small */
+#define LBM_ECUDA (-3)     /* a CUDA runtime call failed (message in lbm_last_error) */
+#define LBM_EDIVERGED (-4) /* a NaN or Inf temperature was detected */
+#define LBM_ETIMEOUT (-5)  /* a bounded wait for the GPU ran out */
+
+enum { LBM_THERMAL_D3Q15 = 15, LBM_THERMAL_D3Q7 = 7 };
+enum { LBM_FP64 = 0, LBM_FP32 = 1 };
+
+/* Boundary modes (bit mask).  Bits 0..2: x, y, z periodic.  Bit 3: the x walls are
+ * adiabatic instead of Dirichlet.  LBM_BC_CAVITY is the paper's cubic cavity (Sec. 3):
+ * no-slip walls everywhere, T_cold / T_hot on the x faces, adiabatic y and z faces. */
+enum {
+    LBM_BC_CAVITY = 0,
+    LBM_BC_XWALLS = 6,       /* Dirichlet x walls, periodic y and z */
+    LBM_BC_PERIODIC = 7,     /* fully periodic box */
+    LBM_BC_ADIABATIC_BOX = 8 /* closed box, every face adiabatic */
+};
+
+/* Adiabatic-wall rule for the thermal populations (Sec. 3 cites a Neumann scheme
+ * without giving it).  Specular reflection (default) mirrors the wall-normal velocity
+ * component of every link that crosses the wall; bounce-back reverses the whole link. */
+enum { LBM_ADIABATIC_BOUNCE_BACK = 0, LBM_ADIABATIC_SPECULAR = 1 };
+
+typedef struct {
+    int nx, ny, nz; /* lattice nodes per direction, each >= 1 */
+} lbm_grid;
+
+/* Physical parameters in lattice units.  lbm_derive_params fills them from (Ra, Pr, Ma)
+ * as Sec. 3 defines: U0 = Ma c_s = sqrt(g beta dT L), g beta = U0^2/(dT L),
+ * nu = sqrt(Pr/Ra) U0 L, alpha = nu/Pr, nu = (1/3)(1/omega - 1/2) (Appendix A) and
+ * alpha = cs2_phi (1/omega - 1/2) (Eq. 23). */
+typedef struct {
+    double omega_f[15];   /* flow rates omega_0..omega_14 (0..3 unused); paper: 4..9 = omega_nu, rest 1 */
+    double omega_g[15];   /* thermal rates omega_0..omega_{Q-1} (0 unused); paper: 1..3 = omega_phi, rest 1 */
+    double gbeta;         /* g beta of the Boussinesq force F_z = g beta (T - T0) */
+    double T_hot, T_cold; /* Dirichlet face temperatures; T0 = (T_hot + T_cold)/2 */
+    double cs2_phi;       /* c_sphi^2 of the thermal equilibrium (Sec. 2.2), in (0, 1/2] (D3Q7: (0, 1/3]) */
+    double ext_force[3];  /* extra uniform body force added to F (0 for the cavity) */
+    double U0;            /* velocity scale used to report u/U0 in lbm_nusselt */
+    int e4_mode;          /* App. A g^_14 equilibrium: 0 E = kxx~ kyy~ / rho, 1 E = rho c_s^4 */
+    int adiabatic_mode;   /* LBM_ADIABATIC_* */
+    int boundary;         /* LBM_BC_* */
+} lbm_params;
+
+typedef struct {
+    int precision;            /* LBM_FP32 (default) or LBM_FP64 storage and arithmetic */
+    uint64_t seed;            /* noise seed of the initial temperature (default 1) */
+    double noise_amp;         /* initial T = uniform noise in [-amp, amp] (default 1e-6) */
+    double cs2_phi;           /* default 1/3 */
+    int e4_mode;              /* default 0 */
+    int adiabatic_mode;       /* default LBM_ADIABATIC_SPECULAR */
+    int residual_interval;    /* steps between residual / NaN checks in lbm_step (default 100, 0 = off) */
+    void* cuda_stream;        /* cudaStream_t to run on; NULL = the legacy default stream */
+    void* device_arena;       /* caller-owned device memory of >= lbm_arena_bytes(), or NULL */
+    size_t device_arena_bytes;
+    double timeout_s;         /* bound on every host wait for the GPU (default 600 s) */
+} lbm_options;
+
+typedef struct {
+    double hot_wall_mean, cold_wall_mean; /* face-averaged Nu on the hot and cold walls */
+    double mid_mean;                      /* mean of the local hot-wall Nu on the symmetry plane y = L/2 */
+    double mid_max, mid_max_z;            /* its maximum and the height z/L where it occurs */
+    double mid_min, mid_min_z;            /* its minimum and where */
+    double umax, umax_z;                  /* max |u_x|/U0 on the vertical centreline x = y = L/2, at z/L */
+    double wmax, wmax_x;                  /* max |u_z|/U0 on the horizontal centreline y = z = L/2, at x/L */
+} lbm_nu;
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, library-owned */
+
+/* Fill *opt with the defaults listed above. */
+void lbm_default_options(lbm_options* opt);
+
+/* Host only, no GPU.  Parameters of the differentially heated cavity (Sec. 3) for
+ * L = grid->nx, dT = 1 (T_hot = 0.5, T_cold = -0.5), from Ra, Pr and Ma = U0 / c_s.
+ * LBM_EINVAL if Ra, Pr or Ma <= 0, if U0 >= 0.3, or if omega_nu or omega_phi falls
+ * outside (0, 2) (the bounds stated for every rate in Sec. 2.2 and Appendix A). */
+int lbm_derive_params(const lbm_grid* grid, int lattice, double Ra, double Pr, double Ma,
+                      const lbm_options* opt, lbm_params* out);
+
+/* Host only.  Device bytes a context of this size needs (for lbm_options.device_arena). */
+size_t lbm_arena_bytes(const lbm_grid* grid, int lattice, int precision);
+
+/* Create a cavity: lbm_derive_params, then lbm_create_params.  The fluid starts at rest
+ * (f = rest weights) with T = seeded noise (g = w^phi T), as a post-collision state. */
+int lbm_create(const lbm_grid* grid, int lattice, double Ra, double Pr, double Ma,
+               const lbm_options* opt /* NULL = defaults */, lbm_ctx** out);
+
+/* Create a context with explicit parameters (every rate must lie in (0, 2)). */
+int lbm_create_params(const lbm_grid* grid, int lattice, const lbm_params* params,
+                      const lbm_options* opt /* NULL = defaults */, lbm_ctx** out);
+
+/* Advance n >= 0 time steps (one fused kernel each), asynchronously on the context's
+ * stream.  Every residual_interval steps a reduction records max |T - T_previous_check|
+ * and flags non-finite temperatures; if any check ran, the call waits (bounded) at its
+ * end and returns LBM_EDIVERGED when the flag is set. */
+int lbm_step(lbm_ctx* ctx, int64_t n);
+
+/* Macroscopic fields of the stored state into caller-owned host arrays of ncell FP64
+ * each (x fastest); any pointer may be NULL.  rho = sum f, T = sum g,
+ * u = (sum f e - F/2)/rho with F from T (Eq. 3 at the same time level). */
+int lbm_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy, double* uz, double* T);
+
+/* Nusselt numbers and peak velocities of Table 1 (Sec. 3).  Local Nu = L |dT/dn| / dT
+ * with dT/dn = (9 T_1 - T_2 - 8 T_w)/3 at a half-way wall; lines on the symmetry plane
+ * average the two straddling nodes when a size is even.  Needs nx >= 2. */
+int lbm_nusselt(lbm_ctx* ctx, lbm_nu* out);
+
+/* The last residual recorded by lbm_step: max over the grid of |T - T at the previous
+ * check| (a negative value if no check has run since creation or set_populations). */
+int lbm_residual(lbm_ctx* ctx, double* max_dT);
+
+/* Copy the stored populations to / from caller-owned host arrays (FP64, layout above;
+ * f has 15 ncell values, g has Q ncell values).  set_populations converts to the
+ * context's precision and restarts the residual snapshot. */
+int lbm_get_populations(lbm_ctx* ctx, double* f, double* g);
+int lbm_set_populations(lbm_ctx* ctx, const double* f, const double* g);
+
+/* Parameters in use, step counter, last error message, stream wait, destruction. */
+int lbm_get_params(const lbm_ctx* ctx, lbm_params* out);
+int64_t lbm_steps_done(const lbm_ctx* ctx);
+const char* lbm_last_error(const lbm_ctx* ctx);
+int lbm_synchronize(lbm_ctx* ctx);
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,513 @@
+// api.cu -- the C ABI declared in include/lbm.h: context life cycle, parameter
+// derivation (Sec. 3 of arXiv:1710.04751), the time-step loop and host transfers.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+#include <string>
+#include <thread>
+
+#include "../../include/lbm.h"
+#include "internal.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_grid grid;
+    int Q;
+    int precision;
+    lbm_params params;
+    lbm_options opt;
+    int64_t ncell, plane;
+    size_t rsize;
+    int device;
+    cudaStream_t stream;
+    void* arena;
+    bool own_arena;
+    size_t arena_bytes;
+    DevState dev;
+    int cur;              // buffer holding the current state
+    int64_t steps;
+    double last_residual; // < 0: none recorded yet
+    unsigned long long* host_bits;  // pinned: residual bits + flag
+    std::string err;
+};
+
+static thread_local std::string g_err;
+
+static int fail(lbm_ctx* ctx, int code, const char* fmt, const char* detail = nullptr) {
+    char buf[512];
+    snprintf(buf, sizeof buf, fmt, detail ? detail : "");
+    if (ctx) ctx->err = buf;
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_OR_FAIL(ctx, call)                                                     \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            return fail((ctx), LBM_ECUDA, "CUDA error in " #call ": %s",            \
+                        cudaGetErrorString(e_));                                    \
+    } while (0)
+
+// Keeps the caller's current device and restores it on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+extern "C" void lbm_default_options(lbm_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = LBM_FP32;
+    o->seed = 1;
+    o->noise_amp = 1e-6;
+    o->cs2_phi = 1.0 / 3.0;
+    o->e4_mode = 0;
+    o->adiabatic_mode = LBM_ADIABATIC_SPECULAR;
+    o->residual_interval = 100;
+    o->cuda_stream = nullptr;
+    o->device_arena = nullptr;
+    o->device_arena_bytes = 0;
+    o->timeout_s = 600.0;
+}
+
+static bool valid_grid(const lbm_grid* g) {
+    return g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1 &&
+           (double)g->nx * g->ny * g->nz < 4.0e9;
+}
+
+static bool valid_lattice(int q) { return q == LBM_THERMAL_D3Q15 || q == LBM_THERMAL_D3Q7; }
+
+extern "C" int lbm_derive_params(const lbm_grid* grid, int lattice, double Ra, double Pr,
+                                 double Ma, const lbm_options* opt, lbm_params* out) {
+    lbm_options o;
+    if (opt) o = *opt; else lbm_default_options(&o);
+    if (!out || !valid_grid(grid)) return fail(nullptr, LBM_EINVAL, "invalid grid%s");
+    if (!valid_lattice(lattice)) return fail(nullptr, LBM_EINVAL, "lattice must be 15 or 7%s");
+    if (!(Ra > 0) || !(Pr > 0) || !(Ma > 0))
+        return fail(nullptr, LBM_EINVAL, "Ra, Pr and Ma must be positive%s");
+    // Sec. 3: Ra = g beta dT L^3 / (alpha nu), Pr = nu / alpha, U0 = sqrt(g beta dT L)
+    const double L = grid->nx, dT = 1.0;
+    const double U0 = Ma * sqrt(1.0 / 3.0);
+    if (U0 >= 0.3) return fail(nullptr, LBM_EINVAL, "Ma * c_s must stay below 0.3%s");
+    const double gbeta = U0 * U0 / (dT * L);
+    const double nu = sqrt(Pr / Ra) * U0 * L;
+    const double alpha = nu / Pr;
+    const double cs2p = o.cs2_phi;
+    if (!(cs2p > 0 && cs2p <= (lattice == 15 ? 0.5 : 1.0 / 3.0)))
+        return fail(nullptr, LBM_EINVAL, "cs2_phi outside the range with non-negative rest weights%s");
+    const double om_nu = 1.0 / (3.0 * nu + 0.5);       // nu = c_s^2 (1/omega - 1/2), App. A
+    const double om_phi = 1.0 / (alpha / cs2p + 0.5);  // D = c_sphi^2 (1/omega - 1/2), Eq. 23
+    if (!(om_nu > 0 && om_nu < 2) || !(om_phi > 0 && om_phi < 2))
+        return fail(nullptr, LBM_EINVAL, "relaxation rate outside (0, 2)%s");
+    memset(out, 0, sizeof *out);
+    for (int b = 0; b < 15; ++b) {
+        out->omega_f[b] = (b >= 4 && b <= 9) ? om_nu : 1.0;
+        out->omega_g[b] = (b >= 1 && b <= 3) ? om_phi : 1.0;
+    }
+    out->gbeta = gbeta;
+    out->T_hot = 0.5 * dT;
+    out->T_cold = -0.5 * dT;
+    out->cs2_phi = cs2p;
+    out->U0 = U0;
+    out->e4_mode = o.e4_mode;
+    out->adiabatic_mode = o.adiabatic_mode;
+    out->boundary = LBM_BC_CAVITY;
+    return LBM_OK;
+}
+
+static int64_t plane_of(int64_t ncell) { return (ncell + 63) / 64 * 64; }
+
+struct Layout {
+    size_t F[2], G[2], snap, staging, partials, result, bits, total;
+};
+
+static Layout layout_of(const lbm_grid* g, int q, int precision) {
+    const int64_t ncell = (int64_t)g->nx * g->ny * g->nz;
+    const int64_t plane = plane_of(ncell);
+    const size_t rs = precision == LBM_FP64 ? 8 : 4;
+    Layout L;
+    size_t off = 0;
+    for (int b = 0; b < 2; ++b) { L.F[b] = off; off = align_up(off + 15 * plane * rs, 256); }
+    for (int b = 0; b < 2; ++b) { L.G[b] = off; off = align_up(off + q * plane * rs, 256); }
+    L.snap = off; off = align_up(off + plane * rs, 256);
+    L.staging = off; off = align_up(off + plane * 8, 256);
+    L.partials = off; off = align_up(off + 2 * kPartialBlocks * 8, 256);
+    L.result = off; off = align_up(off + kResultDoubles * 8, 256);
+    L.bits = off; off = align_up(off + 256, 256);
+    L.total = off;
+    return L;
+}
+
+extern "C" size_t lbm_arena_bytes(const lbm_grid* grid, int lattice, int precision) {
+    if (!valid_grid(grid) || !valid_lattice(lattice)) return 0;
+    return layout_of(grid, lattice, precision).total;
+}
+
+template <typename real>
+static DevParams<real> dev_params(const lbm_ctx* c) {
+    DevParams<real> p;
+    memset(&p, 0, sizeof p);
+    const lbm_params& P = c->params;
+    for (int b = 0; b < 15; ++b) {
+        p.om_f[b] = (real)P.omega_f[b];
+        p.om_g[b] = (real)P.omega_g[b];
+    }
+    const double cs = P.cs2_phi;
+    double w0, w1, w7;
+    if (c->Q == 15) {
+        w7 = cs * cs / 8.0;
+        w1 = 0.5 * (cs - cs * cs);
+        w0 = 1.0 - 6.0 * w1 - 8.0 * w7;
+    } else {
+        w7 = 0.0;
+        w1 = 0.5 * cs;
+        w0 = 1.0 - 6.0 * w1;
+    }
+    for (int a = 0; a < 15; ++a) p.wg[a] = (real)(a == 0 ? w0 : a < 7 ? w1 : w7);
+    p.gbeta = (real)P.gbeta;
+    p.T0 = (real)(0.5 * (P.T_hot + P.T_cold));
+    p.T_hot = (real)P.T_hot;
+    p.T_cold = (real)P.T_cold;
+    p.cs2_phi = (real)P.cs2_phi;
+    p.ext_fx = (real)P.ext_force[0];
+    p.ext_fy = (real)P.ext_force[1];
+    p.ext_fz = (real)P.ext_force[2];
+    p.e4_mode = P.e4_mode;
+    p.adiabatic_mode = P.adiabatic_mode;
+    p.boundary = P.boundary;
+    p.nx = c->grid.nx;
+    p.ny = c->grid.ny;
+    p.nz = c->grid.nz;
+    p.ncell = c->ncell;
+    p.plane = c->plane;
+    return p;
+}
+
+// Wait for all work on the context's stream, polling with the context's time bound.
+static int wait_stream(lbm_ctx* c) {
+    cudaEvent_t ev;
+    CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, c->stream);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev);
+        return fail(c, LBM_ECUDA, "CUDA error in cudaEventRecord: %s", cudaGetErrorString(e));
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        e = cudaEventQuery(ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) {
+            cudaEventDestroy(ev);
+            return fail(c, LBM_ECUDA, "CUDA error while waiting: %s", cudaGetErrorString(e));
+        }
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > c->opt.timeout_s) {
+            cudaEventDestroy(ev);
+            return fail(c, LBM_ETIMEOUT, "timed out waiting for the GPU%s");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
+    }
+    cudaEventDestroy(ev);
+    return LBM_OK;
+}
+
+static int check_params(const lbm_params* p, int q) {
+    for (int b = 4; b < 15; ++b)
+        if (!(p->omega_f[b] > 0 && p->omega_f[b] < 2)) return 0;
+    for (int b = 1; b < q; ++b)
+        if (!(p->omega_g[b] > 0 && p->omega_g[b] < 2)) return 0;
+    const double cmax = q == 15 ? 0.5 : 1.0 / 3.0;
+    if (!(p->cs2_phi > 0 && p->cs2_phi <= cmax)) return 0;
+    if (p->e4_mode != 0 && p->e4_mode != 1) return 0;
+    if (p->adiabatic_mode != 0 && p->adiabatic_mode != 1) return 0;
+    if (p->boundary < 0 || p->boundary > 15) return 0;
+    return 1;
+}
+
+template <typename real>
+static int run_init(lbm_ctx* c) {
+    DevParams<real> p = dev_params<real>(c);
+    CUDA_OR_FAIL(c, launch_init<real>(c->dev, p, c->opt.seed, c->opt.noise_amp, c->stream));
+    CUDA_OR_FAIL(c, launch_residual<real>(c->dev, 0, p, 0, c->stream));
+    return LBM_OK;
+}
+
+extern "C" int lbm_create_params(const lbm_grid* grid, int lattice, const lbm_params* params,
+                                 const lbm_options* opt, lbm_ctx** out) {
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL%s");
+    *out = nullptr;
+    if (!valid_grid(grid)) return fail(nullptr, LBM_EINVAL, "invalid grid%s");
+    if (!valid_lattice(lattice)) return fail(nullptr, LBM_EINVAL, "lattice must be 15 or 7%s");
+    if (!params || !check_params(params, lattice))
+        return fail(nullptr, LBM_EINVAL, "invalid parameters (rates must lie in (0, 2))%s");
+    lbm_options o;
+    if (opt) o = *opt; else lbm_default_options(&o);
+    if (o.precision != LBM_FP32 && o.precision != LBM_FP64)
+        return fail(nullptr, LBM_EINVAL, "precision must be LBM_FP32 or LBM_FP64%s");
+    if (o.residual_interval < 0 || !(o.timeout_s > 0))
+        return fail(nullptr, LBM_EINVAL, "invalid residual_interval or timeout%s");
+
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation failed%s");
+    c->grid = *grid;
+    c->Q = lattice;
+    c->precision = o.precision;
+    c->params = *params;
+    c->opt = o;
+    c->ncell = (int64_t)grid->nx * grid->ny * grid->nz;
+    c->plane = plane_of(c->ncell);
+    c->rsize = o.precision == LBM_FP64 ? 8 : 4;
+    c->stream = (cudaStream_t)o.cuda_stream;
+    c->cur = 0;
+    c->steps = 0;
+    c->last_residual = -1.0;
+    int rc = LBM_OK;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        rc = fail(nullptr, LBM_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+        delete c;
+        return rc;
+    }
+    const Layout L = layout_of(grid, lattice, o.precision);
+    if (o.device_arena) {
+        if (o.device_arena_bytes < L.total || ((uintptr_t)o.device_arena & 255)) {
+            delete c;
+            return fail(nullptr, LBM_ENOMEM, "device arena too small or not 256-byte aligned%s");
+        }
+        c->arena = o.device_arena;
+        c->own_arena = false;
+    } else {
+        e = cudaMalloc(&c->arena, L.total);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(nullptr, LBM_ENOMEM, "cudaMalloc of the state failed: %s", cudaGetErrorString(e));
+        }
+        c->own_arena = true;
+    }
+    c->arena_bytes = L.total;
+    e = cudaMallocHost(&c->host_bits, 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        if (c->own_arena) cudaFree(c->arena);
+        delete c;
+        return fail(nullptr, LBM_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
+    }
+    char* base = static_cast<char*>(c->arena);
+    c->dev.precision = o.precision;
+    c->dev.Q = lattice;
+    for (int b = 0; b < 2; ++b) {
+        c->dev.F[b] = base + L.F[b];
+        c->dev.G[b] = base + L.G[b];
+    }
+    c->dev.snap = base + L.snap;
+    c->dev.staging = reinterpret_cast<double*>(base + L.staging);
+    c->dev.partials = reinterpret_cast<double*>(base + L.partials);
+    c->dev.result = reinterpret_cast<double*>(base + L.result);
+    c->dev.resid_bits = reinterpret_cast<unsigned long long*>(base + L.bits);
+    c->dev.nonfinite = reinterpret_cast<int*>(base + L.bits + 64);
+
+    rc = LBM_OK;
+    if (cudaMemsetAsync(base + L.bits, 0, 256, c->stream) != cudaSuccess)
+        rc = fail(c, LBM_ECUDA, "cudaMemsetAsync failed%s");
+    if (rc == LBM_OK) rc = o.precision == LBM_FP64 ? run_init<double>(c) : run_init<float>(c);
+    if (rc == LBM_OK) rc = wait_stream(c);
+    if (rc != LBM_OK) {
+        g_err = c->err;
+        lbm_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+extern "C" int lbm_create(const lbm_grid* grid, int lattice, double Ra, double Pr, double Ma,
+                          const lbm_options* opt, lbm_ctx** out) {
+    lbm_params p;
+    int rc = lbm_derive_params(grid, lattice, Ra, Pr, Ma, opt, &p);
+    if (rc != LBM_OK) {
+        if (out) *out = nullptr;
+        return rc;
+    }
+    return lbm_create_params(grid, lattice, &p, opt, out);
+}
+
+template <typename real>
+static int run_steps(lbm_ctx* c, int64_t n, bool* checked) {
+    const DevParams<real> p = dev_params<real>(c);
+    const int R = c->opt.residual_interval;
+    for (int64_t s = 0; s < n; ++s) {
+        CUDA_OR_FAIL(c, launch_step<real>(c->dev, c->cur, p, c->stream));
+        c->cur ^= 1;
+        c->steps += 1;
+        if (R > 0 && c->steps % R == 0) {
+            CUDA_OR_FAIL(c, cudaMemsetAsync(c->dev.resid_bits, 0, sizeof(unsigned long long), c->stream));
+            CUDA_OR_FAIL(c, launch_residual<real>(c->dev, c->cur, p, 1, c->stream));
+            *checked = true;
+        }
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_step(lbm_ctx* c, int64_t n) {
+    if (!c || n < 0) return fail(c, LBM_EINVAL, "invalid context or step count%s");
+    DeviceGuard g(c->device);
+    bool checked = false;
+    int rc = c->precision == LBM_FP64 ? run_steps<double>(c, n, &checked)
+                                      : run_steps<float>(c, n, &checked);
+    if (rc != LBM_OK || !checked) return rc;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->host_bits, c->dev.resid_bits, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->host_bits + 1, c->dev.nonfinite, sizeof(int),
+                                    cudaMemcpyDeviceToHost, c->stream));
+    rc = wait_stream(c);
+    if (rc != LBM_OK) return rc;
+    unsigned long long bits = c->host_bits[0];
+    double r;
+    memcpy(&r, &bits, sizeof r);
+    c->last_residual = r;
+    if (*reinterpret_cast<int*>(c->host_bits + 1))
+        return fail(c, LBM_EDIVERGED, "non-finite temperature detected%s");
+    return LBM_OK;
+}
+
+template <typename real>
+static int run_fields(lbm_ctx* c, double* const* outs) {
+    const DevParams<real> p = dev_params<real>(c);
+    for (int w = 0; w < 5; ++w) {
+        if (!outs[w]) continue;
+        CUDA_OR_FAIL(c, launch_field<real>(c->dev, c->cur, p, w, c->stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(outs[w], c->dev.staging, c->ncell * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->stream));
+        int rc = wait_stream(c);
+        if (rc != LBM_OK) return rc;
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_fields(lbm_ctx* c, double* rho, double* ux, double* uy, double* uz, double* T) {
+    if (!c) return fail(c, LBM_EINVAL, "NULL context%s");
+    DeviceGuard g(c->device);
+    double* outs[5] = {rho, ux, uy, uz, T};
+    return c->precision == LBM_FP64 ? run_fields<double>(c, outs) : run_fields<float>(c, outs);
+}
+
+extern "C" int lbm_nusselt(lbm_ctx* c, lbm_nu* out) {
+    if (!c || !out) return fail(c, LBM_EINVAL, "NULL argument%s");
+    if (c->grid.nx < 2) return fail(c, LBM_EINVAL, "lbm_nusselt needs nx >= 2%s");
+    DeviceGuard g(c->device);
+    if (c->precision == LBM_FP64) {
+        CUDA_OR_FAIL(c, launch_nusselt<double>(c->dev, c->cur, dev_params<double>(c), c->params.U0, c->stream));
+    } else {
+        CUDA_OR_FAIL(c, launch_nusselt<float>(c->dev, c->cur, dev_params<float>(c), c->params.U0, c->stream));
+    }
+    double r[kResultDoubles];
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(r, c->dev.result, 11 * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+    int rc = wait_stream(c);
+    if (rc != LBM_OK) return rc;
+    out->hot_wall_mean = r[0];
+    out->cold_wall_mean = r[1];
+    out->mid_mean = r[2];
+    out->mid_max = r[3];
+    out->mid_max_z = r[4];
+    out->mid_min = r[5];
+    out->mid_min_z = r[6];
+    out->umax = r[7];
+    out->umax_z = r[8];
+    out->wmax = r[9];
+    out->wmax_x = r[10];
+    return LBM_OK;
+}
+
+extern "C" int lbm_residual(lbm_ctx* c, double* max_dT) {
+    if (!c || !max_dT) return fail(c, LBM_EINVAL, "NULL argument%s");
+    *max_dT = c->last_residual;
+    return LBM_OK;
+}
+
+template <typename real>
+static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const double* gin) {
+    const int64_t n = c->ncell;
+    for (int side = 0; side < 2; ++side) {
+        const int q = side == 0 ? 15 : c->Q;
+        real* dev = static_cast<real*>(side == 0 ? c->dev.F[c->cur] : c->dev.G[c->cur]);
+        for (int a = 0; a < q; ++a) {
+            real* plane = dev + (int64_t)a * c->plane;
+            if (fin || gin) {  // host -> device
+                const double* src = (side == 0 ? fin : gin) + (int64_t)a * n;
+                CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dev.staging, src, n * sizeof(double),
+                                                cudaMemcpyHostToDevice, c->stream));
+                CUDA_OR_FAIL(c, launch_to_real<real>(plane, c->dev.staging, n, c->stream));
+            } else {  // device -> host
+                double* dst = (side == 0 ? f : g) + (int64_t)a * n;
+                CUDA_OR_FAIL(c, launch_to_double<real>(c->dev.staging, plane, n, c->stream));
+                CUDA_OR_FAIL(c, cudaMemcpyAsync(dst, c->dev.staging, n * sizeof(double),
+                                                cudaMemcpyDeviceToHost, c->stream));
+            }
+            // the staging plane is reused: finish this plane before the next one
+            int rc = wait_stream(c);
+            if (rc != LBM_OK) return rc;
+        }
+    }
+    if (fin || gin) {
+        CUDA_OR_FAIL(c, launch_residual<real>(c->dev, c->cur, dev_params<real>(c), 0, c->stream));
+        c->last_residual = -1.0;
+        return wait_stream(c);
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_populations(lbm_ctx* c, double* f, double* g) {
+    if (!c || !f || !g) return fail(c, LBM_EINVAL, "NULL argument%s");
+    DeviceGuard gd(c->device);
+    return c->precision == LBM_FP64 ? transfer<double>(c, f, g, nullptr, nullptr)
+                                    : transfer<float>(c, f, g, nullptr, nullptr);
+}
+
+extern "C" int lbm_set_populations(lbm_ctx* c, const double* f, const double* g) {
+    if (!c || !f || !g) return fail(c, LBM_EINVAL, "NULL argument%s");
+    DeviceGuard gd(c->device);
+    return c->precision == LBM_FP64 ? transfer<double>(c, nullptr, nullptr, f, g)
+                                    : transfer<float>(c, nullptr, nullptr, f, g);
+}
+
+extern "C" int lbm_get_params(const lbm_ctx* c, lbm_params* out) {
+    if (!c || !out) return LBM_EINVAL;
+    *out = c->params;
+    return LBM_OK;
+}
+
+extern "C" int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; }
+
+extern "C" const char* lbm_last_error(const lbm_ctx* c) {
+    return c ? c->err.c_str() : g_err.c_str();
+}
+
+extern "C" int lbm_synchronize(lbm_ctx* c) {
+    if (!c) return fail(c, LBM_EINVAL, "NULL context%s");
+    DeviceGuard g(c->device);
+    return wait_stream(c);
+}
+
+extern "C" void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    {
+        DeviceGuard g(c->device);
+        wait_stream(c);
+        if (c->own_arena && c->arena) cudaFree(c->arena);
+        if (c->host_bits) cudaFreeHost(c->host_bits);
+    }
+    delete c;
+}

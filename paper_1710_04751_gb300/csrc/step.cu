@@ -1,0 +1,122 @@
+// step.cu -- the fused stream-and-collide time step of arXiv:1710.04751.
+//
+// One thread per lattice node.  Each thread pulls its 15 flow and Q thermal
+// populations from the post-collision arrays of the previous step (Eqs. 2b, 13b),
+// substitutes the wall rules for links whose source node lies outside the cavity
+// (Sec. 3), computes T (Eq. 25), the Boussinesq force (Sec. 3) and u (Eq. 3), runs the
+// flow cascade (App. A) and the thermal cascade (Sec. 2.2 or App. C) in registers and
+// writes the post-collision populations of its own node to the other buffer.
+//
+// Memory layout: structure of arrays, population a of node c at a * plane + c with
+// c = (k * ny + j) * nx + i; consecutive threads own consecutive x, so every load and
+// store of a warp is one contiguous run (shifted by at most one element for e_x != 0).
+#include "collide.cuh"
+#include "internal.h"
+#include "lattice.cuh"
+
+namespace lbm {
+
+// Source coordinate along one axis with periodic wrap when the axis is periodic.
+__device__ __forceinline__ int wrap_axis(int s, int n, bool periodic) {
+    if (periodic) {
+        if (s < 0) s += n;
+        else if (s >= n) s -= n;
+    }
+    return s;
+}
+
+template <typename real, int Q>
+__device__ __forceinline__ void pull(const real* __restrict__ Fin, const real* __restrict__ Gin,
+                                     const DevParams<real>& p, int i, int j, int k, int64_t c,
+                                     real (&f)[15], real (&g)[Q]) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int64_t P = p.plane;
+    const bool px = p.boundary & 1, py = p.boundary & 2, pz = p.boundary & 4;
+    const bool x_dirichlet = !(p.boundary & 8);
+#pragma unroll
+    for (int a = 0; a < 15; ++a) {
+        const int si = wrap_axis(i - ex(a), nx, px);
+        const int sj = wrap_axis(j - ey(a), ny, py);
+        const int sk = wrap_axis(k - ez(a), nz, pz);
+        const bool in_x = (unsigned)si < (unsigned)nx;
+        const bool in_y = (unsigned)sj < (unsigned)ny;
+        const bool in_z = (unsigned)sk < (unsigned)nz;
+        const int64_t s = ((int64_t)sk * ny + sj) * nx + si;
+        if (in_x && in_y && in_z) {
+            f[a] = Fin[a * P + s];
+        } else {
+            f[a] = Fin[opp(a) * P + c];  // no-slip: half-way bounce-back
+        }
+        if (a < Q) {
+            if (in_x && in_y && in_z) {
+                g[a] = Gin[a * P + s];
+            } else if (x_dirichlet && !in_x) {
+                // Dirichlet T: anti-bounce-back with the face temperature
+                const real Tw = si < 0 ? p.T_cold : p.T_hot;
+                g[a] = -Gin[opp(a) * P + c] + real(2) * p.wg[a] * Tw;
+            } else if (p.adiabatic_mode == 1) {
+                // adiabatic, specular: mirror the crossed components; the population is
+                // the one that left toward the wall from the mirrored source node
+                int di = ex(a), dj = ey(a), dk = ez(a), ri = si, rj = sj, rk = sk;
+                if (!in_x) { di = -di; ri = i; }
+                if (!in_y) { dj = -dj; rj = j; }
+                if (!in_z) { dk = -dk; rk = k; }
+                const int b = dir_index(di, dj, dk);
+                g[a] = Gin[b * P + ((int64_t)rk * ny + rj) * nx + ri];
+            } else {
+                g[a] = Gin[opp(a) * P + c];  // adiabatic, bounce-back
+            }
+        }
+    }
+}
+
+template <typename real, int Q>
+__global__ void __launch_bounds__(256) step_kernel(const real* __restrict__ Fin,
+                                                   const real* __restrict__ Gin,
+                                                   real* __restrict__ Fout,
+                                                   real* __restrict__ Gout, DevParams<real> p) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p.ncell) return;
+    const int i = (int)(c % p.nx);
+    const int64_t t = c / p.nx;
+    const int j = (int)(t % p.ny);
+    const int k = (int)(t / p.ny);
+
+    real f[15], g[Q];
+    pull<real, Q>(Fin, Gin, p, i, j, k, c, f, g);
+
+    real T = real(0);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) T += g[a];
+    const real Fz = p.ext_fz + p.gbeta * (T - p.T0);
+
+    real ux, uy, uz;
+    collide_flow<real>(f, p.ext_fx, p.ext_fy, Fz, p, ux, uy, uz);
+#pragma unroll
+    for (int a = 0; a < 15; ++a) Fout[a * p.plane + c] = f[a];
+
+    if constexpr (Q == 15) collide_thermal15<real>(g, ux, uy, uz, p);
+    else collide_thermal7<real>(g, ux, uy, uz, p);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) Gout[a * p.plane + c] = g[a];
+}
+
+template <typename real>
+cudaError_t launch_step(const DevState& s, int cur, const DevParams<real>& p, cudaStream_t st) {
+    const int threads = 256;
+    const int64_t blocks = (p.ncell + threads - 1) / threads;
+    const real* Fin = static_cast<const real*>(s.F[cur]);
+    const real* Gin = static_cast<const real*>(s.G[cur]);
+    real* Fout = static_cast<real*>(s.F[cur ^ 1]);
+    real* Gout = static_cast<real*>(s.G[cur ^ 1]);
+    if (s.Q == 15)
+        step_kernel<real, 15><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Fout, Gout, p);
+    else
+        step_kernel<real, 7><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Fout, Gout, p);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_step<float>(const DevState&, int, const DevParams<float>&, cudaStream_t);
+template cudaError_t launch_step<double>(const DevState&, int, const DevParams<double>&, cudaStream_t);
+
+}  // namespace lbm

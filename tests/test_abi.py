@@ -1,0 +1,95 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads, exports
+every entry point include/lbm.h declares, derives the paper's parameters and rejects
+invalid arguments before touching the device."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_1710_04751_gb300 as lbm
+from paper_1710_04751_gb300 import lbm as binding
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "lbm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_entry_point():
+    L = binding.load()
+    names = declared_functions()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(names) == sorted(binding.EXPORTS)
+
+
+def test_structure_sizes_match_header_layout():
+    # lbm_params: 15+15+4+3+1 doubles then 3 ints (+4 bytes padding)
+    assert ctypes.sizeof(binding.Params) == (15 + 15 + 4 + 3 + 1) * 8 + 16
+    assert ctypes.sizeof(binding.Nu) == 11 * 8
+
+
+@pytest.mark.parametrize("n,Ra", [(32, 1e3), (128, 1e5), (256, 1e6), (91, 1e4)])
+def test_derive_params_matches_oracle(n, Ra):
+    p = lbm.derive_params((n, n, n), 15, Ra, 0.71, 0.05 * math.sqrt(3.0))
+    ref = oracle.physical_parameters(n, Ra, 0.71, 0.05 * math.sqrt(3.0))
+    assert p.omega_f[4] == pytest.approx(ref["omega_nu"], rel=1e-14)
+    assert p.omega_g[1] == pytest.approx(ref["omega_phi"], rel=1e-14)
+    assert p.gbeta == pytest.approx(ref["gbeta"], rel=1e-14)
+    assert p.U0 == pytest.approx(0.05, rel=1e-14)
+    assert [p.omega_f[b] for b in range(10, 15)] == [1.0] * 5
+    assert [p.omega_g[b] for b in range(4, 15)] == [1.0] * 11
+    assert p.T_hot == 0.5 and p.T_cold == -0.5 and p.boundary == lbm.BC_CAVITY
+
+
+def test_paper_parameter_values():
+    # 32^3, Ra = 1e3, Pr = 0.71, U0 = 0.05
+    p = lbm.derive_params((32, 32, 32), 15, 1e3, 0.71, 0.05 * math.sqrt(3.0))
+    assert round(p.omega_f[4], 4) == 1.5926 and round(p.omega_g[1], 4) == 1.4703
+    assert p.gbeta == pytest.approx(7.8125e-5)
+
+
+@pytest.mark.parametrize("args", [
+    dict(grid=(0, 4, 4)), dict(lattice=9), dict(Ra=-1.0), dict(Pr=0.0), dict(Ma=0.6),
+    dict(lattice=7, cs2_phi=0.4),  # D3Q7 rest weight 1 - 3 cs2_phi < 0
+])
+def test_derive_params_rejects(args):
+    a = dict(grid=(16, 16, 16), lattice=15, Ra=1e3, Pr=0.71, Ma=0.0866)
+    a.update(args)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.derive_params(a["grid"], a["lattice"], a["Ra"], a["Pr"], a["Ma"],
+                          **({"cs2_phi": a["cs2_phi"]} if "cs2_phi" in a else {}))
+    assert e.value.code == binding.LBM_EINVAL
+
+
+def test_create_rejects_bad_rates_without_touching_the_device():
+    L = binding.load()
+    p = lbm.derive_params((8, 8, 8), 15, 1e3, 0.71, 0.0866)
+    p.omega_f[12] = 2.0
+    ctx = ctypes.c_void_p()
+    rc = L.lbm_create_params(ctypes.byref(binding.Grid(8, 8, 8)), 15, ctypes.byref(p), None,
+                             ctypes.byref(ctx))
+    assert rc == binding.LBM_EINVAL and not ctx.value
+    assert b"rates" in L.lbm_last_error(None)
+    p.omega_f[12] = 1.0
+    p.cs2_phi = 0.4  # D3Q7 needs cs2_phi <= 1/3 (non-negative rest weight)
+    rc = L.lbm_create_params(ctypes.byref(binding.Grid(8, 8, 8)), 7, ctypes.byref(p), None,
+                             ctypes.byref(ctx))
+    assert rc == binding.LBM_EINVAL
+
+
+def test_arena_bytes():
+    n = 128 ** 3
+    b = lbm.arena_bytes((128, 128, 128), 15, lbm.FP32)
+    # two copies of 30 populations + snapshot (4 B) + staging plane (8 B) + small scratch
+    assert 2 * 30 * 4 * n + 12 * n <= b <= 2 * 30 * 4 * n + 12 * n + 64 * 1024
+    assert lbm.arena_bytes((128, 128, 128), 7, lbm.FP64) > lbm.arena_bytes((128, 128, 128), 7, lbm.FP32)
+    assert lbm.arena_bytes((0, 1, 1), 15, lbm.FP32) == 0
