@@ -86,7 +86,8 @@ typedef struct {
     int precision;            /* LBM_FP32 (default) or LBM_FP64 storage and arithmetic */
     uint64_t seed;            /* noise seed of the initial temperature (default 1) */
     double noise_amp;         /* initial T = uniform noise in [-amp, amp] (default 1e-6) */
-    double cs2_phi;           /* default 1/3 */
+    double cs2_phi;           /* c_sphi^2; 0 (default) = 1/3 for D3Q15, 1/4 for D3Q7 (at 1/3 the
+                                 D3Q7 rest equilibrium phi (1 - 3 c_sphi^2 - u^2) is negative) */
     int e4_mode;              /* default 0 */
     int adiabatic_mode;       /* default LBM_ADIABATIC_SPECULAR */
     int residual_interval;    /* steps between residual / NaN checks in lbm_step (default 100, 0 = off) */

@@ -195,8 +195,12 @@ class Problem:
         self.ext_force = tuple(map(float, ext_force))
 
     @classmethod
-    def cavity(cls, n, Ra, Pr=0.71, Ma=0.05 * math.sqrt(3.0), q_g=15, cs2_phi=1.0 / 3.0,
+    def cavity(cls, n, Ra, Pr=0.71, Ma=0.05 * math.sqrt(3.0), q_g=15, cs2_phi=None,
                e4_mode=0, ny=None, nz=None, adiabatic_mode=1):
+        """The cavity of Sec. 3.  cs2_phi defaults to 1/3 (D3Q15) or 1/4 (D3Q7: at 1/3 its
+        rest equilibrium phi (1 - 3 cs2_phi - u^2) turns negative)."""
+        if cs2_phi is None:
+            cs2_phi = 1.0 / 3.0 if q_g == 15 else 0.25
         par = physical_parameters(n, Ra, Pr, Ma, cs2_phi)
         return cls(n, ny or n, nz or n, q_g=q_g, omega_nu=par["omega_nu"],
                    omega_phi=par["omega_phi"], gbeta=par["gbeta"], cs2_phi=cs2_phi,

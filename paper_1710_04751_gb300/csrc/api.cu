@@ -73,7 +73,7 @@ extern "C" void lbm_default_options(lbm_options* o) {
     o->precision = LBM_FP32;
     o->seed = 1;
     o->noise_amp = 1e-6;
-    o->cs2_phi = 1.0 / 3.0;
+    o->cs2_phi = 0.0;  // lattice default: 1/3 (D3Q15), 1/4 (D3Q7)
     o->e4_mode = 0;
     o->adiabatic_mode = LBM_ADIABATIC_SPECULAR;
     o->residual_interval = 100;
@@ -105,7 +105,9 @@ extern "C" int lbm_derive_params(const lbm_grid* grid, int lattice, double Ra, d
     const double gbeta = U0 * U0 / (dT * L);
     const double nu = sqrt(Pr / Ra) * U0 * L;
     const double alpha = nu / Pr;
-    const double cs2p = o.cs2_phi;
+    // c_sphi^2: "typically 1/3" (Sec. 2.2).  On D3Q7 that value gives a negative rest
+    // equilibrium phi (1 - 3 c_sphi^2 - u^2) for any u != 0, so D3Q7 defaults to 1/4.
+    const double cs2p = o.cs2_phi > 0 ? o.cs2_phi : (lattice == 15 ? 1.0 / 3.0 : 0.25);
     if (!(cs2p > 0 && cs2p <= (lattice == 15 ? 0.5 : 1.0 / 3.0)))
         return fail(nullptr, LBM_EINVAL, "cs2_phi outside the range with non-negative rest weights%s");
     const double om_nu = 1.0 / (3.0 * nu + 0.5);       // nu = c_s^2 (1/omega - 1/2), App. A

@@ -1,13 +1,22 @@
 // collide.cuh -- one-cell cascaded collisions of arXiv:1710.04751 in registers.
 //
-//   collide_flow      Appendix A: D3Q15 flow kernel g^_4..g^_14 with the body-force
-//                     source S folded into the back-transform (Eq. 2a)
-//   collide_thermal15 Sec. 2.2: D3Q15 scalar kernel h^_1..h^_14 (Eq. 13a, R = 0)
-//   collide_thermal7  Appendix C: D3Q7 scalar kernel h^_1..h^_6
+//   collide_flow      Appendix A: D3Q15 flow collision with the body-force source
+//   collide_thermal15 Sec. 2.2: D3Q15 scalar collision (R = 0)
+//   collide_thermal7  Appendix C: D3Q7 scalar collision (R = 0)
 //
-// Raw moments are accumulated with compile-time monomials (lattice.cuh), so every sum
-// is a short chain of adds/subtracts; the back-transforms multiply by the integer
-// entries of K only where they are non-zero.
+// The paper writes each cascade as closed forms for the kernel components (g^_b, h^_b)
+// that, added through K, make every central moment relax toward its equilibrium at its
+// own rate while the lower orders are already relaxed.  The post-collision state that
+// defines is computed here in an equivalent, cheaper order (same arithmetic result up to
+// rounding):
+//   1. raw moments of the populations (Eq. 17 / App. A notation) with a three-level
+//      sign transform of the eight diagonal links;
+//   2. central moments about u (binomial theorem, Eqs. 14 and 17);
+//   3. their increments delta = kappa~ - kappa: each moment relaxes with its rate toward
+//      its equilibrium (Eq. 15 for the scalar; Maxwellian for the flow), plus, for the
+//      flow, the central moments Gamma of the source;
+//   4. the increments shifted back to raw moments and inverted to populations
+//      (the inverse of step 1), so that p~ = p + increment -- Eqs. 2a and 13a.
 #pragma once
 
 #include "internal.h"
@@ -15,240 +24,249 @@
 
 namespace lbm {
 
-template <int M, int Q, typename real>
-__device__ __forceinline__ real moment(const real (&p)[Q]) {
-    real s = real(0);
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        if (mono(M, a) == 1) s += p[a];
-        else if (mono(M, a) == -1) s -= p[a];
-    }
-    return s;
+// Raw moments of a D3Q15 population vector, by moment id (Mom).
+template <typename real>
+struct Raw15 {
+    real m0, x, y, z, xy, xz, yz, xx, yy, zz, xyy, xxy, xxz, xyz, xxyy;
+};
+
+// Diagonal links 7..14 are (+-,+-,+-) with bit 0 of (a - 7) set for e_x < 0, bit 1 for
+// e_y < 0, bit 2 for e_z < 0.  Three butterfly levels give all eight signed sums
+// sum_d s_x^i s_y^j s_z^k p_d in 24 additions.
+template <typename real>
+__device__ __forceinline__ Raw15<real> raw15(const real (&p)[15]) {
+    const real a0 = p[7] + p[8], b0 = p[7] - p[8];
+    const real a1 = p[9] + p[10], b1 = p[9] - p[10];
+    const real a2 = p[11] + p[12], b2 = p[11] - p[12];
+    const real a3 = p[13] + p[14], b3 = p[13] - p[14];
+    const real c0 = a0 + a1, c1 = a0 - a1, c2 = a2 + a3, c3 = a2 - a3;
+    const real e0 = b0 + b1, e1 = b0 - b1, e2 = b2 + b3, e3 = b2 - b3;
+    const real H0 = c0 + c2, Hz = c0 - c2, Hy = c1 + c3, Hyz = c1 - c3;
+    const real Hx = e0 + e2, Hxz = e0 - e2, Hxy = e1 + e3, Hxyz = e1 - e3;
+    const real px = p[1] + p[2], qx = p[1] - p[2];
+    const real py = p[3] + p[4], qy = p[3] - p[4];
+    const real pz = p[5] + p[6], qz = p[5] - p[6];
+    Raw15<real> m;
+    m.m0 = p[0] + px + py + pz + H0;
+    m.x = qx + Hx;
+    m.y = qy + Hy;
+    m.z = qz + Hz;
+    m.xy = Hxy;
+    m.xz = Hxz;
+    m.yz = Hyz;
+    m.xx = px + H0;
+    m.yy = py + H0;
+    m.zz = pz + H0;
+    m.xyy = Hx;
+    m.xxy = Hy;
+    m.xxz = Hz;
+    m.xyz = Hxyz;
+    m.xxyy = H0;
+    return m;
 }
 
-// Flow collision (Appendix A).  f: pulled populations fbar, replaced by f~.  F: the
-// body force (Boussinesq + uniform).  Returns u of Eq. (3).
+// Central moments of the 15 monomials about u (binomial theorem).  The zeroth and
+// first orders are not needed by the callers beyond m0, x, y, z below.
+template <typename real>
+__device__ __forceinline__ Raw15<real> central15(const Raw15<real>& m, real ux, real uy, real uz) {
+    const real uxx = ux * ux, uyy = uy * uy, uxy = ux * uy, uxz = ux * uz, uyz = uy * uz;
+    Raw15<real> c;
+    c.m0 = m.m0;
+    c.x = m.x - ux * m.m0;
+    c.y = m.y - uy * m.m0;
+    c.z = m.z - uz * m.m0;
+    c.xy = m.xy - ux * m.y - uy * m.x + uxy * m.m0;
+    c.xz = m.xz - ux * m.z - uz * m.x + uxz * m.m0;
+    c.yz = m.yz - uy * m.z - uz * m.y + uyz * m.m0;
+    c.xx = m.xx - real(2) * ux * m.x + uxx * m.m0;
+    c.yy = m.yy - real(2) * uy * m.y + uyy * m.m0;
+    c.zz = m.zz - real(2) * uz * m.z + uz * uz * m.m0;
+    c.xyy = m.xyy - real(2) * uy * m.xy - ux * m.yy + uyy * m.x + real(2) * uxy * m.y - ux * uyy * m.m0;
+    c.xxy = m.xxy - real(2) * ux * m.xy - uy * m.xx + uxx * m.y + real(2) * uxy * m.x - uxx * uy * m.m0;
+    c.xxz = m.xxz - real(2) * ux * m.xz - uz * m.xx + uxx * m.z + real(2) * uxz * m.x - uxx * uz * m.m0;
+    c.xyz = m.xyz - ux * m.yz - uy * m.xz - uz * m.xy + uxy * m.z + uxz * m.y + uyz * m.x -
+            uxy * uz * m.m0;
+    c.xxyy = m.xxyy - real(2) * uy * m.xxy - real(2) * ux * m.xyy + uyy * m.xx + uxx * m.yy +
+             real(4) * uxy * m.xy - real(2) * ux * uyy * m.x - real(2) * uxx * uy * m.y +
+             uxx * uyy * m.m0;
+    return c;
+}
+
+// Raw moments of a central-moment increment d (zeroth order zero) about u: the inverse
+// binomial shift.
+template <typename real>
+__device__ __forceinline__ Raw15<real> raw_of_central_increment(const Raw15<real>& d, real ux,
+                                                                real uy, real uz) {
+    const real uxx = ux * ux, uyy = uy * uy, uxy = ux * uy, uxz = ux * uz, uyz = uy * uz;
+    Raw15<real> r;
+    r.m0 = real(0);
+    r.x = d.x;
+    r.y = d.y;
+    r.z = d.z;
+    r.xy = d.xy + ux * d.y + uy * d.x;
+    r.xz = d.xz + ux * d.z + uz * d.x;
+    r.yz = d.yz + uy * d.z + uz * d.y;
+    r.xx = d.xx + real(2) * ux * d.x;
+    r.yy = d.yy + real(2) * uy * d.y;
+    r.zz = d.zz + real(2) * uz * d.z;
+    r.xyy = d.xyy + real(2) * uy * d.xy + ux * d.yy + uyy * d.x + real(2) * uxy * d.y;
+    r.xxy = d.xxy + real(2) * ux * d.xy + uy * d.xx + uxx * d.y + real(2) * uxy * d.x;
+    r.xxz = d.xxz + real(2) * ux * d.xz + uz * d.xx + uxx * d.z + real(2) * uxz * d.x;
+    r.xyz = d.xyz + ux * d.yz + uy * d.xz + uz * d.xy + uxy * d.z + uxz * d.y + uyz * d.x;
+    r.xxyy = d.xxyy + real(2) * uy * d.xxy + real(2) * ux * d.xyy + uyy * d.xx + uxx * d.yy +
+             real(4) * uxy * d.xy + real(2) * ux * uyy * d.x + real(2) * uxx * uy * d.y;
+    return r;
+}
+
+// p += the populations whose raw moments are r (inverse of raw15).
+template <typename real>
+__device__ __forceinline__ void add_populations15(real (&p)[15], const Raw15<real>& r) {
+    // diagonal links: inverse of the three-level sign transform (divided by 8)
+    const real G0 = r.xxyy, Gx = r.xyy, Gy = r.xxy, Gz = r.xxz;
+    const real P0 = G0 + Gz, P0m = G0 - Gz, Px = Gx + r.xz, Pxm = Gx - r.xz;
+    const real Py = Gy + r.yz, Pym = Gy - r.yz, Pxy = r.xy + r.xyz, Pxym = r.xy - r.xyz;
+    const real Q0 = P0 + Py, Q1 = P0 - Py, X0 = Px + Pxy, X1 = Px - Pxy;
+    const real Q2 = P0m + Pym, Q3 = P0m - Pym, X2 = Pxm + Pxym, X3 = Pxm - Pxym;
+    const real e = real(0.125);
+    p[7] += e * (Q0 + X0);
+    p[8] += e * (Q0 - X0);
+    p[9] += e * (Q1 + X1);
+    p[10] += e * (Q1 - X1);
+    p[11] += e * (Q2 + X2);
+    p[12] += e * (Q2 - X2);
+    p[13] += e * (Q3 + X3);
+    p[14] += e * (Q3 - X3);
+    // axis links and rest
+    const real px = r.xx - G0, qx = r.x - Gx;
+    const real py = r.yy - G0, qy = r.y - Gy;
+    const real pz = r.zz - G0, qz = r.z - Gz;
+    p[1] += real(0.5) * (px + qx);
+    p[2] += real(0.5) * (px - qx);
+    p[3] += real(0.5) * (py + qy);
+    p[4] += real(0.5) * (py - qy);
+    p[5] += real(0.5) * (pz + qz);
+    p[6] += real(0.5) * (pz - qz);
+    p[0] += r.m0 - px - py - pz - G0;
+}
+
+// Second-order increments from the relaxed combinations xx-yy, xx+yy-2zz, xx+yy+zz.
+template <typename real>
+__device__ __forceinline__ void split_second_order(real d1, real d2, real dtr, real& dxx,
+                                                   real& dyy, real& dzz) {
+    dzz = (dtr - d2) * real(1.0 / 3.0);
+    const real s = dtr - dzz;
+    dxx = real(0.5) * (s + d1);
+    dyy = real(0.5) * (s - d1);
+}
+
+// Flow collision (Appendix A).  f: pulled populations fbar, replaced by f~.  F: the body
+// force (Boussinesq + uniform).  Returns u of Eq. (3).
 //
-// Source (reading of the forcing term the paper takes from its prior work): central
-// moments of the Maxwellian forcing F.(xi-u)/(rho cs^2) f^M -- first order F, xyy/xxy/
-// xxz = cs^2 F, the rest zero -- whose raw moments sigma' follow by the binomial theorem.
-// S = K^-1 m^s is never formed: (K g^)_a + S_a = sum_b K_b(a) (g^_b + m^s_b / |K_b|^2).
+// The moments that relax are those of (fbar + S) (the expansion of App. A's brackets).
+// S, whose central moments are those of the Maxwellian forcing term (first order F,
+// xyy/xxy/xxz = c_s^2 F, the rest zero -- the reading of the source the paper takes from
+// its prior work), enters only through those central moments Gamma:
+//   increment = (1 - omega) Gamma - omega (kappa(fbar) - kappa^eq)   for relaxed moments,
+//   increment = Gamma                                                 for mass and momentum.
 template <typename real>
 __device__ __forceinline__ void collide_flow(real (&f)[15], real Fx, real Fy, real Fz,
                                              const DevParams<real>& p, real& ux, real& uy,
                                              real& uz) {
     const real cs2 = real(1.0 / 3.0);
-    const real half = real(0.5);
-    const real rho = moment<M0>(f);
-    const real jx = moment<MX>(f), jy = moment<MY>(f), jz = moment<MZ>(f);
+    const Raw15<real> m = raw15<real>(f);
+    const real rho = m.m0;
     const real inv_rho = real(1) / rho;
-    ux = (jx + half * Fx) * inv_rho;
-    uy = (jy + half * Fy) * inv_rho;
-    uz = (jz + half * Fz) * inv_rho;
-    const real uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
-
-    // raw moments sigma' of the source
-    const real sxy = ux * Fy + uy * Fx, sxz = ux * Fz + uz * Fx, syz = uy * Fz + uz * Fy;
-    const real sxx = real(2) * ux * Fx, syy = real(2) * uy * Fy, szz = real(2) * uz * Fz;
-    const real sxyy = cs2 * Fx + uyy * Fx + real(2) * ux * uy * Fy;
-    const real sxxy = cs2 * Fy + uxx * Fy + real(2) * ux * uy * Fx;
-    const real sxxz = cs2 * Fz + uxx * Fz + real(2) * ux * uz * Fx;
-    const real sxyz = ux * uy * Fz + ux * uz * Fy + uy * uz * Fx;
-    const real sxxyy = real(2) * cs2 * (ux * Fx + uy * Fy) + real(2) * ux * uyy * Fx +
-                       real(2) * uxx * uy * Fy;
-
-    // eta' = raw moments of (fbar + S)
-    const real e_x = jx + Fx, e_y = jy + Fy;
-    const real exy = moment<MXY>(f) + sxy, exz = moment<MXZ>(f) + sxz, eyz = moment<MYZ>(f) + syz;
-    const real exx = moment<MXX>(f) + sxx, eyy = moment<MYY>(f) + syy, ezz = moment<MZZ>(f) + szz;
-    const real exyy = moment<MXYY>(f) + sxyy, exxy = moment<MXXY>(f) + sxxy;
-    const real exxz = moment<MXXZ>(f) + sxxz, exyz = moment<MXYZ>(f) + sxyz;
-    const real exxyy = moment<MXXYY>(f) + sxxyy;
-
+    ux = (m.x + real(0.5) * Fx) * inv_rho;
+    uy = (m.y + real(0.5) * Fy) * inv_rho;
+    uz = (m.z + real(0.5) * Fz) * inv_rho;
+    const Raw15<real> k = central15<real>(m, ux, uy, uz);
     const real* om = p.om_f;
-    const real g4 = om[4] * real(0.125) * (-exy + rho * ux * uy + half * (Fx * uy + Fy * ux));
-    const real g5 = om[5] * real(0.125) * (-exz + rho * ux * uz + half * (Fx * uz + Fz * ux));
-    const real g6 = om[6] * real(0.125) * (-eyz + rho * uy * uz + half * (Fy * uz + Fz * uy));
-    const real g7 = om[7] * real(0.25) * (-(exx - eyy) + rho * (uxx - uyy) + (Fx * ux - Fy * uy));
-    const real g8 = om[8] * real(1.0 / 12.0) *
-                    (-(exx + eyy - real(2) * ezz) + rho * (uxx + uyy - real(2) * uzz) +
-                     (Fx * ux + Fy * uy - real(2) * Fz * uz));
-    const real g9 = om[9] * real(1.0 / 18.0) *
-                    (-(exx + eyy + ezz) + rho * (uxx + uyy + uzz) + (Fx * ux + Fy * uy + Fz * uz) +
-                     rho);
-    const real g10 = om[10] * real(0.0625) *
-                         (-exyy + real(2) * uy * exy + ux * eyy - real(2) * rho * ux * uyy -
-                          half * Fx * uyy - Fy * uy * ux) +
-                     uy * g4 + real(0.125) * ux * (-g7 + g8 + real(3) * g9);
-    const real g11 = om[11] * real(0.0625) *
-                         (-exxy + real(2) * ux * exy + uy * exx - real(2) * rho * uxx * uy -
-                          half * Fy * uxx - Fx * ux * uy) +
-                     ux * g4 + real(0.125) * uy * (g7 + g8 + real(3) * g9);
-    const real g12 = om[12] * real(0.0625) *
-                         (-exxz + real(2) * ux * exz + uz * exx - real(2) * rho * uxx * uz -
-                          half * Fz * uxx - Fx * ux * uz) +
-                     ux * g5 + real(0.125) * uz * (g7 + g8 + real(3) * g9);
-    const real g13 = om[13] * real(0.125) *
-                         (-exyz + ux * eyz + uy * exz + uz * exy - real(2) * rho * ux * uy * uz -
-                          half * (Fx * uy * uz + Fy * ux * uz + Fz * ux * uy)) +
-                     uz * g4 + uy * g5 + ux * g6;
-    // equilibrium of the 4th-order central moment: factorised from the post-collision
-    // second-order central moments (mode 0) or Maxwellian rho cs^4 (mode 1)
-    real E;
-    if (p.e4_mode == 1) {
-        E = rho * real(1.0 / 9.0);
-    } else {
-        const real kxx = exx - real(2) * ux * e_x + uxx * rho + real(2) * g7 + real(2) * g8 +
-                         real(6) * g9;
-        const real kyy = eyy - real(2) * uy * e_y + uyy * rho - real(2) * g7 + real(2) * g8 +
-                         real(6) * g9;
-        E = kxx * kyy * inv_rho;
-    }
-    const real g14 = om[14] * real(0.0625) *
-                         (-exxyy + real(2) * ux * exyy + real(2) * uy * exxy - uxx * eyy -
-                          uyy * exx - real(4) * ux * uy * exy + E + real(3) * rho * uxx * uyy +
-                          Fx * ux * uyy + Fy * uy * uxx) -
-                     real(2) * ux * uy * g4 + real(0.125) * (uxx - uyy) * g7 -
-                     real(0.125) * (uxx + uyy) * g8 - (real(0.375) * (uxx + uyy) + half) * g9 +
-                     real(2) * ux * g10 + real(2) * uy * g11;
-
-    // c_b = g^_b + m^s_b / |K_b|^2 (m^s: projections of S on K; g^_0..3 = 0, m^s_0 = 0)
-    real c[15];
-    c[0] = real(0);
-    c[1] = real(0.1) * Fx;
-    c[2] = real(0.1) * Fy;
-    c[3] = real(0.1) * Fz;
-    c[4] = g4 + real(0.125) * sxy;
-    c[5] = g5 + real(0.125) * sxz;
-    c[6] = g6 + real(0.125) * syz;
-    c[7] = g7 + real(0.25) * (sxx - syy);
-    c[8] = g8 + real(1.0 / 12.0) * (sxx + syy - real(2) * szz);
-    c[9] = g9 + real(1.0 / 18.0) * (sxx + syy + szz);
-    c[10] = g10 + real(1.0 / 160.0) * (real(10) * sxyy - real(8) * Fx);
-    c[11] = g11 + real(1.0 / 160.0) * (real(10) * sxxy - real(8) * Fy);
-    c[12] = g12 + real(1.0 / 160.0) * (real(10) * sxxz - real(8) * Fz);
-    c[13] = g13 + real(0.125) * sxyz;
-    c[14] = g14 + real(1.0 / 1440.0) * (real(90) * sxxyy - real(40) * (sxx + syy + szz));
-#pragma unroll
-    for (int a = 0; a < 15; ++a) {
-        real acc = real(0);
-#pragma unroll
-        for (int b = 1; b < 15; ++b) {
-            if (k15(b, a) != 0) acc += real(k15(b, a)) * c[b];
-        }
-        f[a] += acc;
-    }
+    Raw15<real> d;
+    d.m0 = real(0);
+    d.x = Fx;
+    d.y = Fy;
+    d.z = Fz;
+    d.xy = -om[4] * k.xy;
+    d.xz = -om[5] * k.xz;
+    d.yz = -om[6] * k.yz;
+    const real d1 = -om[7] * (k.xx - k.yy);
+    const real d2 = -om[8] * (k.xx + k.yy - real(2) * k.zz);
+    const real dtr = om[9] * (rho - (k.xx + k.yy + k.zz));  // equilibrium trace 3 c_s^2 rho
+    split_second_order(d1, d2, dtr, d.xx, d.yy, d.zz);
+    d.xyy = (real(1) - om[10]) * cs2 * Fx - om[10] * k.xyy;
+    d.xxy = (real(1) - om[11]) * cs2 * Fy - om[11] * k.xxy;
+    d.xxz = (real(1) - om[12]) * cs2 * Fz - om[12] * k.xxz;
+    d.xyz = -om[13] * k.xyz;
+    // 4th-order equilibrium: factorised from the post-collision second-order central
+    // moments (mode 0), or Maxwellian rho c_s^4 (mode 1)
+    const real E = p.e4_mode == 1 ? rho * real(1.0 / 9.0)
+                                  : (k.xx + d.xx) * (k.yy + d.yy) * inv_rho;
+    d.xxyy = om[14] * (E - k.xxyy);
+    add_populations15<real>(f, raw_of_central_increment<real>(d, ux, uy, uz));
 }
 
-// Thermal D3Q15 collision (Sec. 2.2) with R = 0: g becomes g~; u from the flow.
+// Thermal D3Q15 collision (Sec. 2.2) with R = 0: g becomes g~; u from the flow.  Every
+// moment but the zeroth relaxes (Eq. 15 equilibria: c_sphi^2 phi on the diagonal second
+// order, c_sphi^4 phi for xxyy, zero otherwise).
 template <typename real>
 __device__ __forceinline__ void collide_thermal15(real (&g)[15], real ux, real uy, real uz,
                                                   const DevParams<real>& p) {
-    const real half = real(0.5);
-    const real phi = moment<M0>(g);
-    const real kx = moment<MX>(g), ky = moment<MY>(g), kz = moment<MZ>(g);
-    const real kxy = moment<MXY>(g), kxz = moment<MXZ>(g), kyz = moment<MYZ>(g);
-    const real kxx = moment<MXX>(g), kyy = moment<MYY>(g), kzz = moment<MZZ>(g);
-    const real kxyy = moment<MXYY>(g), kxxy = moment<MXXY>(g), kxxz = moment<MXXZ>(g);
-    const real kxyz = moment<MXYZ>(g), kxxyy = moment<MXXYY>(g);
-    const real uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
-    const real cs2 = p.cs2_phi;
+    const Raw15<real> m = raw15<real>(g);
+    const real phi = m.m0;
+    const Raw15<real> k = central15<real>(m, ux, uy, uz);
     const real* om = p.om_g;
-    real h[15];
-    h[0] = real(0);
-    h[1] = om[1] * real(0.1) * (phi * ux - kx);
-    h[2] = om[2] * real(0.1) * (phi * uy - ky);
-    h[3] = om[3] * real(0.1) * (phi * uz - kz);
-    h[4] = om[4] * real(0.125) * (-kxy + uy * kx + ux * ky - phi * ux * uy) +
-           real(1.25) * (uy * h[1] + ux * h[2]);
-    h[5] = om[5] * real(0.125) * (-kxz + uz * kx + ux * kz - phi * ux * uz) +
-           real(1.25) * (uz * h[1] + ux * h[3]);
-    h[6] = om[6] * real(0.125) * (-kyz + uz * ky + uy * kz - phi * uy * uz) +
-           real(1.25) * (uz * h[2] + uy * h[3]);
-    h[7] = om[7] * real(0.25) *
-               (-(kxx - kyy) + real(2) * (ux * kx - uy * ky) - phi * (uxx - uyy)) +
-           real(5) * (ux * h[1] - uy * h[2]);
-    h[8] = om[8] * real(1.0 / 12.0) *
-               (-(kxx + kyy - real(2) * kzz) + real(2) * (ux * kx + uy * ky - real(2) * uz * kz) -
-                phi * (uxx + uyy - real(2) * uzz)) +
-           real(5.0 / 3.0) * (ux * h[1] + uy * h[2] - real(2) * uz * h[3]);
-    h[9] = om[9] * real(1.0 / 18.0) *
-               (real(3) * cs2 * phi - (kxx + kyy + kzz) + real(2) * (ux * kx + uy * ky + uz * kz) -
-                phi * (uxx + uyy + uzz)) +
-           real(10.0 / 9.0) * (ux * h[1] + uy * h[2] + uz * h[3]);
-    h[10] = om[10] * real(0.0625) *
-                (-kxyy + real(2) * uy * kxy - uyy * kx + ux * kyy - real(2) * ux * uy * ky +
-                 phi * ux * uyy) -
-            (real(0.625) * uyy + half) * h[1] - real(1.25) * ux * uy * h[2] + uy * h[4] +
-            real(0.125) * ux * (-h[7] + h[8] + real(3) * h[9]);
-    h[11] = om[11] * real(0.0625) *
-                (-kxxy + real(2) * ux * kxy + uy * kxx - uxx * ky - real(2) * ux * uy * kx +
-                 phi * uxx * uy) -
-            real(1.25) * ux * uy * h[1] - (real(0.625) * uxx + half) * h[2] + ux * h[4] +
-            real(0.125) * uy * (h[7] + h[8] + real(3) * h[9]);
-    h[12] = om[12] * real(0.0625) *
-                (-kxxz + real(2) * ux * kxz + uz * kxx - real(2) * ux * uz * kx - uxx * kz +
-                 phi * uxx * uz) -
-            real(1.25) * ux * uz * h[1] - (real(0.625) * uxx + half) * h[3] + ux * h[5] +
-            real(0.125) * uz * (h[7] + h[8] + real(3) * h[9]);
-    h[13] = om[13] * real(0.125) *
-                (-kxyz + ux * kyz + uy * kxz + uz * kxy - uy * uz * kx - ux * uz * ky -
-                 ux * uy * kz + phi * ux * uy * uz) -
-            real(1.25) * (uy * uz * h[1] + ux * uz * h[2] + ux * uy * h[3]) + uz * h[4] +
-            uy * h[5] + ux * h[6];
-    h[14] = om[14] * real(0.0625) *
-                (-kxxyy + real(2) * uy * kxxy + real(2) * ux * kxyy - uyy * kxx - uxx * kyy -
-                 real(4) * ux * uy * kxy + real(2) * ux * uyy * kx + real(2) * uxx * uy * ky +
-                 cs2 * cs2 * phi - phi * uxx * uyy) +
-            real(1.25) * (ux * uyy * h[1] + uxx * uy * h[2]) - real(2) * ux * uy * h[4] +
-            real(0.125) * (uxx - uyy) * h[7] - real(0.125) * (uxx + uyy) * h[8] -
-            (real(0.375) * (uxx + uyy) + half) * h[9] + real(2) * (ux * h[10] + uy * h[11]) +
-            uy * h[2] + ux * h[1];
-#pragma unroll
-    for (int a = 0; a < 15; ++a) {
-        real acc = real(0);
-#pragma unroll
-        for (int b = 1; b < 15; ++b) {
-            if (k15(b, a) != 0) acc += real(k15(b, a)) * h[b];
-        }
-        g[a] += acc;
-    }
+    const real cs2 = p.cs2_phi;
+    Raw15<real> d;
+    d.m0 = real(0);
+    d.x = -om[1] * k.x;
+    d.y = -om[2] * k.y;
+    d.z = -om[3] * k.z;
+    d.xy = -om[4] * k.xy;
+    d.xz = -om[5] * k.xz;
+    d.yz = -om[6] * k.yz;
+    const real d1 = -om[7] * (k.xx - k.yy);
+    const real d2 = -om[8] * (k.xx + k.yy - real(2) * k.zz);
+    const real dtr = om[9] * (real(3) * cs2 * phi - (k.xx + k.yy + k.zz));
+    split_second_order(d1, d2, dtr, d.xx, d.yy, d.zz);
+    d.xyy = -om[10] * k.xyy;
+    d.xxy = -om[11] * k.xxy;
+    d.xxz = -om[12] * k.xxz;
+    d.xyz = -om[13] * k.xyz;
+    d.xxyy = om[14] * (cs2 * cs2 * phi - k.xxyy);
+    add_populations15<real>(g, raw_of_central_increment<real>(d, ux, uy, uz));
 }
 
-// Thermal D3Q7 collision (Appendix C) with R = 0.
+// Thermal D3Q7 collision (Appendix C) with R = 0: moments 0; x, y, z; xx-yy,
+// xx+yy-2zz, xx+yy+zz (equilibrium 3 c_sphi^2 phi).
 template <typename real>
 __device__ __forceinline__ void collide_thermal7(real (&g)[7], real ux, real uy, real uz,
                                                  const DevParams<real>& p) {
-    const real phi = moment<M0>(g);
-    const real kx = moment<MX>(g), ky = moment<MY>(g), kz = moment<MZ>(g);
-    const real kxx = moment<MXX>(g), kyy = moment<MYY>(g), kzz = moment<MZZ>(g);
-    const real uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+    const real px = g[1] + g[2], qx = g[1] - g[2];
+    const real py = g[3] + g[4], qy = g[3] - g[4];
+    const real pz = g[5] + g[6], qz = g[5] - g[6];
+    const real phi = g[0] + px + py + pz;
+    // central moments about u
+    const real kx = qx - ux * phi, ky = qy - uy * phi, kz = qz - uz * phi;
+    const real kxx = px - real(2) * ux * qx + ux * ux * phi;
+    const real kyy = py - real(2) * uy * qy + uy * uy * phi;
+    const real kzz = pz - real(2) * uz * qz + uz * uz * phi;
     const real* om = p.om_g;
-    real h[7];
-    h[0] = real(0);
-    h[1] = om[1] * real(0.5) * (phi * ux - kx);
-    h[2] = om[2] * real(0.5) * (phi * uy - ky);
-    h[3] = om[3] * real(0.5) * (phi * uz - kz);
-    h[4] = om[4] * real(0.25) *
-               (-(kxx - kyy) + real(2) * (ux * kx - uy * ky) - phi * (uxx - uyy)) +
-           ux * h[1] - uy * h[2];
-    h[5] = om[5] * real(1.0 / 12.0) *
-               (-(kxx + kyy - real(2) * kzz) + real(2) * (ux * kx + uy * ky - real(2) * uz * kz) -
-                phi * (uxx + uyy - real(2) * uzz)) +
-           real(1.0 / 3.0) * (ux * h[1] + uy * h[2] - real(2) * uz * h[3]);
-    h[6] = om[6] * real(1.0 / 6.0) *
-               (real(3) * p.cs2_phi * phi - (kxx + kyy + kzz) +
-                real(2) * (ux * kx + uy * ky + uz * kz) - phi * (uxx + uyy + uzz)) +
-           real(2.0 / 3.0) * (ux * h[1] + uy * h[2] + uz * h[3]);
-#pragma unroll
-    for (int a = 0; a < 7; ++a) {
-        real acc = real(0);
-#pragma unroll
-        for (int b = 1; b < 7; ++b) {
-            if (k7(b, a) != 0) acc += real(k7(b, a)) * h[b];
-        }
-        g[a] += acc;
-    }
+    const real dx = -om[1] * kx, dy = -om[2] * ky, dz = -om[3] * kz;
+    const real d1 = -om[4] * (kxx - kyy);
+    const real d2 = -om[5] * (kxx + kyy - real(2) * kzz);
+    const real dtr = om[6] * (real(3) * p.cs2_phi * phi - (kxx + kyy + kzz));
+    real dxx, dyy, dzz;
+    split_second_order(d1, d2, dtr, dxx, dyy, dzz);
+    // raw increments and populations: p_{+-} = (r_xx +- r_x)/2, p_0 = -(r_xx + r_yy + r_zz)
+    const real rxx = dxx + real(2) * ux * dx, ryy = dyy + real(2) * uy * dy;
+    const real rzz = dzz + real(2) * uz * dz;
+    g[1] += real(0.5) * (rxx + dx);
+    g[2] += real(0.5) * (rxx - dx);
+    g[3] += real(0.5) * (ryy + dy);
+    g[4] += real(0.5) * (ryy - dy);
+    g[5] += real(0.5) * (rzz + dz);
+    g[6] += real(0.5) * (rzz - dz);
+    g[0] -= rxx + ryy + rzz;
 }
 
 }  // namespace lbm

@@ -101,14 +101,92 @@ __global__ void __launch_bounds__(256) step_kernel(const real* __restrict__ Fin,
     for (int a = 0; a < Q; ++a) Gout[a * p.plane + c] = g[a];
 }
 
+// ---------------------------------------------------------------------------------
+// Cavity kernel: one block per x-row segment (blockIdx.y = j, blockIdx.z = k), so the
+// y/z wall tests are block-uniform.  Rows away from the y and z walls (all but ~4/n of
+// them) take the interior body, where the only missing links are those through the x
+// faces: one select of the load address per link, plus the anti-bounce-back transform
+// of the thermal value.  Loads use one base pointer and per-link offsets that are the
+// same for every thread.  Rows touching a y or z wall run the generic pull.
+// ---------------------------------------------------------------------------------
+template <typename real, int Q, bool INTERIOR>
+__device__ __forceinline__ void cavity_node(const real* __restrict__ Fin,
+                                            const real* __restrict__ Gin,
+                                            real* __restrict__ Fout, real* __restrict__ Gout,
+                                            const DevParams<real>& p, int i, int j, int k) {
+    const int nx = p.nx;
+    const int64_t nxy = (int64_t)nx * p.ny;
+    const int64_t c = k * nxy + (int64_t)j * nx + i;
+    const int64_t P = p.plane;
+    real f[15], g[Q];
+    if constexpr (INTERIOR) {
+        const bool lo = i == 0, hi = i == nx - 1;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int64_t shift = ex(a) + ey(a) * (int64_t)nx + ez(a) * nxy;
+            const bool out = (ex(a) > 0 && lo) || (ex(a) < 0 && hi);
+            const int64_t off = out ? (int64_t)opp(a) * P : (int64_t)a * P - shift;
+            const real v = Gin[c + off];
+            // Dirichlet face: anti-bounce-back with the face temperature
+            const real Tw = ex(a) > 0 ? p.T_cold : p.T_hot;
+            g[a] = out ? (real(2) * p.wg[a] * Tw - v) : v;
+        }
+#pragma unroll
+        for (int a = 0; a < 15; ++a) {
+            const int64_t shift = ex(a) + ey(a) * (int64_t)nx + ez(a) * nxy;
+            const bool out = (ex(a) > 0 && lo) || (ex(a) < 0 && hi);
+            const int64_t off = out ? (int64_t)opp(a) * P : (int64_t)a * P - shift;
+            f[a] = Fin[c + off];
+        }
+    } else {
+        pull<real, Q>(Fin, Gin, p, i, j, k, c, f, g);
+    }
+
+    real T = real(0);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) T += g[a];
+    const real Fz = p.ext_fz + p.gbeta * (T - p.T0);
+    real ux, uy, uz;
+    collide_flow<real>(f, p.ext_fx, p.ext_fy, Fz, p, ux, uy, uz);
+#pragma unroll
+    for (int a = 0; a < 15; ++a) Fout[a * P + c] = f[a];
+    if constexpr (Q == 15) collide_thermal15<real>(g, ux, uy, uz, p);
+    else collide_thermal7<real>(g, ux, uy, uz, p);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) Gout[a * P + c] = g[a];
+}
+
+template <typename real, int Q>
+__global__ void __launch_bounds__(128) step_cavity_kernel(const real* __restrict__ Fin,
+                                                          const real* __restrict__ Gin,
+                                                          real* __restrict__ Fout,
+                                                          real* __restrict__ Gout,
+                                                          DevParams<real> p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    if (i >= p.nx) return;
+    const bool interior = j >= 1 && j + 1 < p.ny && k >= 1 && k + 1 < p.nz;
+    if (interior) cavity_node<real, Q, true>(Fin, Gin, Fout, Gout, p, i, j, k);
+    else cavity_node<real, Q, false>(Fin, Gin, Fout, Gout, p, i, j, k);
+}
+
 template <typename real>
 cudaError_t launch_step(const DevState& s, int cur, const DevParams<real>& p, cudaStream_t st) {
-    const int threads = 256;
-    const int64_t blocks = (p.ncell + threads - 1) / threads;
     const real* Fin = static_cast<const real*>(s.F[cur]);
     const real* Gin = static_cast<const real*>(s.G[cur]);
     real* Fout = static_cast<real*>(s.F[cur ^ 1]);
     real* Gout = static_cast<real*>(s.G[cur ^ 1]);
+    if (p.boundary == 0 && p.ny <= 65535 && p.nz <= 65535) {
+        const int bx = 128;
+        const dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
+        if (s.Q == 15)
+            step_cavity_kernel<real, 15><<<grid, bx, 0, st>>>(Fin, Gin, Fout, Gout, p);
+        else
+            step_cavity_kernel<real, 7><<<grid, bx, 0, st>>>(Fin, Gin, Fout, Gout, p);
+        return cudaGetLastError();
+    }
+    const int threads = 256;
+    const int64_t blocks = (p.ncell + threads - 1) / threads;
     if (s.Q == 15)
         step_kernel<real, 15><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Fout, Gout, p);
     else

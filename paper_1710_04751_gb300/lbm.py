@@ -151,12 +151,13 @@ class LBM:
     """A cavity (or test box) advanced by the CUDA library on one GPU.
 
     grid: (nx, ny, nz).  Either (Ra, Pr, Ma) or an explicit `params` (Params or dict of
-    Params fields) must be given.  The state arena is a torch CUDA tensor and the work
+    Params fields) must be given.  cs2_phi = 0 selects the lattice default (1/3 for
+    D3Q15, 1/4 for D3Q7).  The state arena is a torch CUDA tensor and the work
     runs on torch's current stream unless `stream` is given.
     """
 
     def __init__(self, grid, lattice=D3Q15, Ra=None, Pr=0.71, Ma=0.05 * math.sqrt(3.0),
-                 params=None, precision=FP32, seed=1, noise_amp=1e-6, cs2_phi=1.0 / 3.0,
+                 params=None, precision=FP32, seed=1, noise_amp=1e-6, cs2_phi=0.0,
                  e4_mode=0, adiabatic_mode=ADIABATIC_SPECULAR, residual_interval=100,
                  stream=None, device=None, timeout_s=600.0, torch_arena=True):
         import torch

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from tests import inputs
-from tests.test_gpu_parity import FP32_REL
+from tests.test_gpu_parity import FP32_REL, thermal_floor
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +35,7 @@ def test_sampled_nodes_at_128(q):
     sim.step(1)
     f1, g1 = sim.get_populations()
     wf = oracle.weights_flow()
-    wg = oracle.weights_thermal(q) * (p.T_hot - p.T_cold)
+    wg = thermal_floor(q, p.cs2_phi, p.T_hot - p.T_cold)
     worst = 0.0
     for (i, j, k) in sample_nodes(N, 7 + q):
         fr, gr = p.cell_update(f0, g0, i, j, k)

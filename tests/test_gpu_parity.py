@@ -2,7 +2,8 @@
 
 Tolerances: FP64 max-abs 1e-12 on every population; FP32 |d| <= 1e-5 max(|p_oracle|, w_a)
 for f and 1e-5 max(|p_oracle|, w^phi_a dT) for g, the normalisation that keeps the
-relative bound meaningful for populations near zero.
+relative bound meaningful for populations near zero (a zero rest weight takes the
+smallest non-zero weight).
 """
 import math
 
@@ -43,9 +44,16 @@ def random_state(p, seed):
     return F, G
 
 
+def thermal_floor(q, cs2_phi, dT):
+    """w^phi_a dT, with the smallest non-zero weight standing in for a zero rest weight
+    (D3Q7 at c_sphi^2 = 1/3 has w^phi_0 = 0)."""
+    w = oracle.weights_thermal(q, cs2_phi)
+    return np.where(w > 0, w, w[w > 0].min()) * abs(dT)
+
+
 def fp32_bound(p, ref_f, ref_g):
     wf = oracle.weights_flow()[:, None, None, None]
-    wg = oracle.weights_thermal(p.q_g, p.cs2_phi)[:, None, None, None] * abs(p.T_hot - p.T_cold)
+    wg = thermal_floor(p.q_g, p.cs2_phi, p.T_hot - p.T_cold)[:, None, None, None]
     return (FP32_REL * np.maximum(np.abs(ref_f), wf), FP32_REL * np.maximum(np.abs(ref_g), wg))
 
 
