@@ -223,6 +223,30 @@ def e2e_variant(lbm, q, reps, device):
                      "bytes amortised per time step")
 
 
+def time_to_steady(lbm, q, max_steps, threshold=1e-7, chunk=5000):
+    """Plain FP32 method from the initial state until max |dT| over 100 steps falls
+    below `threshold` (config: 128^3, Ra = 1e5): steps, wall seconds and final Nu."""
+    import torch
+    sim = lbm.LBM((N_GRID,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=lbm.FP32,
+                  residual_interval=RESIDUAL_INTERVAL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = -1.0
+    while sim.steps_done < max_steps:
+        sim.step(chunk)
+        res = sim.residual()
+        if 0 <= res < threshold:
+            break
+    dt = time.perf_counter() - t0
+    nu = sim.nusselt()
+    sim.close()
+    return {"converged": bool(0 <= res < threshold), "steps": sim.steps_done,
+            "seconds": round(dt, 2), "residual_per_100": res, "threshold": threshold,
+            "Nu_mean_mid": nu["mid_mean"], "Nu_hot": nu["hot_wall_mean"],
+            "Nu_max": nu["mid_max"], "Nu_min": nu["mid_min"], "u_max": nu["umax"],
+            "w_max": nu["wmax"]}
+
+
 def cpu_baseline(sample_steps=3, q=15):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of the same
     workload (the 128^3 Ra = 1e5 cavity, a few steps from its initial state)."""
@@ -297,6 +321,11 @@ def gpu_arm(args):
         "state_after": {"steps": args.warmup + args.steps, "Nu_hot": main["nu"]["hot_wall_mean"],
                         "residual_per_100": main["residual"]},
     }
+    if args.steady:
+        line["time_to_steady"] = {
+            "D3Q15+D3Q15": time_to_steady(lbm, 15, args.steady_max_steps),
+            "D3Q15+D3Q7": time_to_steady(lbm, 7, args.steady_max_steps),
+        }
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e_variant(lbm, 15, args.e2e_reps, device)
     if rank == 0 and not args.no_cpu_baseline:
@@ -365,6 +394,9 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-reps", type=int, default=20)
+    ap.add_argument("--steady", action="store_true",
+                    help="also run both variants from rest to steady state and report the time")
+    ap.add_argument("--steady-max-steps", type=int, default=3_000_000)
     ap.add_argument("--ref-budget", type=float, default=90.0,
                     help="seconds the reference arm spends on warm-up + timed steps")
     ap.add_argument("--traffic-q15", type=float, default=None,
