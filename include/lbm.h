@@ -70,7 +70,7 @@ typedef struct {
  * nu = sqrt(Pr/Ra) U0 L, alpha = nu/Pr, nu = (1/3)(1/omega - 1/2) (Appendix A) and
  * alpha = cs2_phi (1/omega - 1/2) (Eq. 23). */
 typedef struct {
-    double omega_f[15];   /* flow rates omega_0..omega_14 (0..3 unused); paper: 4..9 = omega_nu, rest 1 */
+    double omega_f[15];   /* flow rates omega_0..omega_14 (0..3 unused); paper: 4..8 = omega_nu (shear), rest 1 */
     double omega_g[15];   /* thermal rates omega_0..omega_{Q-1} (0 unused); paper: 1..3 = omega_phi, rest 1 */
     double gbeta;         /* g beta of the Boussinesq force F_z = g beta (T - T0) */
     double T_hot, T_cold; /* Dirichlet face temperatures; T0 = (T_hot + T_cold)/2 */

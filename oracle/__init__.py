@@ -170,8 +170,8 @@ def physical_parameters(L, Ra, Pr, Ma, cs2_phi=1.0 / 3.0, dT=1.0):
 
 class Problem:
     """A grid problem for the oracle.  Relaxation rates default to the paper's choice:
-    flow omega_4..9 = omega_nu, the rest 1 (App. A); thermal omega_1..3 = omega_phi,
-    the rest 1 (Sec. 2.2 / App. C)."""
+    flow omega_4..8 = omega_nu (shear), the rest 1 (App. A); thermal omega_1..3 =
+    omega_phi, the rest 1 (Sec. 2.2 / App. C)."""
 
     def __init__(self, nx, ny, nz, q_g=15, boundary=BC_CAVITY, omega_nu=1.0, omega_phi=1.0,
                  gbeta=0.0, T_hot=0.5, T_cold=-0.5, cs2_phi=1.0 / 3.0, e4_mode=0,
@@ -181,8 +181,10 @@ class Problem:
         self.boundary, self.e4_mode = int(boundary), int(e4_mode)
         self.adiabatic_mode = int(adiabatic_mode)
         if omega_f is None:
+            # App. A: "nu = cs^2 (1/omega_j - 1/2), j = 5..9", counted from 1: the five
+            # shear moments g^_4..g^_8; the bulk moment g^_9 and the rest relax at 1
             omega_f = [1.0] * 15
-            for b in range(4, 10):
+            for b in range(4, 9):
                 omega_f[b] = omega_nu
         if omega_g is None:
             omega_g = [1.0] * 15

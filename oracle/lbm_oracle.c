@@ -18,7 +18,7 @@
  *   R1  4th-order flow equilibrium E = kxx~ * kyy~ / rho (mode 0) or rho*cs^4 (mode 1)
  *   R2  flow source S: central moments of the Maxwellian forcing term, 1st order F,
  *       3rd order cs^2 F, all others zero, mapped to populations through K^-1
- *   R3  flow omega_4..omega_9 set the viscosity, omega_10..omega_14 = 1
+ *   R3  flow omega_4..omega_8 (shear) set the viscosity, omega_9..omega_14 = 1
  *   R4  thermal omega_1..omega_3 set the diffusivity, the rest = 1
  *   R5  no-slip: half-way bounce-back
  *   R6  Dirichlet T: anti-bounce-back g = -g~_opp + 2 w_a T_w
@@ -28,6 +28,11 @@
  *   R9  stored arrays are post-collision; a step is pull, then collide
  *   R11 Nu from the one-sided stencil (9 T1 - T2 - 8 Tw)/3 at half-way walls
  *   R12 peak velocities on the centrelines of the symmetry plane
+ *
+ * Parity unpinned: the third-order source moments of R2 and the equilibrium E of R1 are
+ * readings the paper does not fix.  Form B (oracle/formb.py) restates the same readings,
+ * so the tests check their transcription, not the readings themselves; Table 1 at
+ * Ra = 1e3 bounds their combined effect only loosely.
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (oracle/build.py).
  * OpenMP only splits the loop over z-planes; each cell's arithmetic is unchanged.

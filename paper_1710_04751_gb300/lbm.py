@@ -24,7 +24,7 @@ EXPORTS = (
     "lbm_default_options", "lbm_derive_params", "lbm_arena_bytes", "lbm_create",
     "lbm_create_params", "lbm_step", "lbm_fields", "lbm_nusselt", "lbm_residual",
     "lbm_get_populations", "lbm_set_populations", "lbm_get_params", "lbm_steps_done",
-    "lbm_last_error", "lbm_synchronize", "lbm_destroy",
+    "lbm_last_error", "lbm_synchronize", "lbm_destroy"
 )
 
 
@@ -256,9 +256,12 @@ class LBM:
         self._check(self._L.lbm_set_populations(self._ctx, _dp(f), _dp(g)))
 
     def params(self):
+        return self.params_struct().as_dict()
+
+    def params_struct(self):
         p = Params()
         self._check(self._L.lbm_get_params(self._ctx, ctypes.byref(p)))
-        return p.as_dict()
+        return p
 
     @property
     def steps_done(self):

@@ -45,7 +45,8 @@ def test_derive_params_matches_oracle(n, Ra):
     assert p.omega_g[1] == pytest.approx(ref["omega_phi"], rel=1e-14)
     assert p.gbeta == pytest.approx(ref["gbeta"], rel=1e-14)
     assert p.U0 == pytest.approx(0.05, rel=1e-14)
-    assert [p.omega_f[b] for b in range(10, 15)] == [1.0] * 5
+    assert [p.omega_f[b] for b in range(4, 9)] == [p.omega_f[4]] * 5
+    assert [p.omega_f[b] for b in range(9, 15)] == [1.0] * 6
     assert [p.omega_g[b] for b in range(4, 15)] == [1.0] * 11
     assert p.T_hot == 0.5 and p.T_cold == -0.5 and p.boundary == lbm.BC_CAVITY
 
@@ -93,3 +94,4 @@ def test_arena_bytes():
     assert 2 * 30 * 4 * n + 12 * n <= b <= 2 * 30 * 4 * n + 12 * n + 64 * 1024
     assert lbm.arena_bytes((128, 128, 128), 7, lbm.FP64) > lbm.arena_bytes((128, 128, 128), 7, lbm.FP32)
     assert lbm.arena_bytes((0, 1, 1), 15, lbm.FP32) == 0
+
