@@ -163,6 +163,32 @@ const char* lbm_last_error(const lbm_ctx* ctx);
 int lbm_synchronize(lbm_ctx* ctx);
 void lbm_destroy(lbm_ctx* ctx);
 
+/* Allocation-free Nusselt reduction.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- code whose device memory is owned
+ * and pre-reserved by an enclosing application or framework, real-time loops that must
+ * not allocate (or risk an allocation failure) once running, plug-ins forbidden to
+ * allocate after start-up.  It computes exactly what lbm_nusselt computes, for
+ * populations the caller holds in its own device buffers, and allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.
+ *   f_dev, g_dev  device pointers to the 15 flow and `lattice` thermal population planes,
+ *                 layout of the host arrays above but with `plane` elements between
+ *                 consecutive planes (plane >= nx*ny*nz); FP32 or FP64 per `precision`.
+ *   params        as for lbm_create_params (T_hot, T_cold, gbeta, ext_force, U0 are used).
+ *   cuda_stream   cudaStream_t to run on (NULL = legacy default stream); the call waits
+ *                 for that stream (bounded, 600 s) before writing *out.
+ * Its scratch is a static device array of 2*1024 + 16 doubles (16.5 KB) that every GPU
+ * loading the library holds until the process exits; it bounds the face count:
+ * ny*nz <= 262144 (1024 blocks of 256 face cells), larger grids give LBM_EINVAL.  The
+ * first call on each device, with that device current, looks up the array's device
+ * address (a one-time set-up); make that first call before any stream capture.  Every
+ * call overwrites the array's partial sums before reading them, so nothing carries over
+ * from the previous call; calls that overlap on the GPU (other streams, other threads)
+ * share the array and race.  Errors: LBM_EINVAL (NULL pointer, sizes, lattice,
+ * precision, plane), LBM_ECUDA, LBM_ETIMEOUT; message in lbm_last_error(NULL). */
+int lbm_nusselt_noalloc(const void* f_dev, const void* g_dev, int64_t plane, int precision,
+                        const lbm_grid* grid, int lattice, const lbm_params* params,
+                        void* cuda_stream, lbm_nu* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,5 +5,5 @@ Python binding."""
 from .lbm import (  # noqa: F401
     ADIABATIC_BOUNCE_BACK, ADIABATIC_SPECULAR, BC_ADIABATIC_BOX, BC_CAVITY, BC_PERIODIC,
     BC_XWALLS, D3Q7, D3Q15, EXPORTS, FP32, FP64, LBM, LBMError, arena_bytes, default_options,
-    derive_params, library_path, load,
+    derive_params, library_path, load, nusselt_noalloc,
 )

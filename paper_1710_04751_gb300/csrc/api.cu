@@ -37,6 +37,8 @@ struct lbm_ctx {
 
 static thread_local std::string g_err;
 
+void lbm::set_last_error(const char* msg) { g_err = msg; }
+
 static int fail(lbm_ctx* ctx, int code, const char* fmt, const char* detail = nullptr) {
     char buf[512];
     snprintf(buf, sizeof buf, fmt, detail ? detail : "");

@@ -380,6 +380,20 @@ cudaError_t launch_nusselt(const DevState& s, int cur, const DevParams<real>& p,
     return cudaGetLastError();
 }
 
+template <typename real>
+cudaError_t launch_nusselt_into(const real* F, const real* G, const DevParams<real>& p, double U0,
+                                int Q, int blocks, double* partials, double* result,
+                                cudaStream_t st) {
+    if (Q == 15) {
+        nusselt_faces_kernel<real, 15><<<blocks, 256, 0, st>>>(G, p, partials);
+        nusselt_lines_kernel<real, 15><<<1, 256, 0, st>>>(F, G, p, blocks, U0, partials, result);
+    } else {
+        nusselt_faces_kernel<real, 7><<<blocks, 256, 0, st>>>(G, p, partials);
+        nusselt_lines_kernel<real, 7><<<1, 256, 0, st>>>(F, G, p, blocks, U0, partials, result);
+    }
+    return cudaGetLastError();
+}
+
 #define LBM_INSTANTIATE(real)                                                                       \
     template cudaError_t launch_init<real>(const DevState&, const DevParams<real>&, uint64_t, double, \
                                            cudaStream_t);                                           \
@@ -390,7 +404,9 @@ cudaError_t launch_nusselt(const DevState& s, int cur, const DevParams<real>& p,
     template cudaError_t launch_residual<real>(const DevState&, int, const DevParams<real>&, int,     \
                                                cudaStream_t);                                       \
     template cudaError_t launch_nusselt<real>(const DevState&, int, const DevParams<real>&, double,   \
-                                              cudaStream_t);
+                                              cudaStream_t);                                        \
+    template cudaError_t launch_nusselt_into<real>(const real*, const real*, const DevParams<real>&,  \
+                                                   double, int, int, double*, double*, cudaStream_t);
 LBM_INSTANTIATE(float)
 LBM_INSTANTIATE(double)
 

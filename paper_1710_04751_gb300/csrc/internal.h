@@ -57,4 +57,14 @@ template <typename real>
 cudaError_t launch_nusselt(const DevState& s, int cur, const DevParams<real>& p, double U0,
                            cudaStream_t st);
 
+// Nusselt reduction into caller-provided device scratch: one face block per 256 face
+// cells (`blocks` of them, partial pairs at partials[0 .. 2*blocks)), result[0..11).
+template <typename real>
+cudaError_t launch_nusselt_into(const real* F, const real* G, const DevParams<real>& p, double U0,
+                                int Q, int blocks, double* partials, double* result,
+                                cudaStream_t st);
+
+// Message returned by lbm_last_error(NULL) on this thread.
+void set_last_error(const char* msg);
+
 }  // namespace lbm

@@ -24,7 +24,7 @@ EXPORTS = (
     "lbm_default_options", "lbm_derive_params", "lbm_arena_bytes", "lbm_create",
     "lbm_create_params", "lbm_step", "lbm_fields", "lbm_nusselt", "lbm_residual",
     "lbm_get_populations", "lbm_set_populations", "lbm_get_params", "lbm_steps_done",
-    "lbm_last_error", "lbm_synchronize", "lbm_destroy"
+    "lbm_last_error", "lbm_synchronize", "lbm_destroy", "lbm_nusselt_noalloc",
 )
 
 
@@ -114,6 +114,9 @@ def load(build_if_missing=True):
     L.lbm_synchronize.argtypes = [ctypes.c_void_p]
     L.lbm_destroy.argtypes = [ctypes.c_void_p]
     L.lbm_destroy.restype = None
+    L.lbm_nusselt_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                      ctypes.c_int, P(Grid), ctypes.c_int, P(Params),
+                                      ctypes.c_void_p, P(Nu)]
     _lib = L
     return L
 
@@ -145,6 +148,21 @@ def arena_bytes(grid, lattice, precision):
 
 def _dp(a):
     return a.ctypes.data_as(_D)
+
+
+def nusselt_noalloc(f_dev, g_dev, plane, precision, grid, lattice, params, stream=None):
+    """lbm_nusselt for populations held in caller-owned device buffers (integer device
+    addresses), without any allocation by the library.  params: a Params structure
+    (e.g. from LBM.params_struct()).  stream: a cudaStream_t as an integer, or None."""
+    L = load()
+    nu = Nu()
+    rc = L.lbm_nusselt_noalloc(ctypes.c_void_p(int(f_dev)), ctypes.c_void_p(int(g_dev)),
+                               int(plane), int(precision), ctypes.byref(Grid(*grid)),
+                               int(lattice), ctypes.byref(params),
+                               ctypes.c_void_p(int(stream) if stream else None), ctypes.byref(nu))
+    if rc != LBM_OK:
+        raise LBMError(rc, L.lbm_last_error(None).decode())
+    return nu.as_dict()
 
 
 class LBM:

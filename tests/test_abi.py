@@ -95,3 +95,21 @@ def test_arena_bytes():
     assert lbm.arena_bytes((128, 128, 128), 7, lbm.FP64) > lbm.arena_bytes((128, 128, 128), 7, lbm.FP32)
     assert lbm.arena_bytes((0, 1, 1), 15, lbm.FP32) == 0
 
+
+def test_noalloc_nusselt_rejects_before_touching_the_device():
+    L = binding.load()
+    p = lbm.derive_params((8, 8, 8), 15, 1e3, 0.71, 0.0866)
+    nu = binding.Nu()
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: validation comes first
+    big = binding.Grid(4, 600, 600)  # ny * nz = 360000 > 262144 face cells of static scratch
+    rc = L.lbm_nusselt_noalloc(fake, fake, 4 * 600 * 600, binding.FP32, ctypes.byref(big), 15,
+                               ctypes.byref(p), None, ctypes.byref(nu))
+    assert rc == binding.LBM_EINVAL
+    assert b"262144" in L.lbm_last_error(None)
+    small = binding.Grid(8, 8, 8)
+    rc = L.lbm_nusselt_noalloc(fake, fake, 100, binding.FP32, ctypes.byref(small), 15,
+                               ctypes.byref(p), None, ctypes.byref(nu))  # plane < nx*ny*nz
+    assert rc == binding.LBM_EINVAL
+    rc = L.lbm_nusselt_noalloc(None, fake, 512, binding.FP32, ctypes.byref(small), 15,
+                               ctypes.byref(p), None, ctypes.byref(nu))
+    assert rc == binding.LBM_EINVAL
