@@ -29,7 +29,11 @@ METRIC = "coupled MLUPS & % HBM roofline; time-to-steady Nu at Ra=1e5 vs plain F
 N_GRID, RA, PR, U0 = 128, 1e5, 0.71, 0.05
 RESIDUAL_INTERVAL = 100
 # algorithmic bytes per node update: every population read once and written once
-BYTES_PER_NODE = {15: 2 * 30 * 4, 7: 2 * 22 * 4}
+def bytes_per_node(q, storage_bytes=4):
+    return 2 * (15 + q) * storage_bytes
+
+
+BYTES_PER_NODE = {15: bytes_per_node(15), 7: bytes_per_node(7)}
 
 
 # ----------------------------------------------------------------------------------
@@ -158,11 +162,12 @@ def time_steps(sim, steps, stream):
     return start.elapsed_time(end) / 1e3
 
 
-def run_variant(lbm, q, steps, warmup, dist, device, clocks=None):
+def run_variant(lbm, q, steps, warmup, dist, device, clocks=None, precision=None):
     import torch
     n3 = N_GRID ** 3
+    precision = lbm.FP32 if precision is None else precision
     stream = torch.cuda.current_stream(device)
-    sim = lbm.LBM((N_GRID,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=lbm.FP32,
+    sim = lbm.LBM((N_GRID,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=precision,
                   residual_interval=RESIDUAL_INTERVAL)
     sim.step(warmup)
     torch.cuda.synchronize()
@@ -178,7 +183,7 @@ def run_variant(lbm, q, steps, warmup, dist, device, clocks=None):
     residual = sim.residual()
 
     # the step kernel alone (no residual launches) for the roofline
-    kern = lbm.LBM((N_GRID,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=lbm.FP32,
+    kern = lbm.LBM((N_GRID,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=precision,
                    residual_interval=0)
     kern.step(max(10, warmup // 4))
     ksteps = max(50, min(steps, 2000))
@@ -223,9 +228,11 @@ def e2e_variant(lbm, q, reps, device):
                      "bytes amortised per time step")
 
 
-def time_to_steady(lbm, q, max_steps, threshold=1e-7, chunk=5000):
+def time_to_steady(lbm, q, max_steps, threshold=1e-6, chunk=1000):
     """Plain FP32 method from the initial state until max |dT| over 100 steps falls
-    below `threshold` (config: 128^3, Ra = 1e5): steps, wall seconds and final Nu."""
+    below `threshold` (128^3, Ra = 1e5): steps, wall seconds and the steady Nu.  In FP32
+    the rounding noise of max |dT| over 100 steps on 2M nodes is about 3e-7, so the
+    threshold is 1e-6 (1e-7 is only reachable in FP64)."""
     import torch
     sim = lbm.LBM((N_GRID,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=lbm.FP32,
                   residual_interval=RESIDUAL_INTERVAL)
@@ -239,8 +246,9 @@ def time_to_steady(lbm, q, max_steps, threshold=1e-7, chunk=5000):
             break
     dt = time.perf_counter() - t0
     nu = sim.nusselt()
+    steps = sim.steps_done
     sim.close()
-    return {"converged": bool(0 <= res < threshold), "steps": sim.steps_done,
+    return {"converged": bool(0 <= res < threshold), "steps": steps,
             "seconds": round(dt, 2), "residual_per_100": res, "threshold": threshold,
             "Nu_mean_mid": nu["mid_mean"], "Nu_hot": nu["hot_wall_mean"],
             "Nu_max": nu["mid_max"], "Nu_min": nu["mid_min"], "u_max": nu["umax"],
@@ -277,14 +285,20 @@ def gpu_arm(args):
     clocks = ClockSampler(local)
     main = run_variant(lbm, 15, args.steps, args.warmup, dist, device, clocks)
     variant = run_variant(lbm, 7, args.steps, args.warmup, dist, device, None)
+    half_steps = max(1, args.steps // 4)
+    sixteen = {}
+    for name, prec, tname in (("FP16_DEV", lbm.FP16_DEV, "__half"), ("BF16_DEV", lbm.BF16_DEV, "__nv_bfloat16")):
+        for q in (15, 7):
+            sixteen[(name, q)] = (tname, run_variant(lbm, q, half_steps, args.warmup, dist, device,
+                                                     None, precision=prec))
 
-    def roof(res, q):
-        achieved = BYTES_PER_NODE[q] * N_GRID ** 3 / res["t_kernel"] / 1e9
+    def roof(res, q, storage_bytes=4, tname="float", traffic=None):
+        bpn = bytes_per_node(q, storage_bytes)
+        achieved = bpn * N_GRID ** 3 / res["t_kernel"] / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": args.traffic.get(q),
-                "peak_kind": peak_kind, "kernel": f"step_kernel<float,{q}>",
-                "bytes_per_node": BYTES_PER_NODE[q],
-                "kernel_ms": round(res["t_kernel"] * 1e3, 4)}
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_kind": peak_kind, "kernel": f"step_cavity_kernel<{tname},{q}>",
+                "bytes_per_node": bpn, "kernel_ms": round(res["t_kernel"] * 1e3, 4)}
 
     total_lups = sum_over_ranks(dist, N_GRID ** 3 * args.steps, device)
     value = total_lups / main["elapsed"] / 1e6
@@ -309,19 +323,26 @@ def gpu_arm(args):
             "l2": "inputs larger than L2: A/B state 503 MB > 129 MB",
             "parallelism": f"replicas{world}" if world > 1 else "single",
         },
-        "roofline": roof(main, 15),
+        "roofline": roof(main, 15, traffic=args.traffic.get(15)),
         "clocks": main["clocks"],
         "gpu_launches": main["launches"],
         "variants": {
             "D3Q15+D3Q7": {"value": round(sum_over_ranks(dist, N_GRID ** 3 * args.steps, device)
                                           / variant["elapsed"] / 1e6, 1),
                            "unit": "MLUPS", "ms_per_step": round(variant["elapsed"] / args.steps * 1e3, 5),
-                           "roofline": roof(variant, 7)},
+                           "roofline": roof(variant, 7, traffic=args.traffic.get(7))},
+            **{f"D3Q15+D3Q{q} {name}": {
+                "value": round(sum_over_ranks(dist, N_GRID ** 3 * half_steps, device)
+                               / res["elapsed"] / 1e6, 1),
+                "unit": "MLUPS", "steps": half_steps,
+                "ms_per_step": round(res["elapsed"] / half_steps * 1e3, 5),
+                "roofline": roof(res, q, 2, tname)}
+               for (name, q), (tname, res) in sixteen.items()},
         },
         "state_after": {"steps": args.warmup + args.steps, "Nu_hot": main["nu"]["hot_wall_mean"],
                         "residual_per_100": main["residual"]},
     }
-    if args.steady:
+    if not args.no_steady:
         line["time_to_steady"] = {
             "D3Q15+D3Q15": time_to_steady(lbm, 15, args.steady_max_steps),
             "D3Q15+D3Q7": time_to_steady(lbm, 7, args.steady_max_steps),
@@ -394,9 +415,9 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-reps", type=int, default=20)
-    ap.add_argument("--steady", action="store_true",
-                    help="also run both variants from rest to steady state and report the time")
-    ap.add_argument("--steady-max-steps", type=int, default=3_000_000)
+    ap.add_argument("--no-steady", action="store_true",
+                    help="skip the run of both variants from rest to steady state")
+    ap.add_argument("--steady-max-steps", type=int, default=400_000)
     ap.add_argument("--ref-budget", type=float, default=90.0,
                     help="seconds the reference arm spends on warm-up + timed steps")
     ap.add_argument("--traffic-q15", type=float, default=None,

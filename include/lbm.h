@@ -44,7 +44,10 @@ extern "C" {
 #define LBM_ETIMEOUT (-5)  /* a bounded wait for the GPU ran out */
 
 enum { LBM_THERMAL_D3Q15 = 15, LBM_THERMAL_D3Q7 = 7 };
-enum { LBM_FP64 = 0, LBM_FP32 = 1 };
+/* Storage and arithmetic: FP64; FP32; or 16-bit storage of each population minus its
+ * rest-state value (w_a for the flow, w^phi_a T0 for the scalar) with FP32 arithmetic:
+ * FP16 (11 significant bits) or BF16 (8 significant bits, FP32 range). */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_DEV = 2, LBM_BF16_DEV = 3 };
 
 /* Boundary modes (bit mask).  Bits 0..2: x, y, z periodic.  Bit 3: the x walls are
  * adiabatic instead of Dirichlet.  LBM_BC_CAVITY is the paper's cubic cavity (Sec. 3):
@@ -83,7 +86,7 @@ typedef struct {
 } lbm_params;
 
 typedef struct {
-    int precision;            /* LBM_FP32 (default) or LBM_FP64 storage and arithmetic */
+    int precision;            /* LBM_FP32 (default), LBM_FP64, LBM_FP16_DEV or LBM_BF16_DEV */
     uint64_t seed;            /* noise seed of the initial temperature (default 1) */
     double noise_amp;         /* initial T = uniform noise in [-amp, amp] (default 1e-6) */
     double cs2_phi;           /* c_sphi^2; 0 (default) = 1/3 for D3Q15, 1/4 for D3Q7 (at 1/3 the

@@ -9,7 +9,7 @@
 #include <string>
 #include <thread>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 #include "internal.h"
 
 using namespace lbm;
@@ -142,15 +142,36 @@ struct Layout {
     size_t F[2], G[2], snap, staging, partials, result, bits, total;
 };
 
+// bytes of one stored population and of the arithmetic type, by precision
+static size_t storage_bytes(int precision) {
+    return precision == LBM_FP64 ? 8 : precision == LBM_FP32 ? 4 : 2;
+}
+static size_t compute_bytes(int precision) { return precision == LBM_FP64 ? 8 : 4; }
+
+static bool valid_precision(int p) {
+    return p == LBM_FP64 || p == LBM_FP32 || p == LBM_FP16_DEV || p == LBM_BF16_DEV;
+}
+
+// Run fn(S{}) with S the storage type of the precision.
+template <typename Fn>
+static int with_storage(int precision, Fn&& fn) {
+    switch (precision) {
+    case LBM_FP64: return fn(double{});
+    case LBM_FP32: return fn(float{});
+    case LBM_FP16_DEV: return fn(__half{});
+    default: return fn(__nv_bfloat16{});
+    }
+}
+
 static Layout layout_of(const lbm_grid* g, int q, int precision) {
     const int64_t ncell = (int64_t)g->nx * g->ny * g->nz;
     const int64_t plane = plane_of(ncell);
-    const size_t rs = precision == LBM_FP64 ? 8 : 4;
+    const size_t rs = storage_bytes(precision);
     Layout L;
     size_t off = 0;
     for (int b = 0; b < 2; ++b) { L.F[b] = off; off = align_up(off + 15 * plane * rs, 256); }
     for (int b = 0; b < 2; ++b) { L.G[b] = off; off = align_up(off + q * plane * rs, 256); }
-    L.snap = off; off = align_up(off + plane * rs, 256);
+    L.snap = off; off = align_up(off + plane * compute_bytes(precision), 256);
     L.staging = off; off = align_up(off + plane * 8, 256);
     L.partials = off; off = align_up(off + 2 * kPartialBlocks * 8, 256);
     L.result = off; off = align_up(off + kResultDoubles * 8, 256);
@@ -160,7 +181,7 @@ static Layout layout_of(const lbm_grid* g, int q, int precision) {
 }
 
 extern "C" size_t lbm_arena_bytes(const lbm_grid* grid, int lattice, int precision) {
-    if (!valid_grid(grid) || !valid_lattice(lattice)) return 0;
+    if (!valid_grid(grid) || !valid_lattice(lattice) || !valid_precision(precision)) return 0;
     return layout_of(grid, lattice, precision).total;
 }
 
@@ -184,7 +205,16 @@ static DevParams<real> dev_params(const lbm_ctx* c) {
         w1 = 0.5 * cs;
         w0 = 1.0 - 6.0 * w1;
     }
-    for (int a = 0; a < 15; ++a) p.wg[a] = (real)(a == 0 ? w0 : a < 7 ? w1 : w7);
+    const double T0 = 0.5 * (P.T_hot + P.T_cold);
+    const double cs2 = 1.0 / 3.0;
+    const double f7 = cs2 * cs2 / 8.0, f1 = 0.5 * (cs2 - cs2 * cs2), f0 = 1.0 - 6.0 * f1 - 8.0 * f7;
+    for (int a = 0; a < 15; ++a) {
+        const double wg = a == 0 ? w0 : a < 7 ? w1 : w7;
+        p.wg[a] = (real)wg;
+        // stored-value offsets (used by the 16-bit forms): rest-state populations
+        p.wf[a] = (real)(a == 0 ? f0 : a < 7 ? f1 : f7);
+        p.wt[a] = (real)(wg * T0);
+    }
     p.gbeta = (real)P.gbeta;
     p.T0 = (real)(0.5 * (P.T_hot + P.T_cold));
     p.T_hot = (real)P.T_hot;
@@ -245,11 +275,11 @@ static int check_params(const lbm_params* p, int q) {
     return 1;
 }
 
-template <typename real>
+template <typename S>
 static int run_init(lbm_ctx* c) {
-    DevParams<real> p = dev_params<real>(c);
-    CUDA_OR_FAIL(c, launch_init<real>(c->dev, p, c->opt.seed, c->opt.noise_amp, c->stream));
-    CUDA_OR_FAIL(c, launch_residual<real>(c->dev, 0, p, 0, c->stream));
+    const ParamsOf<S> p = dev_params<typename Storage<S>::real>(c);
+    CUDA_OR_FAIL(c, launch_init<S>(c->dev, p, c->opt.seed, c->opt.noise_amp, c->stream));
+    CUDA_OR_FAIL(c, launch_residual<S>(c->dev, 0, p, 0, c->stream));
     return LBM_OK;
 }
 
@@ -263,8 +293,8 @@ extern "C" int lbm_create_params(const lbm_grid* grid, int lattice, const lbm_pa
         return fail(nullptr, LBM_EINVAL, "invalid parameters (rates must lie in (0, 2))%s");
     lbm_options o;
     if (opt) o = *opt; else lbm_default_options(&o);
-    if (o.precision != LBM_FP32 && o.precision != LBM_FP64)
-        return fail(nullptr, LBM_EINVAL, "precision must be LBM_FP32 or LBM_FP64%s");
+    if (!valid_precision(o.precision))
+        return fail(nullptr, LBM_EINVAL, "precision must be one of LBM_FP64, LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV%s");
     if (o.residual_interval < 0 || !(o.timeout_s > 0))
         return fail(nullptr, LBM_EINVAL, "invalid residual_interval or timeout%s");
 
@@ -277,7 +307,7 @@ extern "C" int lbm_create_params(const lbm_grid* grid, int lattice, const lbm_pa
     c->opt = o;
     c->ncell = (int64_t)grid->nx * grid->ny * grid->nz;
     c->plane = plane_of(c->ncell);
-    c->rsize = o.precision == LBM_FP64 ? 8 : 4;
+    c->rsize = storage_bytes(o.precision);
     c->stream = (cudaStream_t)o.cuda_stream;
     c->cur = 0;
     c->steps = 0;
@@ -329,7 +359,8 @@ extern "C" int lbm_create_params(const lbm_grid* grid, int lattice, const lbm_pa
     rc = LBM_OK;
     if (cudaMemsetAsync(base + L.bits, 0, 256, c->stream) != cudaSuccess)
         rc = fail(c, LBM_ECUDA, "cudaMemsetAsync failed%s");
-    if (rc == LBM_OK) rc = o.precision == LBM_FP64 ? run_init<double>(c) : run_init<float>(c);
+    if (rc == LBM_OK)
+        rc = with_storage(o.precision, [&](auto tag) { return run_init<decltype(tag)>(c); });
     if (rc == LBM_OK) rc = wait_stream(c);
     if (rc != LBM_OK) {
         g_err = c->err;
@@ -351,17 +382,17 @@ extern "C" int lbm_create(const lbm_grid* grid, int lattice, double Ra, double P
     return lbm_create_params(grid, lattice, &p, opt, out);
 }
 
-template <typename real>
+template <typename S>
 static int run_steps(lbm_ctx* c, int64_t n, bool* checked) {
-    const DevParams<real> p = dev_params<real>(c);
+    const ParamsOf<S> p = dev_params<typename Storage<S>::real>(c);
     const int R = c->opt.residual_interval;
     for (int64_t s = 0; s < n; ++s) {
-        CUDA_OR_FAIL(c, launch_step<real>(c->dev, c->cur, p, c->stream));
+        CUDA_OR_FAIL(c, launch_step<S>(c->dev, c->cur, p, c->stream));
         c->cur ^= 1;
         c->steps += 1;
         if (R > 0 && c->steps % R == 0) {
             CUDA_OR_FAIL(c, cudaMemsetAsync(c->dev.resid_bits, 0, sizeof(unsigned long long), c->stream));
-            CUDA_OR_FAIL(c, launch_residual<real>(c->dev, c->cur, p, 1, c->stream));
+            CUDA_OR_FAIL(c, launch_residual<S>(c->dev, c->cur, p, 1, c->stream));
             *checked = true;
         }
     }
@@ -372,8 +403,8 @@ extern "C" int lbm_step(lbm_ctx* c, int64_t n) {
     if (!c || n < 0) return fail(c, LBM_EINVAL, "invalid context or step count%s");
     DeviceGuard g(c->device);
     bool checked = false;
-    int rc = c->precision == LBM_FP64 ? run_steps<double>(c, n, &checked)
-                                      : run_steps<float>(c, n, &checked);
+    int rc = with_storage(c->precision,
+                          [&](auto tag) { return run_steps<decltype(tag)>(c, n, &checked); });
     if (rc != LBM_OK || !checked) return rc;
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->host_bits, c->dev.resid_bits, sizeof(unsigned long long),
                                     cudaMemcpyDeviceToHost, c->stream));
@@ -390,12 +421,12 @@ extern "C" int lbm_step(lbm_ctx* c, int64_t n) {
     return LBM_OK;
 }
 
-template <typename real>
+template <typename S>
 static int run_fields(lbm_ctx* c, double* const* outs) {
-    const DevParams<real> p = dev_params<real>(c);
+    const ParamsOf<S> p = dev_params<typename Storage<S>::real>(c);
     for (int w = 0; w < 5; ++w) {
         if (!outs[w]) continue;
-        CUDA_OR_FAIL(c, launch_field<real>(c->dev, c->cur, p, w, c->stream));
+        CUDA_OR_FAIL(c, launch_field<S>(c->dev, c->cur, p, w, c->stream));
         CUDA_OR_FAIL(c, cudaMemcpyAsync(outs[w], c->dev.staging, c->ncell * sizeof(double),
                                         cudaMemcpyDeviceToHost, c->stream));
         int rc = wait_stream(c);
@@ -408,18 +439,20 @@ extern "C" int lbm_fields(lbm_ctx* c, double* rho, double* ux, double* uy, doubl
     if (!c) return fail(c, LBM_EINVAL, "NULL context%s");
     DeviceGuard g(c->device);
     double* outs[5] = {rho, ux, uy, uz, T};
-    return c->precision == LBM_FP64 ? run_fields<double>(c, outs) : run_fields<float>(c, outs);
+    return with_storage(c->precision, [&](auto tag) { return run_fields<decltype(tag)>(c, outs); });
 }
 
 extern "C" int lbm_nusselt(lbm_ctx* c, lbm_nu* out) {
     if (!c || !out) return fail(c, LBM_EINVAL, "NULL argument%s");
     if (c->grid.nx < 2) return fail(c, LBM_EINVAL, "lbm_nusselt needs nx >= 2%s");
     DeviceGuard g(c->device);
-    if (c->precision == LBM_FP64) {
-        CUDA_OR_FAIL(c, launch_nusselt<double>(c->dev, c->cur, dev_params<double>(c), c->params.U0, c->stream));
-    } else {
-        CUDA_OR_FAIL(c, launch_nusselt<float>(c->dev, c->cur, dev_params<float>(c), c->params.U0, c->stream));
-    }
+    int lrc = with_storage(c->precision, [&](auto tag) {
+        using S = decltype(tag);
+        CUDA_OR_FAIL(c, launch_nusselt<S>(c->dev, c->cur, dev_params<typename Storage<S>::real>(c),
+                                          c->params.U0, c->stream));
+        return LBM_OK;
+    });
+    if (lrc != LBM_OK) return lrc;
     double r[kResultDoubles];
     CUDA_OR_FAIL(c, cudaMemcpyAsync(r, c->dev.result, 11 * sizeof(double), cudaMemcpyDeviceToHost,
                                     c->stream));
@@ -445,22 +478,25 @@ extern "C" int lbm_residual(lbm_ctx* c, double* max_dT) {
     return LBM_OK;
 }
 
-template <typename real>
+template <typename S>
 static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const double* gin) {
+    using real = typename Storage<S>::real;
+    const ParamsOf<S> p = dev_params<real>(c);
     const int64_t n = c->ncell;
     for (int side = 0; side < 2; ++side) {
         const int q = side == 0 ? 15 : c->Q;
-        real* dev = static_cast<real*>(side == 0 ? c->dev.F[c->cur] : c->dev.G[c->cur]);
+        S* dev = static_cast<S*>(side == 0 ? c->dev.F[c->cur] : c->dev.G[c->cur]);
         for (int a = 0; a < q; ++a) {
-            real* plane = dev + (int64_t)a * c->plane;
+            S* plane = dev + (int64_t)a * c->plane;
+            const double offset = (double)(side == 0 ? p.wf[a] : p.wt[a]);
             if (fin || gin) {  // host -> device
                 const double* src = (side == 0 ? fin : gin) + (int64_t)a * n;
                 CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dev.staging, src, n * sizeof(double),
                                                 cudaMemcpyHostToDevice, c->stream));
-                CUDA_OR_FAIL(c, launch_to_real<real>(plane, c->dev.staging, n, c->stream));
+                CUDA_OR_FAIL(c, launch_to_storage<S>(plane, c->dev.staging, n, offset, c->stream));
             } else {  // device -> host
                 double* dst = (side == 0 ? f : g) + (int64_t)a * n;
-                CUDA_OR_FAIL(c, launch_to_double<real>(c->dev.staging, plane, n, c->stream));
+                CUDA_OR_FAIL(c, launch_to_double<S>(c->dev.staging, plane, n, offset, c->stream));
                 CUDA_OR_FAIL(c, cudaMemcpyAsync(dst, c->dev.staging, n * sizeof(double),
                                                 cudaMemcpyDeviceToHost, c->stream));
             }
@@ -470,7 +506,7 @@ static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const d
         }
     }
     if (fin || gin) {
-        CUDA_OR_FAIL(c, launch_residual<real>(c->dev, c->cur, dev_params<real>(c), 0, c->stream));
+        CUDA_OR_FAIL(c, launch_residual<S>(c->dev, c->cur, p, 0, c->stream));
         c->last_residual = -1.0;
         return wait_stream(c);
     }
@@ -480,15 +516,17 @@ static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const d
 extern "C" int lbm_get_populations(lbm_ctx* c, double* f, double* g) {
     if (!c || !f || !g) return fail(c, LBM_EINVAL, "NULL argument%s");
     DeviceGuard gd(c->device);
-    return c->precision == LBM_FP64 ? transfer<double>(c, f, g, nullptr, nullptr)
-                                    : transfer<float>(c, f, g, nullptr, nullptr);
+    return with_storage(c->precision, [&](auto tag) {
+        return transfer<decltype(tag)>(c, f, g, nullptr, nullptr);
+    });
 }
 
 extern "C" int lbm_set_populations(lbm_ctx* c, const double* f, const double* g) {
     if (!c || !f || !g) return fail(c, LBM_EINVAL, "NULL argument%s");
     DeviceGuard gd(c->device);
-    return c->precision == LBM_FP64 ? transfer<double>(c, nullptr, nullptr, f, g)
-                                    : transfer<float>(c, nullptr, nullptr, f, g);
+    return with_storage(c->precision, [&](auto tag) {
+        return transfer<decltype(tag)>(c, nullptr, nullptr, f, g);
+    });
 }
 
 extern "C" int lbm_get_params(const lbm_ctx* c, lbm_params* out) {

@@ -20,23 +20,26 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return z ^ (z >> 31);
 }
 
-template <typename real, int Q>
-__global__ void init_kernel(real* __restrict__ F, real* __restrict__ G, DevParams<real> p,
-                            uint64_t seed, double amp, double w0, double w1, double w7,
-                            double v0, double v1, double v7) {
+template <typename S, int Q>
+__global__ void init_kernel(S* __restrict__ F, S* __restrict__ G, ParamsOf<S> p, uint64_t seed,
+                            double amp, double w0, double w1, double w7, double v0, double v1,
+                            double v7) {
+    using real = typename Storage<S>::real;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= p.ncell) return;
     const uint64_t r = splitmix64(seed ^ (uint64_t)c);
     const double u01 = (double)(r >> 11) * (1.0 / 9007199254740992.0);
     const double T = amp * (2.0 * u01 - 1.0);
 #pragma unroll
-    for (int a = 0; a < 15; ++a) F[a * p.plane + c] = (real)(a == 0 ? w0 : a < 7 ? w1 : w7);
+    for (int a = 0; a < 15; ++a)
+        F[a * p.plane + c] = Storage<S>::store((real)(a == 0 ? w0 : a < 7 ? w1 : w7), p.wf[a]);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) G[a * p.plane + c] = (real)((a == 0 ? v0 : a < 7 ? v1 : v7) * T);
+    for (int a = 0; a < Q; ++a)
+        G[a * p.plane + c] = Storage<S>::store((real)((a == 0 ? v0 : a < 7 ? v1 : v7) * T), p.wt[a]);
 }
 
-template <typename real>
-cudaError_t launch_init(const DevState& s, const DevParams<real>& p, uint64_t seed, double amp,
+template <typename S>
+cudaError_t launch_init(const DevState& s, const ParamsOf<S>& p, uint64_t seed, double amp,
                         cudaStream_t st) {
     // rest weights: flow (c_s^2 = 1/3) and thermal (c_sphi^2), from the equilibria
     const double cs2 = 1.0 / 3.0, ct = (double)p.cs2_phi;
@@ -53,29 +56,35 @@ cudaError_t launch_init(const DevState& s, const DevParams<real>& p, uint64_t se
     }
     const int threads = 256;
     const unsigned blocks = (unsigned)((p.ncell + threads - 1) / threads);
-    real* F = static_cast<real*>(s.F[0]);
-    real* G = static_cast<real*>(s.G[0]);
+    S* F = static_cast<S*>(s.F[0]);
+    S* G = static_cast<S*>(s.G[0]);
     if (s.Q == 15)
-        init_kernel<real, 15><<<blocks, threads, 0, st>>>(F, G, p, seed, amp, w0, w1, w7, v0, v1, v7);
+        init_kernel<S, 15><<<blocks, threads, 0, st>>>(F, G, p, seed, amp, w0, w1, w7, v0, v1, v7);
     else
-        init_kernel<real, 7><<<blocks, threads, 0, st>>>(F, G, p, seed, amp, w0, w1, w7, v0, v1, v7);
+        init_kernel<S, 7><<<blocks, threads, 0, st>>>(F, G, p, seed, amp, w0, w1, w7, v0, v1, v7);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------
-// Precision conversion of one population plane (host transfers stage FP64 planes).
+// Conversion of one population plane between FP64 host values and storage (host
+// transfers stage FP64 planes).  The 16-bit forms encode and decode exactly as the step
+// kernel does (FP32 offset arithmetic), so set(get(state)) restores the FP16 state.
 // ---------------------------------------------------------------------------------
-template <typename real>
-__global__ void to_real_kernel(real* __restrict__ dst, const double* __restrict__ src, int64_t n) {
+template <typename S>
+__global__ void to_storage_kernel(S* __restrict__ dst, const double* __restrict__ src, int64_t n,
+                                  double offset) {
+    using real = typename Storage<S>::real;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x)
-        dst[c] = (real)src[c];
+        dst[c] = Storage<S>::store((real)src[c], (real)offset);
 }
-template <typename real>
-__global__ void to_double_kernel(double* __restrict__ dst, const real* __restrict__ src, int64_t n) {
+template <typename S>
+__global__ void to_double_kernel(double* __restrict__ dst, const S* __restrict__ src, int64_t n,
+                                 double offset) {
+    using real = typename Storage<S>::real;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x)
-        dst[c] = (double)src[c];
+        dst[c] = (double)Storage<S>::load(src[c], (real)offset);
 }
 
 static unsigned grid_for(int64_t n, int threads) {
@@ -85,14 +94,14 @@ static unsigned grid_for(int64_t n, int threads) {
     return (unsigned)b;
 }
 
-template <typename real>
-cudaError_t launch_to_real(real* dst, const double* src, int64_t n, cudaStream_t st) {
-    to_real_kernel<real><<<grid_for(n, 256), 256, 0, st>>>(dst, src, n);
+template <typename S>
+cudaError_t launch_to_storage(S* dst, const double* src, int64_t n, double offset, cudaStream_t st) {
+    to_storage_kernel<S><<<grid_for(n, 256), 256, 0, st>>>(dst, src, n, offset);
     return cudaGetLastError();
 }
-template <typename real>
-cudaError_t launch_to_double(double* dst, const real* src, int64_t n, cudaStream_t st) {
-    to_double_kernel<real><<<grid_for(n, 256), 256, 0, st>>>(dst, src, n);
+template <typename S>
+cudaError_t launch_to_double(double* dst, const S* src, int64_t n, double offset, cudaStream_t st) {
+    to_double_kernel<S><<<grid_for(n, 256), 256, 0, st>>>(dst, src, n, offset);
     return cudaGetLastError();
 }
 
@@ -100,21 +109,21 @@ cudaError_t launch_to_double(double* dst, const real* src, int64_t n, cudaStream
 // Macroscopic fields of the stored (post-collision) state: rho = sum f, T = sum g,
 // rho u = sum f e - F/2 (collision added F to the momentum, Eq. 2a), in FP64.
 // ---------------------------------------------------------------------------------
-template <typename real, int Q>
-__device__ __forceinline__ void node_macro(const real* __restrict__ F, const real* __restrict__ G,
-                                           const DevParams<real>& p, int64_t c, double& rho,
+template <typename S, int Q>
+__device__ __forceinline__ void node_macro(const S* __restrict__ F, const S* __restrict__ G,
+                                           const ParamsOf<S>& p, int64_t c, double& rho,
                                            double& ux, double& uy, double& uz, double& T) {
     double r = 0, jx = 0, jy = 0, jz = 0, t = 0;
 #pragma unroll
     for (int a = 0; a < 15; ++a) {
-        const double v = (double)F[a * p.plane + c];
+        const double v = (double)Storage<S>::load(F[a * p.plane + c], p.wf[a]);
         r += v;
         jx += ex(a) * v;
         jy += ey(a) * v;
         jz += ez(a) * v;
     }
 #pragma unroll
-    for (int a = 0; a < Q; ++a) t += (double)G[a * p.plane + c];
+    for (int a = 0; a < Q; ++a) t += (double)Storage<S>::load(G[a * p.plane + c], p.wt[a]);
     const double Fz = (double)p.ext_fz + (double)p.gbeta * (t - (double)p.T0);
     rho = r;
     ux = (jx - 0.5 * (double)p.ext_fx) / r;
@@ -123,26 +132,26 @@ __device__ __forceinline__ void node_macro(const real* __restrict__ F, const rea
     T = t;
 }
 
-template <typename real, int Q>
-__global__ void field_kernel(const real* __restrict__ F, const real* __restrict__ G,
-                             DevParams<real> p, int which, double* __restrict__ out) {
+template <typename S, int Q>
+__global__ void field_kernel(const S* __restrict__ F, const S* __restrict__ G, ParamsOf<S> p,
+                             int which, double* __restrict__ out) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < p.ncell;
          c += (int64_t)gridDim.x * blockDim.x) {
         double rho, ux, uy, uz, T;
-        node_macro<real, Q>(F, G, p, c, rho, ux, uy, uz, T);
+        node_macro<S, Q>(F, G, p, c, rho, ux, uy, uz, T);
         out[c] = which == 0 ? rho : which == 1 ? ux : which == 2 ? uy : which == 3 ? uz : T;
     }
 }
 
-template <typename real>
-cudaError_t launch_field(const DevState& s, int cur, const DevParams<real>& p, int which,
+template <typename S>
+cudaError_t launch_field(const DevState& s, int cur, const ParamsOf<S>& p, int which,
                          cudaStream_t st) {
-    const real* F = static_cast<const real*>(s.F[cur]);
-    const real* G = static_cast<const real*>(s.G[cur]);
+    const S* F = static_cast<const S*>(s.F[cur]);
+    const S* G = static_cast<const S*>(s.G[cur]);
     if (s.Q == 15)
-        field_kernel<real, 15><<<grid_for(p.ncell, 256), 256, 0, st>>>(F, G, p, which, s.staging);
+        field_kernel<S, 15><<<grid_for(p.ncell, 256), 256, 0, st>>>(F, G, p, which, s.staging);
     else
-        field_kernel<real, 7><<<grid_for(p.ncell, 256), 256, 0, st>>>(F, G, p, which, s.staging);
+        field_kernel<S, 7><<<grid_for(p.ncell, 256), 256, 0, st>>>(F, G, p, which, s.staging);
     return cudaGetLastError();
 }
 
@@ -176,19 +185,20 @@ __device__ __forceinline__ void warp_argmax(double& v, int& idx) {
 // Residual: max over the grid of |T - T_snapshot|, snapshot <- T, and a flag for any
 // non-finite T.  With record == 0 the kernel only refreshes the snapshot.
 // ---------------------------------------------------------------------------------
-template <typename real, int Q>
-__global__ void __launch_bounds__(256) residual_kernel(const real* __restrict__ G,
-                                                       real* __restrict__ snap, DevParams<real> p,
-                                                       int record,
+template <typename S, int Q>
+__global__ void __launch_bounds__(256) residual_kernel(const S* __restrict__ G,
+                                                       typename Storage<S>::real* __restrict__ snap,
+                                                       ParamsOf<S> p, int record,
                                                        unsigned long long* __restrict__ max_bits,
                                                        int* __restrict__ nonfinite) {
+    using real = typename Storage<S>::real;
     double local = 0.0;
     int bad = 0;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < p.ncell;
          c += (int64_t)gridDim.x * blockDim.x) {
         real T = real(0);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) T += G[a * p.plane + c];
+        for (int a = 0; a < Q; ++a) T += Storage<S>::load(G[a * p.plane + c], p.wt[a]);
         if (!isfinite(T)) bad = 1;
         const double d = fabs((double)T - (double)snap[c]);
         if (d > local) local = d;
@@ -209,16 +219,17 @@ __global__ void __launch_bounds__(256) residual_kernel(const real* __restrict__ 
     }
 }
 
-template <typename real>
-cudaError_t launch_residual(const DevState& s, int cur, const DevParams<real>& p, int record,
+template <typename S>
+cudaError_t launch_residual(const DevState& s, int cur, const ParamsOf<S>& p, int record,
                             cudaStream_t st) {
-    const real* G = static_cast<const real*>(s.G[cur]);
+    using real = typename Storage<S>::real;
+    const S* G = static_cast<const S*>(s.G[cur]);
     real* snap = static_cast<real*>(s.snap);
     const unsigned blocks = grid_for(p.ncell, 256) > 152 * 8 ? 152 * 8 : grid_for(p.ncell, 256);
     if (s.Q == 15)
-        residual_kernel<real, 15><<<blocks, 256, 0, st>>>(G, snap, p, record, s.resid_bits, s.nonfinite);
+        residual_kernel<S, 15><<<blocks, 256, 0, st>>>(G, snap, p, record, s.resid_bits, s.nonfinite);
     else
-        residual_kernel<real, 7><<<blocks, 256, 0, st>>>(G, snap, p, record, s.resid_bits, s.nonfinite);
+        residual_kernel<S, 7><<<blocks, 256, 0, st>>>(G, snap, p, record, s.resid_bits, s.nonfinite);
     return cudaGetLastError();
 }
 
@@ -229,19 +240,19 @@ cudaError_t launch_residual(const DevState& s, int cur, const DevParams<real>& p
 // and evaluates the symmetry-plane lines: Nu(z) on the hot wall, |u_x|(z) on the
 // vertical centreline and |u_z|(x) on the horizontal centreline.
 // ---------------------------------------------------------------------------------
-template <typename real, int Q>
-__device__ __forceinline__ double node_T(const real* __restrict__ G, const DevParams<real>& p,
-                                         int i, int j, int k) {
+template <typename S, int Q>
+__device__ __forceinline__ double node_T(const S* __restrict__ G, const ParamsOf<S>& p, int i,
+                                         int j, int k) {
     const int64_t c = ((int64_t)k * p.ny + j) * p.nx + i;
     double t = 0.0;
 #pragma unroll
-    for (int a = 0; a < Q; ++a) t += (double)G[a * p.plane + c];
+    for (int a = 0; a < Q; ++a) t += (double)Storage<S>::load(G[a * p.plane + c], p.wt[a]);
     return t;
 }
 
-template <typename real, int Q>
-__global__ void __launch_bounds__(256) nusselt_faces_kernel(const real* __restrict__ G,
-                                                            DevParams<real> p,
+template <typename S, int Q>
+__global__ void __launch_bounds__(256) nusselt_faces_kernel(const S* __restrict__ G,
+                                                            ParamsOf<S> p,
                                                             double* __restrict__ partials) {
     const double L = p.nx, dT = (double)p.T_hot - (double)p.T_cold;
     double hot = 0.0, cold = 0.0;
@@ -249,10 +260,10 @@ __global__ void __launch_bounds__(256) nusselt_faces_kernel(const real* __restri
     for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nface;
          f += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(f % p.ny), k = (int)(f / p.ny);
-        const double th1 = node_T<real, Q>(G, p, p.nx - 1, j, k);
-        const double th2 = node_T<real, Q>(G, p, p.nx - 2, j, k);
-        const double tc1 = node_T<real, Q>(G, p, 0, j, k);
-        const double tc2 = node_T<real, Q>(G, p, 1, j, k);
+        const double th1 = node_T<S, Q>(G, p, p.nx - 1, j, k);
+        const double th2 = node_T<S, Q>(G, p, p.nx - 2, j, k);
+        const double tc1 = node_T<S, Q>(G, p, 0, j, k);
+        const double tc2 = node_T<S, Q>(G, p, 1, j, k);
         hot += -L * (9.0 * th1 - th2 - 8.0 * (double)p.T_hot) / (3.0 * dT);
         cold += L * (9.0 * tc1 - tc2 - 8.0 * (double)p.T_cold) / (3.0 * dT);
     }
@@ -270,10 +281,10 @@ __global__ void __launch_bounds__(256) nusselt_faces_kernel(const real* __restri
     }
 }
 
-template <typename real, int Q>
-__global__ void __launch_bounds__(256) nusselt_lines_kernel(const real* __restrict__ F,
-                                                            const real* __restrict__ G,
-                                                            DevParams<real> p, int nblocks,
+template <typename S, int Q>
+__global__ void __launch_bounds__(256) nusselt_lines_kernel(const S* __restrict__ F,
+                                                            const S* __restrict__ G,
+                                                            ParamsOf<S> p, int nblocks,
                                                             double U0,
                                                             const double* __restrict__ partials,
                                                             double* __restrict__ result) {
@@ -287,8 +298,8 @@ __global__ void __launch_bounds__(256) nusselt_lines_kernel(const real* __restri
     double umax = -1.0, wmax = -1.0;
     int kum = 0x7fffffff, iwm = 0x7fffffff;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-        const double t1 = 0.5 * (node_T<real, Q>(G, p, nx - 1, j0, k) + node_T<real, Q>(G, p, nx - 1, j1, k));
-        const double t2 = 0.5 * (node_T<real, Q>(G, p, nx - 2, j0, k) + node_T<real, Q>(G, p, nx - 2, j1, k));
+        const double t1 = 0.5 * (node_T<S, Q>(G, p, nx - 1, j0, k) + node_T<S, Q>(G, p, nx - 1, j1, k));
+        const double t2 = 0.5 * (node_T<S, Q>(G, p, nx - 2, j0, k) + node_T<S, Q>(G, p, nx - 2, j1, k));
         const double nu = -L * (9.0 * t1 - t2 - 8.0 * (double)p.T_hot) / (3.0 * dT);
         nsum += nu;
         argmax_combine(nmax, kmax, nu, k);
@@ -297,7 +308,7 @@ __global__ void __launch_bounds__(256) nusselt_lines_kernel(const real* __restri
         const int is[2] = {i0, i1}, js[2] = {j0, j1};
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) {
-                node_macro<real, Q>(F, G, p, ((int64_t)k * ny + js[b]) * nx + is[a], r, ux, uy, uz, T);
+                node_macro<S, Q>(F, G, p, ((int64_t)k * ny + js[b]) * nx + is[a], r, ux, uy, uz, T);
                 acc += ux;
             }
         argmax_combine(umax, kum, fabs(0.25 * acc), k);
@@ -307,7 +318,7 @@ __global__ void __launch_bounds__(256) nusselt_lines_kernel(const real* __restri
         const int js[2] = {j0, j1}, ks[2] = {k0, k1};
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) {
-                node_macro<real, Q>(F, G, p, ((int64_t)ks[b] * ny + js[a]) * nx + i, r, ux, uy, uz, T);
+                node_macro<S, Q>(F, G, p, ((int64_t)ks[b] * ny + js[a]) * nx + i, r, ux, uy, uz, T);
                 acc += uz;
             }
         argmax_combine(wmax, iwm, fabs(0.25 * acc), i);
@@ -362,52 +373,54 @@ __global__ void __launch_bounds__(256) nusselt_lines_kernel(const real* __restri
     }
 }
 
-template <typename real>
-cudaError_t launch_nusselt(const DevState& s, int cur, const DevParams<real>& p, double U0,
+template <typename S>
+cudaError_t launch_nusselt(const DevState& s, int cur, const ParamsOf<S>& p, double U0,
                            cudaStream_t st) {
-    const real* F = static_cast<const real*>(s.F[cur]);
-    const real* G = static_cast<const real*>(s.G[cur]);
+    const S* F = static_cast<const S*>(s.F[cur]);
+    const S* G = static_cast<const S*>(s.G[cur]);
     int64_t nface = (int64_t)p.ny * p.nz;
     int blocks = (int)((nface + 255) / 256);
     if (blocks > kPartialBlocks) blocks = kPartialBlocks;
     if (s.Q == 15) {
-        nusselt_faces_kernel<real, 15><<<blocks, 256, 0, st>>>(G, p, s.partials);
-        nusselt_lines_kernel<real, 15><<<1, 256, 0, st>>>(F, G, p, blocks, U0, s.partials, s.result);
+        nusselt_faces_kernel<S, 15><<<blocks, 256, 0, st>>>(G, p, s.partials);
+        nusselt_lines_kernel<S, 15><<<1, 256, 0, st>>>(F, G, p, blocks, U0, s.partials, s.result);
     } else {
-        nusselt_faces_kernel<real, 7><<<blocks, 256, 0, st>>>(G, p, s.partials);
-        nusselt_lines_kernel<real, 7><<<1, 256, 0, st>>>(F, G, p, blocks, U0, s.partials, s.result);
+        nusselt_faces_kernel<S, 7><<<blocks, 256, 0, st>>>(G, p, s.partials);
+        nusselt_lines_kernel<S, 7><<<1, 256, 0, st>>>(F, G, p, blocks, U0, s.partials, s.result);
     }
     return cudaGetLastError();
 }
 
-template <typename real>
-cudaError_t launch_nusselt_into(const real* F, const real* G, const DevParams<real>& p, double U0,
+template <typename S>
+cudaError_t launch_nusselt_into(const S* F, const S* G, const ParamsOf<S>& p, double U0,
                                 int Q, int blocks, double* partials, double* result,
                                 cudaStream_t st) {
     if (Q == 15) {
-        nusselt_faces_kernel<real, 15><<<blocks, 256, 0, st>>>(G, p, partials);
-        nusselt_lines_kernel<real, 15><<<1, 256, 0, st>>>(F, G, p, blocks, U0, partials, result);
+        nusselt_faces_kernel<S, 15><<<blocks, 256, 0, st>>>(G, p, partials);
+        nusselt_lines_kernel<S, 15><<<1, 256, 0, st>>>(F, G, p, blocks, U0, partials, result);
     } else {
-        nusselt_faces_kernel<real, 7><<<blocks, 256, 0, st>>>(G, p, partials);
-        nusselt_lines_kernel<real, 7><<<1, 256, 0, st>>>(F, G, p, blocks, U0, partials, result);
+        nusselt_faces_kernel<S, 7><<<blocks, 256, 0, st>>>(G, p, partials);
+        nusselt_lines_kernel<S, 7><<<1, 256, 0, st>>>(F, G, p, blocks, U0, partials, result);
     }
     return cudaGetLastError();
 }
 
-#define LBM_INSTANTIATE(real)                                                                       \
-    template cudaError_t launch_init<real>(const DevState&, const DevParams<real>&, uint64_t, double, \
-                                           cudaStream_t);                                           \
-    template cudaError_t launch_to_real<real>(real*, const double*, int64_t, cudaStream_t);           \
-    template cudaError_t launch_to_double<real>(double*, const real*, int64_t, cudaStream_t);         \
-    template cudaError_t launch_field<real>(const DevState&, int, const DevParams<real>&, int,        \
-                                            cudaStream_t);                                          \
-    template cudaError_t launch_residual<real>(const DevState&, int, const DevParams<real>&, int,     \
-                                               cudaStream_t);                                       \
-    template cudaError_t launch_nusselt<real>(const DevState&, int, const DevParams<real>&, double,   \
-                                              cudaStream_t);                                        \
-    template cudaError_t launch_nusselt_into<real>(const real*, const real*, const DevParams<real>&,  \
-                                                   double, int, int, double*, double*, cudaStream_t);
-LBM_INSTANTIATE(float)
+#define LBM_INSTANTIATE(S)                                                                         \
+    template cudaError_t launch_init<S>(const DevState&, const ParamsOf<S>&, uint64_t, double,      \
+                                        cudaStream_t);                                             \
+    template cudaError_t launch_to_storage<S>(S*, const double*, int64_t, double, cudaStream_t);    \
+    template cudaError_t launch_to_double<S>(double*, const S*, int64_t, double, cudaStream_t);     \
+    template cudaError_t launch_field<S>(const DevState&, int, const ParamsOf<S>&, int,             \
+                                         cudaStream_t);                                            \
+    template cudaError_t launch_residual<S>(const DevState&, int, const ParamsOf<S>&, int,          \
+                                            cudaStream_t);                                         \
+    template cudaError_t launch_nusselt<S>(const DevState&, int, const ParamsOf<S>&, double,        \
+                                           cudaStream_t);                                          \
+    template cudaError_t launch_nusselt_into<S>(const S*, const S*, const ParamsOf<S>&, double, int, \
+                                                int, double*, double*, cudaStream_t);
 LBM_INSTANTIATE(double)
+LBM_INSTANTIATE(float)
+LBM_INSTANTIATE(__half)
+LBM_INSTANTIATE(__nv_bfloat16)
 
 }  // namespace lbm

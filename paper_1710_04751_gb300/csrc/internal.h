@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "storage.cuh"
+
 namespace lbm {
 
 // Kernel parameters, passed by value (they land in the constant bank).
@@ -12,6 +14,8 @@ struct DevParams {
     real om_f[15];      // flow relaxation rates (App. A)
     real om_g[15];      // thermal relaxation rates (Sec. 2.2 / App. C)
     real wg[15];        // thermal rest weights w^phi_a (anti-bounce-back)
+    real wf[15];        // stored-value offsets of the flow populations (16-bit forms: w_a)
+    real wt[15];        // stored-value offsets of the scalar populations (w^phi_a T0)
     real gbeta, T0, T_hot, T_cold, cs2_phi;
     real ext_fx, ext_fy, ext_fz;
     int e4_mode, adiabatic_mode, boundary;
@@ -22,7 +26,7 @@ struct DevParams {
 
 // Host-side view of one context's device buffers for the launchers.
 struct DevState {
-    int precision;      // 0 fp64, 1 fp32
+    int precision;      // 0 fp64, 1 fp32, 2 fp16 deviations, 3 bf16 deviations
     int Q;              // 15 or 7
     void* F[2];
     void* G[2];
@@ -37,30 +41,37 @@ struct DevState {
 constexpr int kPartialBlocks = 1024;   // max blocks of the face reduction
 constexpr int kResultDoubles = 16;
 
-// Launchers (return cudaGetLastError()).  `cur` selects the source buffer of a step.
-template <typename real>
-cudaError_t launch_step(const DevState& s, int cur, const DevParams<real>& p, cudaStream_t st);
-template <typename real>
-cudaError_t launch_init(const DevState& s, const DevParams<real>& p, uint64_t seed, double amp,
+// Launchers (return cudaGetLastError()), templated on the storage type S (double,
+// float, __half, __nv_bfloat16); arithmetic is Storage<S>::real.  `cur` selects the
+// source buffer of a step.
+template <typename S>
+using ParamsOf = DevParams<typename Storage<S>::real>;
+
+template <typename S>
+cudaError_t launch_step(const DevState& s, int cur, const ParamsOf<S>& p, cudaStream_t st);
+template <typename S>
+cudaError_t launch_init(const DevState& s, const ParamsOf<S>& p, uint64_t seed, double amp,
                         cudaStream_t st);
-template <typename real>
-cudaError_t launch_to_real(real* dst, const double* src, int64_t n, cudaStream_t st);
-template <typename real>
-cudaError_t launch_to_double(double* dst, const real* src, int64_t n, cudaStream_t st);
-template <typename real>
-cudaError_t launch_field(const DevState& s, int cur, const DevParams<real>& p, int which,
+// one population plane between FP64 host values and storage (offset: that plane's
+// stored-value offset, used by the 16-bit forms)
+template <typename S>
+cudaError_t launch_to_storage(S* dst, const double* src, int64_t n, double offset, cudaStream_t st);
+template <typename S>
+cudaError_t launch_to_double(double* dst, const S* src, int64_t n, double offset, cudaStream_t st);
+template <typename S>
+cudaError_t launch_field(const DevState& s, int cur, const ParamsOf<S>& p, int which,
                          cudaStream_t st);
-template <typename real>
-cudaError_t launch_residual(const DevState& s, int cur, const DevParams<real>& p, int record,
+template <typename S>
+cudaError_t launch_residual(const DevState& s, int cur, const ParamsOf<S>& p, int record,
                             cudaStream_t st);
-template <typename real>
-cudaError_t launch_nusselt(const DevState& s, int cur, const DevParams<real>& p, double U0,
+template <typename S>
+cudaError_t launch_nusselt(const DevState& s, int cur, const ParamsOf<S>& p, double U0,
                            cudaStream_t st);
 
 // Nusselt reduction into caller-provided device scratch: one face block per 256 face
 // cells (`blocks` of them, partial pairs at partials[0 .. 2*blocks)), result[0..11).
-template <typename real>
-cudaError_t launch_nusselt_into(const real* F, const real* G, const DevParams<real>& p, double U0,
+template <typename S>
+cudaError_t launch_nusselt_into(const S* F, const S* G, const ParamsOf<S>& p, double U0,
                                 int Q, int blocks, double* partials, double* result,
                                 cudaStream_t st);
 

@@ -22,7 +22,7 @@
 #include <mutex>
 #include <thread>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 #include "internal.h"
 
 using namespace lbm;

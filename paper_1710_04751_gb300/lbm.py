@@ -15,7 +15,7 @@ from . import build as _build
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5
 D3Q15, D3Q7 = 15, 7
-FP64, FP32 = 0, 1
+FP64, FP32, FP16_DEV, BF16_DEV = 0, 1, 2, 3
 BC_CAVITY, BC_XWALLS, BC_PERIODIC, BC_ADIABATIC_BOX = 0, 6, 7, 8
 ADIABATIC_BOUNCE_BACK, ADIABATIC_SPECULAR = 0, 1
 

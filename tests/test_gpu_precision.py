@@ -1,0 +1,94 @@
+"""The 16-bit storage forms (FP16 / BF16 deviations from the rest state, FP32 arithmetic)
+against the FP64 oracle and against the FP32 path.
+
+One step from a state both sides share (the GPU's own decoded state): each population
+may differ from the oracle by the rounding of its stored deviation, 2^-11 |p - p_rest|
+(FP16) or 2^-8 |p - p_rest| (BF16), plus the FP32 bound of the FP32 tests and, for FP16,
+half the smallest subnormal step (2^-25)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import inputs
+from tests.test_gpu_parity import FP32_REL, gpu_for, random_state, thermal_floor
+
+pytestmark = pytest.mark.gpu
+
+EPS = {"FP16_DEV": 2.0 ** -11, "BF16_DEV": 2.0 ** -8}
+SUBNORMAL_HALF = {"FP16_DEV": 2.0 ** -25, "BF16_DEV": 0.0}
+
+
+def _bound(p, prec_name, ref_f, ref_g):
+    wf = oracle.weights_flow()[:, None, None, None]
+    T0 = 0.5 * (p.T_hot + p.T_cold)
+    wt = (oracle.weights_thermal(p.q_g, p.cs2_phi) * T0)[:, None, None, None]
+    floor_g = thermal_floor(p.q_g, p.cs2_phi, p.T_hot - p.T_cold)[:, None, None, None]
+    e, sub = EPS[prec_name], SUBNORMAL_HALF[prec_name]
+    bf = e * np.abs(ref_f - wf) + FP32_REL * np.maximum(np.abs(ref_f), wf) + sub
+    bg = e * np.abs(ref_g - wt) + FP32_REL * np.maximum(np.abs(ref_g), floor_g) + sub
+    return bf, bg
+
+
+CASES = [(13, 7, 5, 15), (9, 11, 6, 7), (32, 8, 8, 15)]
+
+
+@pytest.mark.parametrize("prec_name", ["FP16_DEV", "BF16_DEV"])
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}-q{c[3]}" for c in CASES])
+def test_one_step_against_oracle(prec_name, case):
+    import paper_1710_04751_gb300 as lbm
+    nx, ny, nz, q = case
+    p = oracle.Problem(nx, ny, nz, q_g=q, omega_nu=1.7, omega_phi=1.6, gbeta=2e-3, U0=0.05,
+                       cs2_phi=1 / 3 if q == 15 else 0.25)
+    F, G = random_state(p, 40 + nx)
+    sim = gpu_for(p, getattr(lbm, prec_name))
+    sim.set_populations(F, G)
+    f, g = sim.get_populations()  # the decoded 16-bit state both sides start from
+    # storing the state rounds only the deviation from the rest state
+    bf0, bg0 = _bound(p, prec_name, F, G)
+    assert (np.abs(f - F) <= bf0).all() and (np.abs(g - G) <= bg0).all()
+    sim.step(1)
+    F1, G1 = p.step(f, g)
+    f1, g1 = sim.get_populations()
+    bf, bg = _bound(p, prec_name, F1, G1)
+    assert (np.abs(f1 - F1) <= bf).all(), np.max(np.abs(f1 - F1) / bf)
+    assert (np.abs(g1 - G1) <= bg).all(), np.max(np.abs(g1 - G1) / bg)
+
+
+def test_fp16_checkpoint_roundtrip_is_exact():
+    import paper_1710_04751_gb300 as lbm
+    a = lbm.LBM((20, 12, 10), 15, Ra=3e3, precision=lbm.FP16_DEV)
+    a.step(150)
+    f, g = a.get_populations()
+    b = lbm.LBM((20, 12, 10), 15, Ra=3e3, precision=lbm.FP16_DEV, seed=5)
+    b.set_populations(f, g)
+    f2, g2 = b.get_populations()
+    assert np.array_equal(f, f2) and np.array_equal(g, g2)
+    a.step(50)
+    b.step(50)
+    fa, ga = a.get_populations()
+    fb, gb = b.get_populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+@pytest.mark.timeout(600)
+def test_steady_nusselt_of_the_16bit_forms():
+    # 48^3, Ra = 1e4, to max |dT| per 100 steps < 1e-6 (or 150k steps): steady Nu of FP16
+    # within 2% of FP32; BF16 (8 significant bits) within 30%
+    import paper_1710_04751_gb300 as lbm
+    out = {}
+    for name in ("FP32", "FP16_DEV", "BF16_DEV"):
+        sim = lbm.LBM((48, 48, 48), 15, Ra=1e4, Ma=0.05 * math.sqrt(3.0),
+                      precision=getattr(lbm, name))
+        while sim.steps_done < 150_000:
+            sim.step(2000)
+            r = sim.residual()
+            if 0 <= r < 1e-6:
+                break
+        out[name] = (sim.nusselt(), sim.steps_done, sim.residual())
+    ref = out["FP32"][0]
+    print({k: (v[0]["mid_mean"], v[0]["hot_wall_mean"], v[1], v[2]) for k, v in out.items()})
+    for k in ("mid_mean", "hot_wall_mean"):
+        assert out["FP16_DEV"][0][k] == pytest.approx(ref[k], rel=2e-2), k
+        assert out["BF16_DEV"][0][k] == pytest.approx(ref[k], rel=0.3), k
