@@ -139,7 +139,7 @@ extern "C" int lbm_derive_params(const lbm_grid* grid, int lattice, double Ra, d
 static int64_t plane_of(int64_t ncell) { return (ncell + 63) / 64 * 64; }
 
 struct Layout {
-    size_t F[2], G[2], snap, staging, partials, result, bits, total;
+    size_t F[2], G[2], T[2], snap, staging, partials, result, bits, total;
 };
 
 // bytes of one stored population and of the arithmetic type, by precision
@@ -171,6 +171,9 @@ static Layout layout_of(const lbm_grid* g, int q, int precision) {
     size_t off = 0;
     for (int b = 0; b < 2; ++b) { L.F[b] = off; off = align_up(off + 15 * plane * rs, 256); }
     for (int b = 0; b < 2; ++b) { L.G[b] = off; off = align_up(off + q * plane * rs, 256); }
+    // 16-bit forms: FP32 node temperatures the stored thermal deviations refer to
+    const bool dev = precision == LBM_FP16_DEV || precision == LBM_BF16_DEV;
+    for (int b = 0; b < 2; ++b) { L.T[b] = off; off = align_up(off + (dev ? plane * 4 : 0), 256); }
     L.snap = off; off = align_up(off + plane * compute_bytes(precision), 256);
     L.staging = off; off = align_up(off + plane * 8, 256);
     L.partials = off; off = align_up(off + 2 * kPartialBlocks * 8, 256);
@@ -205,15 +208,13 @@ static DevParams<real> dev_params(const lbm_ctx* c) {
         w1 = 0.5 * cs;
         w0 = 1.0 - 6.0 * w1;
     }
-    const double T0 = 0.5 * (P.T_hot + P.T_cold);
     const double cs2 = 1.0 / 3.0;
     const double f7 = cs2 * cs2 / 8.0, f1 = 0.5 * (cs2 - cs2 * cs2), f0 = 1.0 - 6.0 * f1 - 8.0 * f7;
     for (int a = 0; a < 15; ++a) {
         const double wg = a == 0 ? w0 : a < 7 ? w1 : w7;
         p.wg[a] = (real)wg;
-        // stored-value offsets (used by the 16-bit forms): rest-state populations
+        // stored-value offsets of the flow populations (16-bit forms): rest-state values
         p.wf[a] = (real)(a == 0 ? f0 : a < 7 ? f1 : f7);
-        p.wt[a] = (real)(wg * T0);
     }
     p.gbeta = (real)P.gbeta;
     p.T0 = (real)(0.5 * (P.T_hot + P.T_cold));
@@ -345,9 +346,11 @@ extern "C" int lbm_create_params(const lbm_grid* grid, int lattice, const lbm_pa
     char* base = static_cast<char*>(c->arena);
     c->dev.precision = o.precision;
     c->dev.Q = lattice;
+    const bool dev16 = o.precision == LBM_FP16_DEV || o.precision == LBM_BF16_DEV;
     for (int b = 0; b < 2; ++b) {
         c->dev.F[b] = base + L.F[b];
         c->dev.G[b] = base + L.G[b];
+        c->dev.T[b] = dev16 ? base + L.T[b] : nullptr;
     }
     c->dev.snap = base + L.snap;
     c->dev.staging = reinterpret_cast<double*>(base + L.staging);
@@ -483,20 +486,34 @@ static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const d
     using real = typename Storage<S>::real;
     const ParamsOf<S> p = dev_params<real>(c);
     const int64_t n = c->ncell;
+    const bool upload = fin || gin;
+    float* Tn = static_cast<float*>(c->dev.T[c->cur]);  // 16-bit forms only, else NULL
+    if (upload && Storage<S>::deviation) {
+        // the node temperatures the thermal deviations will refer to: T = sum_a g_a
+        for (int a = 0; a < c->Q; ++a) {
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dev.staging, gin + (int64_t)a * n, n * sizeof(double),
+                                            cudaMemcpyHostToDevice, c->stream));
+            CUDA_OR_FAIL(c, launch_accumulate_T(Tn, c->dev.staging, n, a == 0, c->stream));
+            int rc = wait_stream(c);
+            if (rc != LBM_OK) return rc;
+        }
+    }
     for (int side = 0; side < 2; ++side) {
         const int q = side == 0 ? 15 : c->Q;
         S* dev = static_cast<S*>(side == 0 ? c->dev.F[c->cur] : c->dev.G[c->cur]);
+        // stored-value offset: flow w_a; thermal w^phi_a times the node temperature
+        const float* Tplane = side == 1 ? Tn : nullptr;
         for (int a = 0; a < q; ++a) {
             S* plane = dev + (int64_t)a * c->plane;
-            const double offset = (double)(side == 0 ? p.wf[a] : p.wt[a]);
-            if (fin || gin) {  // host -> device
+            const double offset = (double)(side == 0 ? p.wf[a] : p.wg[a]);
+            if (upload) {  // host -> device
                 const double* src = (side == 0 ? fin : gin) + (int64_t)a * n;
                 CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dev.staging, src, n * sizeof(double),
                                                 cudaMemcpyHostToDevice, c->stream));
-                CUDA_OR_FAIL(c, launch_to_storage<S>(plane, c->dev.staging, n, offset, c->stream));
+                CUDA_OR_FAIL(c, launch_to_storage<S>(plane, c->dev.staging, n, offset, Tplane, c->stream));
             } else {  // device -> host
                 double* dst = (side == 0 ? f : g) + (int64_t)a * n;
-                CUDA_OR_FAIL(c, launch_to_double<S>(c->dev.staging, plane, n, offset, c->stream));
+                CUDA_OR_FAIL(c, launch_to_double<S>(c->dev.staging, plane, n, offset, Tplane, c->stream));
                 CUDA_OR_FAIL(c, cudaMemcpyAsync(dst, c->dev.staging, n * sizeof(double),
                                                 cudaMemcpyDeviceToHost, c->stream));
             }
@@ -505,7 +522,7 @@ static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const d
             if (rc != LBM_OK) return rc;
         }
     }
-    if (fin || gin) {
+    if (upload) {
         CUDA_OR_FAIL(c, launch_residual<S>(c->dev, c->cur, p, 0, c->stream));
         c->last_residual = -1.0;
         return wait_stream(c);

@@ -21,9 +21,9 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 
 template <typename S, int Q>
-__global__ void init_kernel(S* __restrict__ F, S* __restrict__ G, ParamsOf<S> p, uint64_t seed,
-                            double amp, double w0, double w1, double w7, double v0, double v1,
-                            double v7) {
+__global__ void init_kernel(S* __restrict__ F, S* __restrict__ G, float* __restrict__ Tn,
+                            ParamsOf<S> p, uint64_t seed, double amp, double w0, double w1,
+                            double w7, double v0, double v1, double v7) {
     using real = typename Storage<S>::real;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= p.ncell) return;
@@ -33,9 +33,15 @@ __global__ void init_kernel(S* __restrict__ F, S* __restrict__ G, ParamsOf<S> p,
 #pragma unroll
     for (int a = 0; a < 15; ++a)
         F[a * p.plane + c] = Storage<S>::store((real)(a == 0 ? w0 : a < 7 ? w1 : w7), p.wf[a]);
+    // 16-bit forms: g is stored as its deviation from w^phi_a T of this node (zero here)
+    real Tref = real(0);
+    if constexpr (Storage<S>::deviation) {
+        Tref = (real)T;
+        Tn[c] = (float)T;
+    }
 #pragma unroll
     for (int a = 0; a < Q; ++a)
-        G[a * p.plane + c] = Storage<S>::store((real)((a == 0 ? v0 : a < 7 ? v1 : v7) * T), p.wt[a]);
+        G[a * p.plane + c] = Storage<S>::store((real)((a == 0 ? v0 : a < 7 ? v1 : v7) * T), p.wg[a] * Tref);
 }
 
 template <typename S>
@@ -58,10 +64,11 @@ cudaError_t launch_init(const DevState& s, const ParamsOf<S>& p, uint64_t seed, 
     const unsigned blocks = (unsigned)((p.ncell + threads - 1) / threads);
     S* F = static_cast<S*>(s.F[0]);
     S* G = static_cast<S*>(s.G[0]);
+    float* Tn = static_cast<float*>(s.T[0]);
     if (s.Q == 15)
-        init_kernel<S, 15><<<blocks, threads, 0, st>>>(F, G, p, seed, amp, w0, w1, w7, v0, v1, v7);
+        init_kernel<S, 15><<<blocks, threads, 0, st>>>(F, G, Tn, p, seed, amp, w0, w1, w7, v0, v1, v7);
     else
-        init_kernel<S, 7><<<blocks, threads, 0, st>>>(F, G, p, seed, amp, w0, w1, w7, v0, v1, v7);
+        init_kernel<S, 7><<<blocks, threads, 0, st>>>(F, G, Tn, p, seed, amp, w0, w1, w7, v0, v1, v7);
     return cudaGetLastError();
 }
 
@@ -70,21 +77,36 @@ cudaError_t launch_init(const DevState& s, const ParamsOf<S>& p, uint64_t seed, 
 // transfers stage FP64 planes).  The 16-bit forms encode and decode exactly as the step
 // kernel does (FP32 offset arithmetic), so set(get(state)) restores the FP16 state.
 // ---------------------------------------------------------------------------------
+// offset of node c: `offset` (flow planes), or `offset` * Tn[c] (thermal planes of the
+// 16-bit forms, offset = w^phi_a)
+template <typename S>
+__device__ __forceinline__ typename Storage<S>::real conv_offset(double offset,
+                                                                 const float* __restrict__ Tn,
+                                                                 int64_t c) {
+    using real = typename Storage<S>::real;
+    return Tn ? (real)offset * Tn[c] : (real)offset;
+}
 template <typename S>
 __global__ void to_storage_kernel(S* __restrict__ dst, const double* __restrict__ src, int64_t n,
-                                  double offset) {
+                                  double offset, const float* __restrict__ Tn) {
     using real = typename Storage<S>::real;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x)
-        dst[c] = Storage<S>::store((real)src[c], (real)offset);
+        dst[c] = Storage<S>::store((real)src[c], conv_offset<S>(offset, Tn, c));
 }
 template <typename S>
 __global__ void to_double_kernel(double* __restrict__ dst, const S* __restrict__ src, int64_t n,
-                                 double offset) {
-    using real = typename Storage<S>::real;
+                                 double offset, const float* __restrict__ Tn) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x)
-        dst[c] = (double)Storage<S>::load(src[c], (real)offset);
+        dst[c] = (double)Storage<S>::load(src[c], conv_offset<S>(offset, Tn, c));
+}
+// Tn[c] (+)= (float) src[c]: the node temperature of a state being uploaded (16-bit forms)
+__global__ void accumulate_T_kernel(float* __restrict__ Tn, const double* __restrict__ src,
+                                    int64_t n, int first) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x)
+        Tn[c] = first ? (float)src[c] : Tn[c] + (float)src[c];
 }
 
 static unsigned grid_for(int64_t n, int threads) {
@@ -95,13 +117,19 @@ static unsigned grid_for(int64_t n, int threads) {
 }
 
 template <typename S>
-cudaError_t launch_to_storage(S* dst, const double* src, int64_t n, double offset, cudaStream_t st) {
-    to_storage_kernel<S><<<grid_for(n, 256), 256, 0, st>>>(dst, src, n, offset);
+cudaError_t launch_to_storage(S* dst, const double* src, int64_t n, double offset, const float* Tn,
+                              cudaStream_t st) {
+    to_storage_kernel<S><<<grid_for(n, 256), 256, 0, st>>>(dst, src, n, offset, Tn);
     return cudaGetLastError();
 }
 template <typename S>
-cudaError_t launch_to_double(double* dst, const S* src, int64_t n, double offset, cudaStream_t st) {
-    to_double_kernel<S><<<grid_for(n, 256), 256, 0, st>>>(dst, src, n, offset);
+cudaError_t launch_to_double(double* dst, const S* src, int64_t n, double offset, const float* Tn,
+                             cudaStream_t st) {
+    to_double_kernel<S><<<grid_for(n, 256), 256, 0, st>>>(dst, src, n, offset, Tn);
+    return cudaGetLastError();
+}
+cudaError_t launch_accumulate_T(float* Tn, const double* src, int64_t n, int first, cudaStream_t st) {
+    accumulate_T_kernel<<<grid_for(n, 256), 256, 0, st>>>(Tn, src, n, first);
     return cudaGetLastError();
 }
 
@@ -109,8 +137,18 @@ cudaError_t launch_to_double(double* dst, const S* src, int64_t n, double offset
 // Macroscopic fields of the stored (post-collision) state: rho = sum f, T = sum g,
 // rho u = sum f e - F/2 (collision added F to the momentum, Eq. 2a), in FP64.
 // ---------------------------------------------------------------------------------
+// stored thermal population a of node c, decoded
+template <typename S>
+__device__ __forceinline__ double thermal_value(const S* __restrict__ G, const float* __restrict__ Tn,
+                                                const ParamsOf<S>& p, int a, int64_t c) {
+    typename Storage<S>::real off = 0;
+    if constexpr (Storage<S>::deviation) off = p.wg[a] * Tn[c];
+    return (double)Storage<S>::load(G[a * p.plane + c], off);
+}
+
 template <typename S, int Q>
 __device__ __forceinline__ void node_macro(const S* __restrict__ F, const S* __restrict__ G,
+                                           const float* __restrict__ Tn,
                                            const ParamsOf<S>& p, int64_t c, double& rho,
                                            double& ux, double& uy, double& uz, double& T) {
     double r = 0, jx = 0, jy = 0, jz = 0, t = 0;
@@ -123,7 +161,7 @@ __device__ __forceinline__ void node_macro(const S* __restrict__ F, const S* __r
         jz += ez(a) * v;
     }
 #pragma unroll
-    for (int a = 0; a < Q; ++a) t += (double)Storage<S>::load(G[a * p.plane + c], p.wt[a]);
+    for (int a = 0; a < Q; ++a) t += thermal_value<S>(G, Tn, p, a, c);
     const double Fz = (double)p.ext_fz + (double)p.gbeta * (t - (double)p.T0);
     rho = r;
     ux = (jx - 0.5 * (double)p.ext_fx) / r;
@@ -133,12 +171,13 @@ __device__ __forceinline__ void node_macro(const S* __restrict__ F, const S* __r
 }
 
 template <typename S, int Q>
-__global__ void field_kernel(const S* __restrict__ F, const S* __restrict__ G, ParamsOf<S> p,
-                             int which, double* __restrict__ out) {
+__global__ void field_kernel(const S* __restrict__ F, const S* __restrict__ G,
+                             const float* __restrict__ Tn, ParamsOf<S> p, int which,
+                             double* __restrict__ out) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < p.ncell;
          c += (int64_t)gridDim.x * blockDim.x) {
         double rho, ux, uy, uz, T;
-        node_macro<S, Q>(F, G, p, c, rho, ux, uy, uz, T);
+        node_macro<S, Q>(F, G, Tn, p, c, rho, ux, uy, uz, T);
         out[c] = which == 0 ? rho : which == 1 ? ux : which == 2 ? uy : which == 3 ? uz : T;
     }
 }
@@ -148,10 +187,11 @@ cudaError_t launch_field(const DevState& s, int cur, const ParamsOf<S>& p, int w
                          cudaStream_t st) {
     const S* F = static_cast<const S*>(s.F[cur]);
     const S* G = static_cast<const S*>(s.G[cur]);
+    const float* Tn = static_cast<const float*>(s.T[cur]);
     if (s.Q == 15)
-        field_kernel<S, 15><<<grid_for(p.ncell, 256), 256, 0, st>>>(F, G, p, which, s.staging);
+        field_kernel<S, 15><<<grid_for(p.ncell, 256), 256, 0, st>>>(F, G, Tn, p, which, s.staging);
     else
-        field_kernel<S, 7><<<grid_for(p.ncell, 256), 256, 0, st>>>(F, G, p, which, s.staging);
+        field_kernel<S, 7><<<grid_for(p.ncell, 256), 256, 0, st>>>(F, G, Tn, p, which, s.staging);
     return cudaGetLastError();
 }
 
@@ -187,6 +227,7 @@ __device__ __forceinline__ void warp_argmax(double& v, int& idx) {
 // ---------------------------------------------------------------------------------
 template <typename S, int Q>
 __global__ void __launch_bounds__(256) residual_kernel(const S* __restrict__ G,
+                                                       const float* __restrict__ Tn,
                                                        typename Storage<S>::real* __restrict__ snap,
                                                        ParamsOf<S> p, int record,
                                                        unsigned long long* __restrict__ max_bits,
@@ -198,7 +239,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const S* __restrict__ G,
          c += (int64_t)gridDim.x * blockDim.x) {
         real T = real(0);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) T += Storage<S>::load(G[a * p.plane + c], p.wt[a]);
+        for (int a = 0; a < Q; ++a) T += (real)thermal_value<S>(G, Tn, p, a, c);
         if (!isfinite(T)) bad = 1;
         const double d = fabs((double)T - (double)snap[c]);
         if (d > local) local = d;
@@ -224,12 +265,13 @@ cudaError_t launch_residual(const DevState& s, int cur, const ParamsOf<S>& p, in
                             cudaStream_t st) {
     using real = typename Storage<S>::real;
     const S* G = static_cast<const S*>(s.G[cur]);
+    const float* Tn = static_cast<const float*>(s.T[cur]);
     real* snap = static_cast<real*>(s.snap);
     const unsigned blocks = grid_for(p.ncell, 256) > 152 * 8 ? 152 * 8 : grid_for(p.ncell, 256);
     if (s.Q == 15)
-        residual_kernel<S, 15><<<blocks, 256, 0, st>>>(G, snap, p, record, s.resid_bits, s.nonfinite);
+        residual_kernel<S, 15><<<blocks, 256, 0, st>>>(G, Tn, snap, p, record, s.resid_bits, s.nonfinite);
     else
-        residual_kernel<S, 7><<<blocks, 256, 0, st>>>(G, snap, p, record, s.resid_bits, s.nonfinite);
+        residual_kernel<S, 7><<<blocks, 256, 0, st>>>(G, Tn, snap, p, record, s.resid_bits, s.nonfinite);
     return cudaGetLastError();
 }
 
@@ -241,17 +283,18 @@ cudaError_t launch_residual(const DevState& s, int cur, const ParamsOf<S>& p, in
 // vertical centreline and |u_z|(x) on the horizontal centreline.
 // ---------------------------------------------------------------------------------
 template <typename S, int Q>
-__device__ __forceinline__ double node_T(const S* __restrict__ G, const ParamsOf<S>& p, int i,
-                                         int j, int k) {
+__device__ __forceinline__ double node_T(const S* __restrict__ G, const float* __restrict__ Tn,
+                                         const ParamsOf<S>& p, int i, int j, int k) {
     const int64_t c = ((int64_t)k * p.ny + j) * p.nx + i;
     double t = 0.0;
 #pragma unroll
-    for (int a = 0; a < Q; ++a) t += (double)Storage<S>::load(G[a * p.plane + c], p.wt[a]);
+    for (int a = 0; a < Q; ++a) t += thermal_value<S>(G, Tn, p, a, c);
     return t;
 }
 
 template <typename S, int Q>
 __global__ void __launch_bounds__(256) nusselt_faces_kernel(const S* __restrict__ G,
+                                                            const float* __restrict__ Tn,
                                                             ParamsOf<S> p,
                                                             double* __restrict__ partials) {
     const double L = p.nx, dT = (double)p.T_hot - (double)p.T_cold;
@@ -260,10 +303,10 @@ __global__ void __launch_bounds__(256) nusselt_faces_kernel(const S* __restrict_
     for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nface;
          f += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(f % p.ny), k = (int)(f / p.ny);
-        const double th1 = node_T<S, Q>(G, p, p.nx - 1, j, k);
-        const double th2 = node_T<S, Q>(G, p, p.nx - 2, j, k);
-        const double tc1 = node_T<S, Q>(G, p, 0, j, k);
-        const double tc2 = node_T<S, Q>(G, p, 1, j, k);
+        const double th1 = node_T<S, Q>(G, Tn, p, p.nx - 1, j, k);
+        const double th2 = node_T<S, Q>(G, Tn, p, p.nx - 2, j, k);
+        const double tc1 = node_T<S, Q>(G, Tn, p, 0, j, k);
+        const double tc2 = node_T<S, Q>(G, Tn, p, 1, j, k);
         hot += -L * (9.0 * th1 - th2 - 8.0 * (double)p.T_hot) / (3.0 * dT);
         cold += L * (9.0 * tc1 - tc2 - 8.0 * (double)p.T_cold) / (3.0 * dT);
     }
@@ -284,6 +327,7 @@ __global__ void __launch_bounds__(256) nusselt_faces_kernel(const S* __restrict_
 template <typename S, int Q>
 __global__ void __launch_bounds__(256) nusselt_lines_kernel(const S* __restrict__ F,
                                                             const S* __restrict__ G,
+                                                            const float* __restrict__ Tn,
                                                             ParamsOf<S> p, int nblocks,
                                                             double U0,
                                                             const double* __restrict__ partials,
@@ -298,8 +342,8 @@ __global__ void __launch_bounds__(256) nusselt_lines_kernel(const S* __restrict_
     double umax = -1.0, wmax = -1.0;
     int kum = 0x7fffffff, iwm = 0x7fffffff;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-        const double t1 = 0.5 * (node_T<S, Q>(G, p, nx - 1, j0, k) + node_T<S, Q>(G, p, nx - 1, j1, k));
-        const double t2 = 0.5 * (node_T<S, Q>(G, p, nx - 2, j0, k) + node_T<S, Q>(G, p, nx - 2, j1, k));
+        const double t1 = 0.5 * (node_T<S, Q>(G, Tn, p, nx - 1, j0, k) + node_T<S, Q>(G, Tn, p, nx - 1, j1, k));
+        const double t2 = 0.5 * (node_T<S, Q>(G, Tn, p, nx - 2, j0, k) + node_T<S, Q>(G, Tn, p, nx - 2, j1, k));
         const double nu = -L * (9.0 * t1 - t2 - 8.0 * (double)p.T_hot) / (3.0 * dT);
         nsum += nu;
         argmax_combine(nmax, kmax, nu, k);
@@ -308,7 +352,7 @@ __global__ void __launch_bounds__(256) nusselt_lines_kernel(const S* __restrict_
         const int is[2] = {i0, i1}, js[2] = {j0, j1};
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) {
-                node_macro<S, Q>(F, G, p, ((int64_t)k * ny + js[b]) * nx + is[a], r, ux, uy, uz, T);
+                node_macro<S, Q>(F, G, Tn, p, ((int64_t)k * ny + js[b]) * nx + is[a], r, ux, uy, uz, T);
                 acc += ux;
             }
         argmax_combine(umax, kum, fabs(0.25 * acc), k);
@@ -318,7 +362,7 @@ __global__ void __launch_bounds__(256) nusselt_lines_kernel(const S* __restrict_
         const int js[2] = {j0, j1}, ks[2] = {k0, k1};
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) {
-                node_macro<S, Q>(F, G, p, ((int64_t)ks[b] * ny + js[a]) * nx + i, r, ux, uy, uz, T);
+                node_macro<S, Q>(F, G, Tn, p, ((int64_t)ks[b] * ny + js[a]) * nx + i, r, ux, uy, uz, T);
                 acc += uz;
             }
         argmax_combine(wmax, iwm, fabs(0.25 * acc), i);
@@ -378,15 +422,16 @@ cudaError_t launch_nusselt(const DevState& s, int cur, const ParamsOf<S>& p, dou
                            cudaStream_t st) {
     const S* F = static_cast<const S*>(s.F[cur]);
     const S* G = static_cast<const S*>(s.G[cur]);
+    const float* Tn = static_cast<const float*>(s.T[cur]);
     int64_t nface = (int64_t)p.ny * p.nz;
     int blocks = (int)((nface + 255) / 256);
     if (blocks > kPartialBlocks) blocks = kPartialBlocks;
     if (s.Q == 15) {
-        nusselt_faces_kernel<S, 15><<<blocks, 256, 0, st>>>(G, p, s.partials);
-        nusselt_lines_kernel<S, 15><<<1, 256, 0, st>>>(F, G, p, blocks, U0, s.partials, s.result);
+        nusselt_faces_kernel<S, 15><<<blocks, 256, 0, st>>>(G, Tn, p, s.partials);
+        nusselt_lines_kernel<S, 15><<<1, 256, 0, st>>>(F, G, Tn, p, blocks, U0, s.partials, s.result);
     } else {
-        nusselt_faces_kernel<S, 7><<<blocks, 256, 0, st>>>(G, p, s.partials);
-        nusselt_lines_kernel<S, 7><<<1, 256, 0, st>>>(F, G, p, blocks, U0, s.partials, s.result);
+        nusselt_faces_kernel<S, 7><<<blocks, 256, 0, st>>>(G, Tn, p, s.partials);
+        nusselt_lines_kernel<S, 7><<<1, 256, 0, st>>>(F, G, Tn, p, blocks, U0, s.partials, s.result);
     }
     return cudaGetLastError();
 }
@@ -395,12 +440,13 @@ template <typename S>
 cudaError_t launch_nusselt_into(const S* F, const S* G, const ParamsOf<S>& p, double U0,
                                 int Q, int blocks, double* partials, double* result,
                                 cudaStream_t st) {
+    // FP32 / FP64 only: no node-temperature plane
     if (Q == 15) {
-        nusselt_faces_kernel<S, 15><<<blocks, 256, 0, st>>>(G, p, partials);
-        nusselt_lines_kernel<S, 15><<<1, 256, 0, st>>>(F, G, p, blocks, U0, partials, result);
+        nusselt_faces_kernel<S, 15><<<blocks, 256, 0, st>>>(G, nullptr, p, partials);
+        nusselt_lines_kernel<S, 15><<<1, 256, 0, st>>>(F, G, nullptr, p, blocks, U0, partials, result);
     } else {
-        nusselt_faces_kernel<S, 7><<<blocks, 256, 0, st>>>(G, p, partials);
-        nusselt_lines_kernel<S, 7><<<1, 256, 0, st>>>(F, G, p, blocks, U0, partials, result);
+        nusselt_faces_kernel<S, 7><<<blocks, 256, 0, st>>>(G, nullptr, p, partials);
+        nusselt_lines_kernel<S, 7><<<1, 256, 0, st>>>(F, G, nullptr, p, blocks, U0, partials, result);
     }
     return cudaGetLastError();
 }
@@ -408,8 +454,10 @@ cudaError_t launch_nusselt_into(const S* F, const S* G, const ParamsOf<S>& p, do
 #define LBM_INSTANTIATE(S)                                                                         \
     template cudaError_t launch_init<S>(const DevState&, const ParamsOf<S>&, uint64_t, double,      \
                                         cudaStream_t);                                             \
-    template cudaError_t launch_to_storage<S>(S*, const double*, int64_t, double, cudaStream_t);    \
-    template cudaError_t launch_to_double<S>(double*, const S*, int64_t, double, cudaStream_t);     \
+    template cudaError_t launch_to_storage<S>(S*, const double*, int64_t, double, const float*,     \
+                                              cudaStream_t);                                       \
+    template cudaError_t launch_to_double<S>(double*, const S*, int64_t, double, const float*,      \
+                                             cudaStream_t);                                        \
     template cudaError_t launch_field<S>(const DevState&, int, const ParamsOf<S>&, int,             \
                                          cudaStream_t);                                            \
     template cudaError_t launch_residual<S>(const DevState&, int, const ParamsOf<S>&, int,          \

@@ -15,7 +15,6 @@ struct DevParams {
     real om_g[15];      // thermal relaxation rates (Sec. 2.2 / App. C)
     real wg[15];        // thermal rest weights w^phi_a (anti-bounce-back)
     real wf[15];        // stored-value offsets of the flow populations (16-bit forms: w_a)
-    real wt[15];        // stored-value offsets of the scalar populations (w^phi_a T0)
     real gbeta, T0, T_hot, T_cold, cs2_phi;
     real ext_fx, ext_fy, ext_fz;
     int e4_mode, adiabatic_mode, boundary;
@@ -30,6 +29,7 @@ struct DevState {
     int Q;              // 15 or 7
     void* F[2];
     void* G[2];
+    void* T[2];         // 16-bit forms: FP32 node temperature the thermal deviations refer to
     void* snap;         // temperature snapshot for the residual
     double* staging;    // one plane of doubles
     double* partials;   // per-block reduction partials
@@ -54,10 +54,15 @@ cudaError_t launch_init(const DevState& s, const ParamsOf<S>& p, uint64_t seed, 
                         cudaStream_t st);
 // one population plane between FP64 host values and storage (offset: that plane's
 // stored-value offset, used by the 16-bit forms)
+// (thermal planes of the 16-bit forms: offset = w^phi_a and Tn the node temperatures)
 template <typename S>
-cudaError_t launch_to_storage(S* dst, const double* src, int64_t n, double offset, cudaStream_t st);
+cudaError_t launch_to_storage(S* dst, const double* src, int64_t n, double offset, const float* Tn,
+                              cudaStream_t st);
 template <typename S>
-cudaError_t launch_to_double(double* dst, const S* src, int64_t n, double offset, cudaStream_t st);
+cudaError_t launch_to_double(double* dst, const S* src, int64_t n, double offset, const float* Tn,
+                             cudaStream_t st);
+// Tn = src (first) or Tn += src, in FP32: node temperatures of an uploaded state
+cudaError_t launch_accumulate_T(float* Tn, const double* src, int64_t n, int first, cudaStream_t st);
 template <typename S>
 cudaError_t launch_field(const DevState& s, int cur, const ParamsOf<S>& p, int which,
                          cudaStream_t st);

@@ -10,7 +10,11 @@
 // Memory layout: structure of arrays, population a of node c at a * plane + c with
 // c = (k * ny + j) * nx + i; consecutive threads own consecutive x, so every load and
 // store of a warp is one contiguous run (shifted by at most one element for e_x != 0).
-// S is the storage type (storage.cuh); arithmetic is Storage<S>::real.
+// S is the storage type (storage.cuh); arithmetic is Storage<S>::real.  In the 16-bit
+// forms a thermal population is stored as its deviation from w^phi_a T_node, where
+// T_node is the temperature of the node that holds it (kept in an FP32 plane, Tin /
+// Tout): the pull adds w^phi_a T of the source node back, the store subtracts
+// w^phi_a T of this node.
 #include "collide.cuh"
 #include "internal.h"
 #include "lattice.cuh"
@@ -26,9 +30,19 @@ __device__ __forceinline__ int wrap_axis(int s, int n, bool periodic) {
     return s;
 }
 
+// Offset a stored thermal population of node `node` decodes with (16-bit forms).
+template <typename S>
+__device__ __forceinline__ typename Storage<S>::real thermal_offset(const float* __restrict__ Tin,
+                                                                    const ParamsOf<S>& p, int a,
+                                                                    int64_t node) {
+    if constexpr (Storage<S>::deviation) return p.wg[a] * Tin[node];
+    else return typename Storage<S>::real(0);
+}
+
 // Pull of every link with the general wall rules (any boundary mode).
 template <typename S, int Q>
 __device__ __forceinline__ void pull(const S* __restrict__ Fin, const S* __restrict__ Gin,
+                                     const float* __restrict__ Tin,
                                      const ParamsOf<S>& p, int i, int j, int k, int64_t c,
                                      typename Storage<S>::real (&f)[15],
                                      typename Storage<S>::real (&g)[Q]) {
@@ -55,11 +69,12 @@ __device__ __forceinline__ void pull(const S* __restrict__ Fin, const S* __restr
         }
         if (a < Q) {
             if (in_x && in_y && in_z) {
-                g[a] = St::load(Gin[a * P + s], p.wt[a]);
+                g[a] = St::load(Gin[a * P + s], thermal_offset<S>(Tin, p, a, s));
             } else if (x_dirichlet && !in_x) {
                 // Dirichlet T: anti-bounce-back with the face temperature
                 const real Tw = si < 0 ? p.T_cold : p.T_hot;
-                g[a] = -St::load(Gin[opp(a) * P + c], p.wt[a]) + real(2) * p.wg[a] * Tw;
+                g[a] = -St::load(Gin[opp(a) * P + c], thermal_offset<S>(Tin, p, a, c)) +
+                       real(2) * p.wg[a] * Tw;
             } else if (p.adiabatic_mode == 1) {
                 // adiabatic, specular: mirror the crossed components; the population is
                 // the one that left toward the wall from the mirrored source node
@@ -68,9 +83,11 @@ __device__ __forceinline__ void pull(const S* __restrict__ Fin, const S* __restr
                 if (!in_y) { dj = -dj; rj = j; }
                 if (!in_z) { dk = -dk; rk = k; }
                 const int b = dir_index(di, dj, dk);
-                g[a] = St::load(Gin[b * P + ((int64_t)rk * ny + rj) * nx + ri], p.wt[a]);
+                const int64_t r = ((int64_t)rk * ny + rj) * nx + ri;
+                g[a] = St::load(Gin[b * P + r], thermal_offset<S>(Tin, p, a, r));
             } else {
-                g[a] = St::load(Gin[opp(a) * P + c], p.wt[a]);  // adiabatic, bounce-back
+                // adiabatic, bounce-back
+                g[a] = St::load(Gin[opp(a) * P + c], thermal_offset<S>(Tin, p, a, c));
             }
         }
     }
@@ -81,6 +98,7 @@ template <typename S, int Q>
 __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15],
                                               typename Storage<S>::real (&g)[Q],
                                               S* __restrict__ Fout, S* __restrict__ Gout,
+                                              float* __restrict__ Tout,
                                               const ParamsOf<S>& p, int64_t c) {
     using real = typename Storage<S>::real;
     using St = Storage<S>;
@@ -95,16 +113,22 @@ __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15]
     for (int a = 0; a < 15; ++a) Fout[a * P + c] = St::store(f[a], p.wf[a]);
     if constexpr (Q == 15) collide_thermal15<real>(g, ux, uy, uz, p);
     else collide_thermal7<real>(g, ux, uy, uz, p);
+    if constexpr (St::deviation) Tout[c] = T;  // collision conserves T: the node's reference
 #pragma unroll
-    for (int a = 0; a < Q; ++a) Gout[a * P + c] = St::store(g[a], p.wt[a]);
+    for (int a = 0; a < Q; ++a) {
+        real off = real(0);
+        if constexpr (St::deviation) off = p.wg[a] * T;
+        Gout[a * P + c] = St::store(g[a], off);
+    }
 }
 
 // Generic kernel: one thread per node of the flattened grid, any boundary mode.
 template <typename S, int Q>
 __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ Fin,
                                                    const S* __restrict__ Gin,
-                                                   S* __restrict__ Fout,
-                                                   S* __restrict__ Gout, ParamsOf<S> p) {
+                                                   const float* __restrict__ Tin,
+                                                   S* __restrict__ Fout, S* __restrict__ Gout,
+                                                   float* __restrict__ Tout, ParamsOf<S> p) {
     using real = typename Storage<S>::real;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= p.ncell) return;
@@ -113,8 +137,8 @@ __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ Fin,
     const int j = (int)(t % p.ny);
     const int k = (int)(t / p.ny);
     real f[15], g[Q];
-    pull<S, Q>(Fin, Gin, p, i, j, k, c, f, g);
-    collide_store<S, Q>(f, g, Fout, Gout, p, c);
+    pull<S, Q>(Fin, Gin, Tin, p, i, j, k, c, f, g);
+    collide_store<S, Q>(f, g, Fout, Gout, Tout, p, c);
 }
 
 // ---------------------------------------------------------------------------------
@@ -127,7 +151,8 @@ __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ Fin,
 // ---------------------------------------------------------------------------------
 template <typename S, int Q, bool INTERIOR>
 __device__ __forceinline__ void cavity_node(const S* __restrict__ Fin, const S* __restrict__ Gin,
-                                            S* __restrict__ Fout, S* __restrict__ Gout,
+                                            const float* __restrict__ Tin, S* __restrict__ Fout,
+                                            S* __restrict__ Gout, float* __restrict__ Tout,
                                             const ParamsOf<S>& p, int i, int j, int k) {
     using real = typename Storage<S>::real;
     using St = Storage<S>;
@@ -143,7 +168,7 @@ __device__ __forceinline__ void cavity_node(const S* __restrict__ Fin, const S* 
             const int64_t shift = ex(a) + ey(a) * (int64_t)nx + ez(a) * nxy;
             const bool out = (ex(a) > 0 && lo) || (ex(a) < 0 && hi);
             const int64_t off = out ? (int64_t)opp(a) * P : (int64_t)a * P - shift;
-            const real v = St::load(Gin[c + off], p.wt[a]);
+            const real v = St::load(Gin[c + off], thermal_offset<S>(Tin, p, a, out ? c : c - shift));
             // Dirichlet face: anti-bounce-back with the face temperature
             const real Tw = ex(a) > 0 ? p.T_cold : p.T_hot;
             g[a] = out ? (real(2) * p.wg[a] * Tw - v) : v;
@@ -156,9 +181,9 @@ __device__ __forceinline__ void cavity_node(const S* __restrict__ Fin, const S* 
             f[a] = St::load(Fin[c + off], p.wf[a]);
         }
     } else {
-        pull<S, Q>(Fin, Gin, p, i, j, k, c, f, g);
+        pull<S, Q>(Fin, Gin, Tin, p, i, j, k, c, f, g);
     }
-    collide_store<S, Q>(f, g, Fout, Gout, p, c);
+    collide_store<S, Q>(f, g, Fout, Gout, Tout, p, c);
 }
 
 // Blocks per SM the single-precision kernels are built for: 7 for D3Q15 (at most 72
@@ -172,13 +197,14 @@ constexpr int cavity_min_blocks() {
 template <typename S, int Q>
 __global__ void __launch_bounds__(128, (cavity_min_blocks<S, Q>()))
     step_cavity_kernel(const S* __restrict__ Fin, const S* __restrict__ Gin,
-                       S* __restrict__ Fout, S* __restrict__ Gout, ParamsOf<S> p) {
+                       const float* __restrict__ Tin, S* __restrict__ Fout,
+                       S* __restrict__ Gout, float* __restrict__ Tout, ParamsOf<S> p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
     if (i >= p.nx) return;
     const bool interior = j >= 1 && j + 1 < p.ny && k >= 1 && k + 1 < p.nz;
-    if (interior) cavity_node<S, Q, true>(Fin, Gin, Fout, Gout, p, i, j, k);
-    else cavity_node<S, Q, false>(Fin, Gin, Fout, Gout, p, i, j, k);
+    if (interior) cavity_node<S, Q, true>(Fin, Gin, Tin, Fout, Gout, Tout, p, i, j, k);
+    else cavity_node<S, Q, false>(Fin, Gin, Tin, Fout, Gout, Tout, p, i, j, k);
 }
 
 template <typename S>
@@ -187,21 +213,23 @@ cudaError_t launch_step(const DevState& s, int cur, const ParamsOf<S>& p, cudaSt
     const S* Gin = static_cast<const S*>(s.G[cur]);
     S* Fout = static_cast<S*>(s.F[cur ^ 1]);
     S* Gout = static_cast<S*>(s.G[cur ^ 1]);
+    const float* Tin = static_cast<const float*>(s.T[cur]);
+    float* Tout = static_cast<float*>(s.T[cur ^ 1]);
     if (p.boundary == 0 && p.ny <= 65535 && p.nz <= 65535) {
         const int bx = 128;
         const dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
         if (s.Q == 15)
-            step_cavity_kernel<S, 15><<<grid, bx, 0, st>>>(Fin, Gin, Fout, Gout, p);
+            step_cavity_kernel<S, 15><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
         else
-            step_cavity_kernel<S, 7><<<grid, bx, 0, st>>>(Fin, Gin, Fout, Gout, p);
+            step_cavity_kernel<S, 7><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
         return cudaGetLastError();
     }
     const int threads = 256;
     const int64_t blocks = (p.ncell + threads - 1) / threads;
     if (s.Q == 15)
-        step_kernel<S, 15><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Fout, Gout, p);
+        step_kernel<S, 15><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
     else
-        step_kernel<S, 7><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Fout, Gout, p);
+        step_kernel<S, 7><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
     return cudaGetLastError();
 }
 
