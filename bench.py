@@ -28,9 +28,10 @@ if ROOT not in sys.path:
 METRIC = "coupled MLUPS & % HBM roofline; time-to-steady Nu at Ra=1e5 vs plain FP32"
 N_GRID, RA, PR, U0 = 128, 1e5, 0.71, 0.05
 RESIDUAL_INTERVAL = 100
-# algorithmic bytes per node update: every population read once and written once
+# algorithmic bytes per node update: every population read once and written once; the
+# 16-bit forms also read and write the FP32 node temperature their thermal deviations use
 def bytes_per_node(q, storage_bytes=4):
-    return 2 * (15 + q) * storage_bytes
+    return 2 * (15 + q) * storage_bytes + (2 * 4 if storage_bytes == 2 else 0)
 
 
 BYTES_PER_NODE = {15: bytes_per_node(15), 7: bytes_per_node(7)}
