@@ -33,7 +33,7 @@ class _Problem(ctypes.Structure):
         ("omega_f", ctypes.c_double * 15), ("omega_g", ctypes.c_double * 15),
         ("gbeta", ctypes.c_double), ("T_hot", ctypes.c_double), ("T_cold", ctypes.c_double),
         ("cs2_phi", ctypes.c_double), ("ext_force", ctypes.c_double * 3),
-        ("U0", ctypes.c_double),
+        ("U0", ctypes.c_double), ("heat_source", ctypes.c_double),
     ]
 
 
@@ -52,8 +52,9 @@ def lib():
         _lib = ctypes.CDLL(_build.build())
         L = _lib
         L.orc_collide_flow.argtypes = [_D, _D, _D, ctypes.c_int, _D, _D, _D]
-        L.orc_collide_thermal15.argtypes = [_D, _D, _D, ctypes.c_double, _D]
-        L.orc_collide_thermal7.argtypes = [_D, _D, _D, ctypes.c_double, _D]
+        L.orc_collide_thermal15.argtypes = [_D, _D, _D, ctypes.c_double, ctypes.c_double, _D]
+        L.orc_collide_thermal7.argtypes = [_D, _D, _D, ctypes.c_double, ctypes.c_double, _D]
+        L.orc_scalar_source.argtypes = [ctypes.c_int, ctypes.c_double, _D, _D]
         L.orc_flow_source.argtypes = [_D, _D, _D]
         L.orc_init.argtypes = [ctypes.POINTER(_Problem), ctypes.c_uint64, ctypes.c_double, _D, _D]
         L.orc_step.argtypes = [ctypes.POINTER(_Problem), _D, _D, _D, _D]
@@ -141,14 +142,22 @@ def collide_flow(fbar, F, omega, e4_mode=0):
     return out, float(rho[0]), u
 
 
-def collide_thermal(gbar, u, omega, cs2_phi=1.0 / 3.0):
-    """Sec. 2.2 (15 populations) or Appendix C (7 populations) for one cell."""
+def collide_thermal(gbar, u, omega, cs2_phi=1.0 / 3.0, R=0.0):
+    """Sec. 2.2 (15 populations) or Appendix C (7 populations) for one cell, with the
+    scalar source R of Eq. (4)."""
     gbar = _f64(gbar)
     q = gbar.shape[0]
     out = np.zeros(q)
     fn = lib().orc_collide_thermal15 if q == 15 else lib().orc_collide_thermal7
-    fn(_dp(gbar), _dp(_f64(u)), _dp(_f64(omega)), float(cs2_phi), _dp(out))
+    fn(_dp(gbar), _dp(_f64(u)), _dp(_f64(omega)), float(cs2_phi), float(R), _dp(out))
     return out
+
+
+def scalar_source(q, R, u):
+    """S^phi of Appendix B (q = 15) or C (q = 7)."""
+    S = np.zeros(q)
+    lib().orc_scalar_source(int(q), float(R), _dp(_f64(u)), _dp(S))
+    return S
 
 
 # ----------------------------------------------------------------------------------
@@ -176,10 +185,11 @@ class Problem:
     def __init__(self, nx, ny, nz, q_g=15, boundary=BC_CAVITY, omega_nu=1.0, omega_phi=1.0,
                  gbeta=0.0, T_hot=0.5, T_cold=-0.5, cs2_phi=1.0 / 3.0, e4_mode=0,
                  ext_force=(0.0, 0.0, 0.0), U0=0.0, omega_f=None, omega_g=None,
-                 adiabatic_mode=1):
+                 adiabatic_mode=1, heat_source=0.0):
         self.nx, self.ny, self.nz, self.q_g = int(nx), int(ny), int(nz), int(q_g)
         self.boundary, self.e4_mode = int(boundary), int(e4_mode)
         self.adiabatic_mode = int(adiabatic_mode)
+        self.heat_source = float(heat_source)
         if omega_f is None:
             # App. A: "nu = cs^2 (1/omega_j - 1/2), j = 5..9", counted from 1: the five
             # shear moments g^_4..g^_8; the bulk moment g^_9 and the rest relax at 1
@@ -222,6 +232,7 @@ class Problem:
             p.omega_g[b] = self.omega_g[b]
         p.gbeta, p.T_hot, p.T_cold = self.gbeta, self.T_hot, self.T_cold
         p.cs2_phi, p.U0 = self.cs2_phi, self.U0
+        p.heat_source = self.heat_source
         for d in range(3):
             p.ext_force[d] = self.ext_force[d]
         return p

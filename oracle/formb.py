@@ -50,24 +50,34 @@ def _second_order(k7, k8, k9):
     return 0.5 * (s + k7), 0.5 * (s - k7)
 
 
-def thermal_collide(gbar, u, omega, cs2_phi=CS2):
-    """Scalar collision with R = 0: all moments but the zeroth relax (Sec. 2.2, App. C)."""
+def thermal_collide(gbar, u, omega, cs2_phi=CS2, R=0.0):
+    """Scalar collision with source R (Sec. 2.2, App. C; Eqs. 12-16, 25).  The source's
+    only non-zero central moment is the zeroth, R.  phi = sum gbar + R/2.  The zeroth
+    moment gains R; the first-order moments of gbar relax toward 0; every higher moment
+    of (gbar + S) -- equal to gbar's, since S has no higher central moments -- relaxes
+    toward its equilibrium at phi."""
     gbar = np.asarray(gbar, dtype=np.float64)
     q = gbar.shape[0]
     C = central_matrix(u, q)
     kap = C @ gbar
-    phi = kap[0]
+    phi = kap[0] + 0.5 * R
     eq = np.zeros(q)
-    eq[0] = phi
     if q == 15:
         eq[9] = 3.0 * cs2_phi * phi          # xx + yy + zz -> 3 c_sphi^2 phi
         eq[14] = cs2_phi * cs2_phi * phi     # xxyy -> c_sphi^4 phi
     else:
         eq[6] = 3.0 * cs2_phi * phi
-    om = np.asarray(omega, dtype=np.float64)[:q].copy()
-    om[0] = 0.0  # the scalar is the collision invariant
+    om = np.asarray(omega, dtype=np.float64)[:q]
     post = kap + om * (eq - kap)
+    post[0] = kap[0] + R
     return np.linalg.solve(C, post)
+
+
+def scalar_source(q, R, u):
+    """S whose central moments (the q combinations) are R for the zeroth, 0 otherwise."""
+    G = np.zeros(q)
+    G[0] = R
+    return np.linalg.solve(central_matrix(u, q), G)
 
 
 def source_central_moments(F):

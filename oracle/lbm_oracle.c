@@ -194,6 +194,8 @@ __attribute__((constructor)) static void orc_tables_init(void) {
  * The binomial theorem turns them into raw moments sigma', which are projected on K
  * (m^s_b = <K_b|S>) and inverted through the orthogonality of K, as the paper does
  * for the scalar source (Appendix B). */
+static void source_from_raw15(const double* s, double S[15]);
+
 void orc_flow_source(const double F[3], const double u[3], double S[15]) {
     const double cs2 = 1.0 / 3.0;
     double Fx = F[0], Fy = F[1], Fz = F[2];
@@ -215,8 +217,14 @@ void orc_flow_source(const double F[3], const double u[3], double S[15]) {
     s[MXYZ] = ux * uy * Fz + ux * uz * Fy + uy * uz * Fx;
     s[MXXYY] = 2.0 * cs2 * (ux * Fx + uy * Fy) + 2.0 * ux * uy * uy * Fx + 2.0 * ux * ux * uy * Fy;
 
-    /* Projections on K.  On D3Q15, e_x^3 = e_x, e_x e_z^2 = e_x e_y^2, e_y e_z^2 =
-     * e_x^2 e_y, e_y^2 e_z = e_x^2 e_z and all three products e_i^2 e_j^2 coincide. */
+    source_from_raw15(s, S);
+}
+
+/* S_a = sum_b K_b(a) m^s_b / |K_b|^2 for the raw moments s[] of S (the inversion the
+ * paper uses for the scalar source, Eq. 19 and Appendix B).  The projections m^s_b use
+ * the identities of the D3Q15 lattice: e_x^3 = e_x, e_x e_z^2 = e_x e_y^2, e_y e_z^2 =
+ * e_x^2 e_y, e_y^2 e_z = e_x^2 e_z, and all three products e_i^2 e_j^2 coincide. */
+static void source_from_raw15(const double* s, double S[15]) {
     double m[15];
     m[0] = s[M0];
     m[1] = s[MX];
@@ -238,6 +246,52 @@ void orc_flow_source(const double F[3], const double u[3], double S[15]) {
         double acc = 0.0;
         for (int b = 0; b < 15; ++b) acc += K15[b * 15 + a] * m[b] / NORM15[b];
         S[a] = acc;
+    }
+}
+
+/* Raw moments of the scalar source (Sec. 2.2): its only non-zero central moment is the
+ * zeroth, R (Eq. 16), so by the binomial theorem sigma'_{x^m y^n z^p} = u_x^m u_y^n u_z^p R
+ * (the list printed after Eq. 17). */
+static void scalar_source_raw(double R, const double u[3], double* s) {
+    double ux = u[0], uy = u[1], uz = u[2];
+    s[M0] = R;
+    s[MX] = ux * R;
+    s[MY] = uy * R;
+    s[MZ] = uz * R;
+    s[MXY] = ux * uy * R;
+    s[MXZ] = ux * uz * R;
+    s[MYZ] = uy * uz * R;
+    s[MXX] = ux * ux * R;
+    s[MYY] = uy * uy * R;
+    s[MZZ] = uz * uz * R;
+    s[MXYY] = ux * uy * uy * R;
+    s[MXXY] = ux * ux * uy * R;
+    s[MXXZ] = ux * ux * uz * R;
+    s[MXYZ] = ux * uy * uz * R;
+    s[MXXYY] = ux * ux * uy * uy * R;
+}
+
+/* Scalar source in velocity space, D3Q15 (Appendix B, S^phi = K^-1 m^s) and D3Q7
+ * (Appendix C, rows 3 and 4 with m^s_2 as K^-1 gives, m^s_6 = (7 u^2 - 6) R). */
+void orc_scalar_source(int q, double R, const double u[3], double* S) {
+    double s[NMOM];
+    scalar_source_raw(R, u, s);
+    if (q == 15) {
+        source_from_raw15(s, S);
+    } else {
+        double m[7];
+        m[0] = s[M0];
+        m[1] = s[MX];
+        m[2] = s[MY];
+        m[3] = s[MZ];
+        m[4] = s[MXX] - s[MYY];
+        m[5] = s[MXX] + s[MYY] - 2.0 * s[MZZ];
+        m[6] = 7.0 * (s[MXX] + s[MYY] + s[MZZ]) - 6.0 * s[M0];
+        for (int a = 0; a < 7; ++a) {
+            double acc = 0.0;
+            for (int b = 0; b < 7; ++b) acc += K7[b * 7 + a] * m[b] / NORM7[b];
+            S[a] = acc;
+        }
     }
 }
 
@@ -332,103 +386,113 @@ void orc_collide_flow(const double fbar[15], const double F[3], const double om[
 }
 
 /* ------------------------------------------------------------------------------ */
-/* Thermal collision, D3Q15: Sec. 2.2 (kernel h^_0..h^_14, Eq. 13a), source R = 0.  */
+/* Thermal collision, D3Q15: Sec. 2.2 (kernel h^_0..h^_14, Eq. 13a) with source R.  */
 /* ------------------------------------------------------------------------------ */
 void orc_collide_thermal15(const double gbar[15], const double u[3], const double om[15],
-                           double cs2, double out[15]) {
-    double k[NMOM];
-    raw_moments(gbar, 15, k); /* eta-bar' = kappa-bar' + sigma' with sigma' = 0 (R = 0) */
-    double phi = k[M0];       /* Eq. (25) with R = 0 */
+                           double cs2, double R, double out[15]) {
     double ux = u[0], uy = u[1], uz = u[2];
+    double k[NMOM], sg[NMOM], e[NMOM];
+    raw_moments(gbar, 15, k);      /* kappa-bar' (Eq. 17) */
+    scalar_source_raw(R, u, sg);   /* sigma' */
+    for (int m = 0; m < NMOM; ++m) e[m] = k[m] + sg[m]; /* eta-bar' = kappa-bar' + sigma' (Eq. 21) */
+    double phi = k[M0] + 0.5 * R;  /* Eq. (25) */
+    double pr = phi + 0.5 * R;     /* the (phi + R/2) of the kernel */
     double cs4 = cs2 * cs2;
     double h[15];
     h[0] = 0.0;
-    h[1] = om[1] / 10.0 * (phi * ux - k[MX]);
-    h[2] = om[2] / 10.0 * (phi * uy - k[MY]);
-    h[3] = om[3] / 10.0 * (phi * uz - k[MZ]);
-    h[4] = om[4] / 8.0 * (-k[MXY] + uy * k[MX] + ux * k[MY] - phi * ux * uy) +
+    h[1] = om[1] / 10.0 * (phi * ux - k[MX] - ux * 0.5 * R);
+    h[2] = om[2] / 10.0 * (phi * uy - k[MY] - uy * 0.5 * R);
+    h[3] = om[3] / 10.0 * (phi * uz - k[MZ] - uz * 0.5 * R);
+    h[4] = om[4] / 8.0 * (-e[MXY] + uy * e[MX] + ux * e[MY] - pr * ux * uy) +
            1.25 * (uy * h[1] + ux * h[2]);
-    h[5] = om[5] / 8.0 * (-k[MXZ] + uz * k[MX] + ux * k[MZ] - phi * ux * uz) +
+    h[5] = om[5] / 8.0 * (-e[MXZ] + uz * e[MX] + ux * e[MZ] - pr * ux * uz) +
            1.25 * (uz * h[1] + ux * h[3]);
-    h[6] = om[6] / 8.0 * (-k[MYZ] + uz * k[MY] + uy * k[MZ] - phi * uy * uz) +
+    h[6] = om[6] / 8.0 * (-e[MYZ] + uz * e[MY] + uy * e[MZ] - pr * uy * uz) +
            1.25 * (uz * h[2] + uy * h[3]);
     h[7] = om[7] / 4.0 *
-               (-(k[MXX] - k[MYY]) + 2.0 * (ux * k[MX] - uy * k[MY]) - phi * (ux * ux - uy * uy)) +
+               (-(e[MXX] - e[MYY]) + 2.0 * (ux * e[MX] - uy * e[MY]) - pr * (ux * ux - uy * uy)) +
            5.0 * (ux * h[1] - uy * h[2]);
     h[8] = om[8] / 12.0 *
-               (-(k[MXX] + k[MYY] - 2.0 * k[MZZ]) + 2.0 * (ux * k[MX] + uy * k[MY] - 2.0 * uz * k[MZ]) -
-                phi * (ux * ux + uy * uy - 2.0 * uz * uz)) +
+               (-(e[MXX] + e[MYY] - 2.0 * e[MZZ]) + 2.0 * (ux * e[MX] + uy * e[MY] - 2.0 * uz * e[MZ]) -
+                pr * (ux * ux + uy * uy - 2.0 * uz * uz)) +
            (5.0 / 3.0) * (ux * h[1] + uy * h[2] - 2.0 * uz * h[3]);
     h[9] = om[9] / 18.0 *
-               (3.0 * cs2 * phi - (k[MXX] + k[MYY] + k[MZZ]) +
-                2.0 * (ux * k[MX] + uy * k[MY] + uz * k[MZ]) - phi * (ux * ux + uy * uy + uz * uz)) +
+               (3.0 * cs2 * phi - (e[MXX] + e[MYY] + e[MZZ]) +
+                2.0 * (ux * e[MX] + uy * e[MY] + uz * e[MZ]) - pr * (ux * ux + uy * uy + uz * uz)) +
            (10.0 / 9.0) * (ux * h[1] + uy * h[2] + uz * h[3]);
     h[10] = om[10] / 16.0 *
-                (-k[MXYY] + 2.0 * uy * k[MXY] - uy * uy * k[MX] + ux * k[MYY] -
-                 2.0 * ux * uy * k[MY] + phi * ux * uy * uy) -
+                (-e[MXYY] + 2.0 * uy * e[MXY] - uy * uy * e[MX] + ux * e[MYY] -
+                 2.0 * ux * uy * e[MY] + pr * ux * uy * uy) -
             (0.625 * uy * uy + 0.5) * h[1] - 1.25 * ux * uy * h[2] + uy * h[4] +
             0.125 * ux * (-h[7] + h[8] + 3.0 * h[9]);
     h[11] = om[11] / 16.0 *
-                (-k[MXXY] + 2.0 * ux * k[MXY] + uy * k[MXX] - ux * ux * k[MY] -
-                 2.0 * ux * uy * k[MX] + phi * ux * ux * uy) -
+                (-e[MXXY] + 2.0 * ux * e[MXY] + uy * e[MXX] - ux * ux * e[MY] -
+                 2.0 * ux * uy * e[MX] + pr * ux * ux * uy) -
             1.25 * ux * uy * h[1] - (0.625 * ux * ux + 0.5) * h[2] + ux * h[4] +
             0.125 * uy * (h[7] + h[8] + 3.0 * h[9]);
     h[12] = om[12] / 16.0 *
-                (-k[MXXZ] + 2.0 * ux * k[MXZ] + uz * k[MXX] - 2.0 * ux * uz * k[MX] -
-                 ux * ux * k[MZ] + phi * ux * ux * uz) -
+                (-e[MXXZ] + 2.0 * ux * e[MXZ] + uz * e[MXX] - 2.0 * ux * uz * e[MX] -
+                 ux * ux * e[MZ] + pr * ux * ux * uz) -
             1.25 * ux * uz * h[1] - (0.625 * ux * ux + 0.5) * h[3] + ux * h[5] +
             0.125 * uz * (h[7] + h[8] + 3.0 * h[9]);
     h[13] = om[13] / 8.0 *
-                (-k[MXYZ] + ux * k[MYZ] + uy * k[MXZ] + uz * k[MXY] - uy * uz * k[MX] -
-                 ux * uz * k[MY] - ux * uy * k[MZ] + phi * ux * uy * uz) -
+                (-e[MXYZ] + ux * e[MYZ] + uy * e[MXZ] + uz * e[MXY] - uy * uz * e[MX] -
+                 ux * uz * e[MY] - ux * uy * e[MZ] + pr * ux * uy * uz) -
             1.25 * (uy * uz * h[1] + ux * uz * h[2] + ux * uy * h[3]) + uz * h[4] + uy * h[5] +
             ux * h[6];
     h[14] = om[14] / 16.0 *
-                (-k[MXXYY] + 2.0 * uy * k[MXXY] + 2.0 * ux * k[MXYY] - uy * uy * k[MXX] -
-                 ux * ux * k[MYY] - 4.0 * ux * uy * k[MXY] + 2.0 * ux * uy * uy * k[MX] +
-                 2.0 * ux * ux * uy * k[MY] + cs4 * phi - phi * ux * ux * uy * uy) +
+                (-e[MXXYY] + 2.0 * uy * e[MXXY] + 2.0 * ux * e[MXYY] - uy * uy * e[MXX] -
+                 ux * ux * e[MYY] - 4.0 * ux * uy * e[MXY] + 2.0 * ux * uy * uy * e[MX] +
+                 2.0 * ux * ux * uy * e[MY] + cs4 * phi - pr * ux * ux * uy * uy) +
             1.25 * (ux * uy * uy * h[1] + ux * ux * uy * h[2]) - 2.0 * ux * uy * h[4] +
             0.125 * (ux * ux - uy * uy) * h[7] - 0.125 * (ux * ux + uy * uy) * h[8] -
             (0.375 * (ux * ux + uy * uy) + 0.5) * h[9] + 2.0 * (ux * h[10] + uy * h[11]) +
             uy * h[2] + ux * h[1];
 
-    /* Eq. (13a) with S^phi = 0: g~ = gbar + (K h^). */
+    /* Eq. (13a): g~ = gbar + (K h^) + S^phi. */
+    double S[15];
+    orc_scalar_source(15, R, u, S);
     for (int a = 0; a < 15; ++a) {
         double kh = 0.0;
         for (int b = 0; b < 15; ++b) kh += K15[b * 15 + a] * h[b];
-        out[a] = gbar[a] + kh;
+        out[a] = gbar[a] + kh + S[a];
     }
 }
 
 /* ------------------------------------------------------------------------------ */
-/* Thermal collision, D3Q7: Appendix C (kernel h^_0..h^_6), source R = 0.           */
+/* Thermal collision, D3Q7: Appendix C (kernel h^_0..h^_6) with source R.           */
 /* ------------------------------------------------------------------------------ */
 void orc_collide_thermal7(const double gbar[7], const double u[3], const double om[7],
-                          double cs2, double out[7]) {
-    double k[NMOM];
-    raw_moments(gbar, 7, k);
-    double phi = k[M0];
+                          double cs2, double R, double out[7]) {
     double ux = u[0], uy = u[1], uz = u[2];
+    double k[NMOM], sg[NMOM], e[NMOM];
+    raw_moments(gbar, 7, k);
+    scalar_source_raw(R, u, sg);
+    for (int m = 0; m < NMOM; ++m) e[m] = k[m] + sg[m];
+    double phi = k[M0] + 0.5 * R;
+    double pr = phi + 0.5 * R;
     double h[7];
     h[0] = 0.0; /* the paper prints this line as "h_1 = 0"; h_0 is meant */
-    h[1] = om[1] / 2.0 * (phi * ux - k[MX]);
-    h[2] = om[2] / 2.0 * (phi * uy - k[MY]);
-    h[3] = om[3] / 2.0 * (phi * uz - k[MZ]);
+    h[1] = om[1] / 2.0 * (phi * ux - k[MX] - ux * 0.5 * R);
+    h[2] = om[2] / 2.0 * (phi * uy - k[MY] - uy * 0.5 * R);
+    h[3] = om[3] / 2.0 * (phi * uz - k[MZ] - uz * 0.5 * R);
     h[4] = om[4] / 4.0 *
-               (-(k[MXX] - k[MYY]) + 2.0 * (ux * k[MX] - uy * k[MY]) - phi * (ux * ux - uy * uy)) +
+               (-(e[MXX] - e[MYY]) + 2.0 * (ux * e[MX] - uy * e[MY]) - pr * (ux * ux - uy * uy)) +
            ux * h[1] - uy * h[2];
     h[5] = om[5] / 12.0 *
-               (-(k[MXX] + k[MYY] - 2.0 * k[MZZ]) + 2.0 * (ux * k[MX] + uy * k[MY] - 2.0 * uz * k[MZ]) -
-                phi * (ux * ux + uy * uy - 2.0 * uz * uz)) +
+               (-(e[MXX] + e[MYY] - 2.0 * e[MZZ]) + 2.0 * (ux * e[MX] + uy * e[MY] - 2.0 * uz * e[MZ]) -
+                pr * (ux * ux + uy * uy - 2.0 * uz * uz)) +
            (1.0 / 3.0) * (ux * h[1] + uy * h[2] - 2.0 * uz * h[3]);
     h[6] = om[6] / 6.0 *
-               (3.0 * cs2 * phi - (k[MXX] + k[MYY] + k[MZZ]) +
-                2.0 * (ux * k[MX] + uy * k[MY] + uz * k[MZ]) - phi * (ux * ux + uy * uy + uz * uz)) +
+               (3.0 * cs2 * phi - (e[MXX] + e[MYY] + e[MZZ]) +
+                2.0 * (ux * e[MX] + uy * e[MY] + uz * e[MZ]) - pr * (ux * ux + uy * uy + uz * uz)) +
            (2.0 / 3.0) * (ux * h[1] + uy * h[2] + uz * h[3]);
+    double S[7];
+    orc_scalar_source(7, R, u, S);
     for (int a = 0; a < 7; ++a) {
         double kh = 0.0;
         for (int b = 0; b < 7; ++b) kh += K7[b * 7 + a] * h[b];
-        out[a] = gbar[a] + kh;
+        out[a] = gbar[a] + kh + S[a];
     }
 }
 
@@ -513,18 +577,19 @@ void orc_cell_update(const orc_problem* p, const double* Fin, const double* Gin,
                      int k, double fout[15], double* gout) {
     double fb[15], gb[15];
     pull_cell(p, Fin, Gin, i, j, k, fb, gb);
-    /* Eq. (25) with R = 0: T = sum gbar. */
+    /* Eq. (25): T = sum gbar + R/2. */
     double T = 0.0;
     for (int a = 0; a < p->q_g; ++a) T += gb[a];
+    T += 0.5 * p->heat_source;
     /* Boussinesq force (Sec. 3), reading R8. */
     double T0 = 0.5 * (p->T_hot + p->T_cold);
     double F[3] = {p->ext_force[0], p->ext_force[1], p->ext_force[2] + p->gbeta * (T - T0)};
     double rho, u[3];
     orc_collide_flow(fb, F, p->omega_f, p->e4_mode, fout, &rho, u);
     if (p->q_g == 15)
-        orc_collide_thermal15(gb, u, p->omega_g, p->cs2_phi, gout);
+        orc_collide_thermal15(gb, u, p->omega_g, p->cs2_phi, p->heat_source, gout);
     else
-        orc_collide_thermal7(gb, u, p->omega_g, p->cs2_phi, gout);
+        orc_collide_thermal7(gb, u, p->omega_g, p->cs2_phi, p->heat_source, gout);
 }
 
 int orc_step(const orc_problem* p, const double* Fin, const double* Gin, double* Fout,
@@ -562,7 +627,7 @@ int orc_run(const orc_problem* p, double* F, double* G, double* Fs, double* Gs, 
     return 0;
 }
 
-/* Macroscopic fields of a stored (post-collision) state: rho = sum F, T = sum G and,
+/* Macroscopic fields of a stored (post-collision) state: rho = sum F, T = sum G - R/2 and,
  * because collision adds F to the momentum (Eq. 2a, sum S e = F), rho u = sum F e - F/2
  * reproduces Eq. (3) of the same time level. */
 void orc_fields(const orc_problem* p, const double* F, const double* G, double* rho, double* ux,
@@ -579,6 +644,7 @@ void orc_fields(const orc_problem* p, const double* F, const double* G, double* 
             jz += f * EZ[a];
         }
         for (int a = 0; a < p->q_g; ++a) t += G[(size_t)a * n + c];
+        t -= 0.5 * p->heat_source; /* collision added R: phi = sum g~ - R/2 (Eq. 25) */
         double Fx = p->ext_force[0], Fy = p->ext_force[1];
         double Fz = p->ext_force[2] + p->gbeta * (t - T0);
         if (rho) rho[c] = r;

@@ -43,6 +43,7 @@ typedef struct {
     double cs2_phi;       /* c_{s phi}^2 of the thermal equilibrium (Sec. 2.2) */
     double ext_force[3];  /* extra uniform body force (test problems only; 0 in the cavity) */
     double U0;            /* velocity scale sqrt(g beta dT L) used to report u/U0 */
+    double heat_source;   /* uniform scalar source R of the CDE (Eq. 4); 0 in the cavity */
 } orc_problem;
 
 typedef struct {
@@ -64,9 +65,10 @@ void orc_flow_source(const double F[3], const double u[3], double S[15]);
 void orc_collide_flow(const double fbar[15], const double F[3], const double omega[15],
                       int e4_mode, double out[15], double* rho_out, double u_out[3]);
 void orc_collide_thermal15(const double gbar[15], const double u[3], const double omega[15],
-                           double cs2_phi, double out[15]);
+                           double cs2_phi, double R, double out[15]);
 void orc_collide_thermal7(const double gbar[7], const double u[3], const double omega[7],
-                          double cs2_phi, double out[7]);
+                          double cs2_phi, double R, double out[7]);
+void orc_scalar_source(int q, double R, const double u[3], double* S);
 
 /* Whole-grid operations. */
 void orc_init(const orc_problem* p, uint64_t seed, double noise_amp, double* F, double* G);

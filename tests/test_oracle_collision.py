@@ -53,7 +53,8 @@ def test_flow_source_form_a_equals_form_b_and_moments():
 
 @pytest.mark.parametrize("q", [15, 7])
 @pytest.mark.parametrize("cs2", [1.0 / 3.0, 0.25])
-def test_thermal_form_a_equals_form_b(q, cs2):
+@pytest.mark.parametrize("R", [0.0, 3e-3])
+def test_thermal_form_a_equals_form_b(q, cs2, R):
     rng_g = inputs.perturbed_populations(np.ones(q) * 0.05, (300,), 21, rel=1.0).T
     T = inputs.uniform_field((300,), 22, -0.5, 0.5)
     U = inputs.random_vectors(300, 23, 0.1)
@@ -62,8 +63,8 @@ def test_thermal_form_a_equals_form_b(q, cs2):
     for i in range(300):
         g = w * T[i] + rng_g[i]
         om = inputs.random_rates(q, 100 + i)
-        a = oracle.collide_thermal(g, U[i], om, cs2)
-        b = formb.thermal_collide(g, U[i], om, cs2)
+        a = oracle.collide_thermal(g, U[i], om, cs2, R * (1 + T[i]))
+        b = formb.thermal_collide(g, U[i], om, cs2, R * (1 + T[i]))
         worst = max(worst, np.abs(a - b).max())
     assert worst < TOL, worst
 
@@ -113,3 +114,33 @@ def test_rates_of_one_are_the_equilibrium():
         g = oracle.weights_thermal(15) * 0.3 + 0.01 * f[i]
         out = oracle.collide_thermal(g, u, np.ones(15))
         np.testing.assert_allclose(out, formb.thermal_equilibrium(g.sum(), u), atol=1e-15)
+
+
+@pytest.mark.parametrize("q", [15, 7])
+def test_scalar_source(q):
+    # Appendix B / C: S^phi has total R and, for the chosen central-moment combinations,
+    # no moment other than the zeroth (Eq. 16); it equals the generic inversion
+    e = oracle.velocities(q).astype(np.float64)
+    for i, (R, u) in enumerate([(1e-3, (0.0, 0.0, 0.0)), (-2e-3, (0.05, -0.03, 0.02)),
+                                (4e-3, (-0.1, 0.07, 0.09))]):
+        S = oracle.scalar_source(q, R, u)
+        assert abs(S.sum() - R) < 1e-18
+        np.testing.assert_allclose(formb.central_matrix(u, q) @ S, [R] + [0.0] * (q - 1),
+                                   atol=1e-18)
+        np.testing.assert_allclose(S, formb.scalar_source(q, R, u), atol=1e-18)
+        # the first raw moments are those the paper lists: sum S e = u R
+        np.testing.assert_allclose(e.T @ S, np.array(u) * R, atol=1e-18)
+
+
+def test_scalar_source_matches_printed_projections_to_second_order():
+    # Eq. (19): the projections m^s_0..m^s_9 and m^s_13 printed by the paper are those of S
+    # (m^s_10..12 and m^s_14 print continuous u^3 and three distinct u_i^2 u_j^2 terms that
+    # the lattice cannot hold; the inversion uses the lattice moments, reading R14)
+    K = oracle.kmatrix(15).astype(np.float64)
+    R, (ux, uy, uz) = 2e-3, (0.05, -0.03, 0.02)
+    m = K @ oracle.scalar_source(15, R, (ux, uy, uz))
+    printed = {0: R, 1: ux * R, 2: uy * R, 3: uz * R, 4: ux * uy * R, 5: ux * uz * R,
+               6: uy * uz * R, 7: (ux * ux - uy * uy) * R, 8: (ux * ux + uy * uy - 2 * uz * uz) * R,
+               9: (ux * ux + uy * uy + uz * uz - 2) * R, 13: ux * uy * uz * R}
+    for b, v in printed.items():
+        assert abs(m[b] - v) < 1e-18, b

@@ -191,3 +191,36 @@ def test_table1_ra1e3_coarse_grid(q):
     assert abs(near(nu["mid_min_z"]) - near(ref["Nu_min"]["lbm_pos"])) < h
     # hot and cold walls carry the same heat (centro-symmetry)
     assert nu["hot_wall_mean"] == pytest.approx(nu["cold_wall_mean"], rel=1e-6)
+
+
+@pytest.mark.parametrize("q", [15, 7])
+def test_uniform_heat_source_in_a_closed_box(q):
+    # Eq. (4) with a uniform source R on an adiabatic box: the total scalar grows by R per
+    # node and step, exactly
+    R = 2e-4
+    p = oracle.Problem(6, 5, 4, q_g=q, boundary=oracle.BC_ADIABATIC_BOX, omega_nu=1.2,
+                       omega_phi=1.5, gbeta=1e-3, heat_source=R, cs2_phi=1 / 3 if q == 15 else 0.25)
+    F, G = _random_state(p, 12)
+    total0 = p.fields(F, G)["T"].sum()
+    for n in (1, 7):
+        F, G = p.run(F, G, n)
+        total = p.fields(F, G)["T"].sum()
+        assert total - total0 == pytest.approx(n * R * p.ncell, rel=1e-10)
+        total0 = total
+
+
+@pytest.mark.parametrize("q,omphi,cs2", [(15, 1.4, 1 / 3), (15, 1.0, 1 / 3), (7, 1.4, 0.25)])
+def test_steady_conduction_with_a_heat_source(q, omphi, cs2):
+    # Dirichlet x walls, periodic y, z, uniform source: T'' = -R/D.  The LBM steady state
+    # has exactly that curvature; the half-way walls add a uniform offset of order R
+    N, R = 16, 1e-4
+    p = oracle.Problem(N, 2, 2, q_g=q, boundary=oracle.BC_XWALLS, omega_phi=omphi,
+                       cs2_phi=cs2, heat_source=R)
+    F, G = p.init(1, 0.0)
+    F, G = p.run(F, G, 20000)
+    T = p.fields(F, G)["T"][0, 0]
+    D = cs2 * (1.0 / omphi - 0.5)
+    np.testing.assert_allclose(T[2:] - 2 * T[1:-1] + T[:-2], -R / D, rtol=1e-8)
+    x = np.arange(N) + 0.5
+    exact = -0.5 + x / N + R / (2 * D) * x * (N - x)
+    assert np.abs(T - exact).max() <= R
