@@ -80,6 +80,8 @@ typedef struct {
     double cs2_phi;       /* c_sphi^2 of the thermal equilibrium (Sec. 2.2), in (0, 1/2] (D3Q7: (0, 1/3]) */
     double ext_force[3];  /* extra uniform body force added to F (0 for the cavity) */
     double U0;            /* velocity scale used to report u/U0 in lbm_nusselt */
+    double heat_source;   /* uniform scalar source R of the CDE (Eq. 4, App. B/C); 0 in the cavity.
+                             T = sum g + R/2 (Eq. 25) */
     int e4_mode;          /* App. A g^_14 equilibrium: 0 E = kxx~ kyy~ / rho, 1 E = rho c_s^4 */
     int adiabatic_mode;   /* LBM_ADIABATIC_* */
     int boundary;         /* LBM_BC_* */

@@ -221,6 +221,7 @@ static DevParams<real> dev_params(const lbm_ctx* c) {
     p.T_hot = (real)P.T_hot;
     p.T_cold = (real)P.T_cold;
     p.cs2_phi = (real)P.cs2_phi;
+    p.heat_source = (real)P.heat_source;
     p.ext_fx = (real)P.ext_force[0];
     p.ext_fy = (real)P.ext_force[1];
     p.ext_fz = (real)P.ext_force[2];
@@ -273,6 +274,7 @@ static int check_params(const lbm_params* p, int q) {
     if (p->e4_mode != 0 && p->e4_mode != 1) return 0;
     if (p->adiabatic_mode != 0 && p->adiabatic_mode != 1) return 0;
     if (p->boundary < 0 || p->boundary > 15) return 0;
+    if (!std::isfinite(p->heat_source)) return 0;
     return 1;
 }
 

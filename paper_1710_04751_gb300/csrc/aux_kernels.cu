@@ -162,6 +162,7 @@ __device__ __forceinline__ void node_macro(const S* __restrict__ F, const S* __r
     }
 #pragma unroll
     for (int a = 0; a < Q; ++a) t += thermal_value<S>(G, Tn, p, a, c);
+    t -= 0.5 * (double)p.heat_source;  // collision added R: phi = sum g~ - R/2 (Eq. 25)
     const double Fz = (double)p.ext_fz + (double)p.gbeta * (t - (double)p.T0);
     rho = r;
     ux = (jx - 0.5 * (double)p.ext_fx) / r;
@@ -240,6 +241,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const S* __restrict__ G,
         real T = real(0);
 #pragma unroll
         for (int a = 0; a < Q; ++a) T += (real)thermal_value<S>(G, Tn, p, a, c);
+        T -= real(0.5) * p.heat_source;
         if (!isfinite(T)) bad = 1;
         const double d = fabs((double)T - (double)snap[c]);
         if (d > local) local = d;
@@ -289,7 +291,7 @@ __device__ __forceinline__ double node_T(const S* __restrict__ G, const float* _
     double t = 0.0;
 #pragma unroll
     for (int a = 0; a < Q; ++a) t += thermal_value<S>(G, Tn, p, a, c);
-    return t;
+    return t - 0.5 * (double)p.heat_source;
 }
 
 template <typename S, int Q>

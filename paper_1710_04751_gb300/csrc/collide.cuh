@@ -1,8 +1,8 @@
 // collide.cuh -- one-cell cascaded collisions of arXiv:1710.04751 in registers.
 //
 //   collide_flow      Appendix A: D3Q15 flow collision with the body-force source
-//   collide_thermal15 Sec. 2.2: D3Q15 scalar collision (R = 0)
-//   collide_thermal7  Appendix C: D3Q7 scalar collision (R = 0)
+//   collide_thermal15 Sec. 2.2: D3Q15 scalar collision with a uniform source R
+//   collide_thermal7  Appendix C: D3Q7 scalar collision with a uniform source R
 //
 // The paper writes each cascade as closed forms for the kernel components (g^_b, h^_b)
 // that, added through K, make every central moment relax toward its equilibrium at its
@@ -92,9 +92,9 @@ __device__ __forceinline__ Raw15<real> central15(const Raw15<real>& m, real ux, 
     return c;
 }
 
-// Raw moments of a central-moment increment d (zeroth order zero) about u: the inverse
-// binomial shift.
-template <typename real>
+// Raw moments of a central-moment increment d about u: the inverse binomial shift.  With
+// D0 = false the zeroth-order increment is zero (the flow) and its terms are dropped.
+template <bool D0, typename real>
 __device__ __forceinline__ Raw15<real> raw_of_central_increment(const Raw15<real>& d, real ux,
                                                                 real uy, real uz) {
     const real uxx = ux * ux, uyy = uy * uy, uxy = ux * uy, uxz = ux * uz, uyz = uy * uz;
@@ -115,6 +115,24 @@ __device__ __forceinline__ Raw15<real> raw_of_central_increment(const Raw15<real
     r.xyz = d.xyz + ux * d.yz + uy * d.xz + uz * d.xy + uxy * d.z + uxz * d.y + uyz * d.x;
     r.xxyy = d.xxyy + real(2) * uy * d.xxy + real(2) * ux * d.xyy + uyy * d.xx + uxx * d.yy +
              real(4) * uxy * d.xy + real(2) * ux * uyy * d.x + real(2) * uxx * uy * d.y;
+    if constexpr (D0) {
+        const real d0 = d.m0;
+        r.m0 = d0;
+        r.x += ux * d0;
+        r.y += uy * d0;
+        r.z += uz * d0;
+        r.xy += uxy * d0;
+        r.xz += uxz * d0;
+        r.yz += uyz * d0;
+        r.xx += uxx * d0;
+        r.yy += uyy * d0;
+        r.zz += uz * uz * d0;
+        r.xyy += ux * uyy * d0;
+        r.xxy += uxx * uy * d0;
+        r.xxz += uxx * uz * d0;
+        r.xyz += uxy * uz * d0;
+        r.xxyy += uxx * uyy * d0;
+    }
     return r;
 }
 
@@ -202,22 +220,25 @@ __device__ __forceinline__ void collide_flow(real (&f)[15], real Fx, real Fy, re
     const real E = p.e4_mode == 1 ? rho * real(1.0 / 9.0)
                                   : (k.xx + d.xx) * (k.yy + d.yy) * inv_rho;
     d.xxyy = om[14] * (E - k.xxyy);
-    add_populations15<real>(f, raw_of_central_increment<real>(d, ux, uy, uz));
+    add_populations15<real>(f, raw_of_central_increment<false, real>(d, ux, uy, uz));
 }
 
-// Thermal D3Q15 collision (Sec. 2.2) with R = 0: g becomes g~; u from the flow.  Every
-// moment but the zeroth relaxes (Eq. 15 equilibria: c_sphi^2 phi on the diagonal second
-// order, c_sphi^4 phi for xxyy, zero otherwise).
+// Thermal D3Q15 collision (Sec. 2.2) with the uniform source R = p.heat_source: g becomes
+// g~; u from the flow.  phi = sum gbar + R/2 (Eq. 25).  The source's only central moment
+// is the zeroth, so the zeroth moment gains R and every other moment of gbar relaxes
+// toward its equilibrium at phi (Eq. 15: c_sphi^2 phi on the diagonal second order,
+// c_sphi^4 phi for xxyy, zero otherwise).
 template <typename real>
 __device__ __forceinline__ void collide_thermal15(real (&g)[15], real ux, real uy, real uz,
                                                   const DevParams<real>& p) {
     const Raw15<real> m = raw15<real>(g);
-    const real phi = m.m0;
+    const real R = p.heat_source;
+    const real phi = m.m0 + real(0.5) * R;
     const Raw15<real> k = central15<real>(m, ux, uy, uz);
     const real* om = p.om_g;
     const real cs2 = p.cs2_phi;
     Raw15<real> d;
-    d.m0 = real(0);
+    d.m0 = R;
     d.x = -om[1] * k.x;
     d.y = -om[2] * k.y;
     d.z = -om[3] * k.z;
@@ -233,23 +254,25 @@ __device__ __forceinline__ void collide_thermal15(real (&g)[15], real ux, real u
     d.xxz = -om[12] * k.xxz;
     d.xyz = -om[13] * k.xyz;
     d.xxyy = om[14] * (cs2 * cs2 * phi - k.xxyy);
-    add_populations15<real>(g, raw_of_central_increment<real>(d, ux, uy, uz));
+    add_populations15<real>(g, raw_of_central_increment<true, real>(d, ux, uy, uz));
 }
 
-// Thermal D3Q7 collision (Appendix C) with R = 0: moments 0; x, y, z; xx-yy,
-// xx+yy-2zz, xx+yy+zz (equilibrium 3 c_sphi^2 phi).
+// Thermal D3Q7 collision (Appendix C) with the uniform source R: moments 0; x, y, z;
+// xx-yy, xx+yy-2zz, xx+yy+zz (equilibrium 3 c_sphi^2 phi, phi = sum gbar + R/2).
 template <typename real>
 __device__ __forceinline__ void collide_thermal7(real (&g)[7], real ux, real uy, real uz,
                                                  const DevParams<real>& p) {
     const real px = g[1] + g[2], qx = g[1] - g[2];
     const real py = g[3] + g[4], qy = g[3] - g[4];
     const real pz = g[5] + g[6], qz = g[5] - g[6];
-    const real phi = g[0] + px + py + pz;
-    // central moments about u
-    const real kx = qx - ux * phi, ky = qy - uy * phi, kz = qz - uz * phi;
-    const real kxx = px - real(2) * ux * qx + ux * ux * phi;
-    const real kyy = py - real(2) * uy * qy + uy * uy * phi;
-    const real kzz = pz - real(2) * uz * qz + uz * uz * phi;
+    const real m0 = g[0] + px + py + pz;
+    const real R = p.heat_source;
+    const real phi = m0 + real(0.5) * R;
+    // central moments of gbar about u
+    const real kx = qx - ux * m0, ky = qy - uy * m0, kz = qz - uz * m0;
+    const real kxx = px - real(2) * ux * qx + ux * ux * m0;
+    const real kyy = py - real(2) * uy * qy + uy * uy * m0;
+    const real kzz = pz - real(2) * uz * qz + uz * uz * m0;
     const real* om = p.om_g;
     const real dx = -om[1] * kx, dy = -om[2] * ky, dz = -om[3] * kz;
     const real d1 = -om[4] * (kxx - kyy);
@@ -257,16 +280,19 @@ __device__ __forceinline__ void collide_thermal7(real (&g)[7], real ux, real uy,
     const real dtr = om[6] * (real(3) * p.cs2_phi * phi - (kxx + kyy + kzz));
     real dxx, dyy, dzz;
     split_second_order(d1, d2, dtr, dxx, dyy, dzz);
-    // raw increments and populations: p_{+-} = (r_xx +- r_x)/2, p_0 = -(r_xx + r_yy + r_zz)
-    const real rxx = dxx + real(2) * ux * dx, ryy = dyy + real(2) * uy * dy;
-    const real rzz = dzz + real(2) * uz * dz;
-    g[1] += real(0.5) * (rxx + dx);
-    g[2] += real(0.5) * (rxx - dx);
-    g[3] += real(0.5) * (ryy + dy);
-    g[4] += real(0.5) * (ryy - dy);
-    g[5] += real(0.5) * (rzz + dz);
-    g[6] += real(0.5) * (rzz - dz);
-    g[0] -= rxx + ryy + rzz;
+    // raw increments (zeroth: R) and populations: p_{+-} = (r_xx +- r_x)/2,
+    // p_0 = r_0 - (r_xx + r_yy + r_zz)
+    const real rx = dx + ux * R, ry = dy + uy * R, rz = dz + uz * R;
+    const real rxx = dxx + real(2) * ux * dx + ux * ux * R;
+    const real ryy = dyy + real(2) * uy * dy + uy * uy * R;
+    const real rzz = dzz + real(2) * uz * dz + uz * uz * R;
+    g[1] += real(0.5) * (rxx + rx);
+    g[2] += real(0.5) * (rxx - rx);
+    g[3] += real(0.5) * (ryy + ry);
+    g[4] += real(0.5) * (ryy - ry);
+    g[5] += real(0.5) * (rzz + rz);
+    g[6] += real(0.5) * (rzz - rz);
+    g[0] += R - (rxx + ryy + rzz);
 }
 
 }  // namespace lbm

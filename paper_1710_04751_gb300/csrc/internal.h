@@ -16,6 +16,7 @@ struct DevParams {
     real wg[15];        // thermal rest weights w^phi_a (anti-bounce-back)
     real wf[15];        // stored-value offsets of the flow populations (16-bit forms: w_a)
     real gbeta, T0, T_hot, T_cold, cs2_phi;
+    real heat_source;   // uniform scalar source R (Eq. 4)
     real ext_fx, ext_fy, ext_fz;
     int e4_mode, adiabatic_mode, boundary;
     int nx, ny, nz;

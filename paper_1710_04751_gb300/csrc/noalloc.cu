@@ -75,6 +75,7 @@ DevParams<real> params_for(const lbm_grid& g, int Q, const lbm_params& P, int64_
     p.T_hot = (real)P.T_hot;
     p.T_cold = (real)P.T_cold;
     p.cs2_phi = (real)P.cs2_phi;
+    p.heat_source = (real)P.heat_source;
     p.ext_fx = (real)P.ext_force[0];
     p.ext_fy = (real)P.ext_force[1];
     p.ext_fz = (real)P.ext_force[2];

@@ -106,6 +106,7 @@ __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15]
     real T = real(0);
 #pragma unroll
     for (int a = 0; a < Q; ++a) T += g[a];
+    T += real(0.5) * p.heat_source;  // Eq. (25)
     const real Fz = p.ext_fz + p.gbeta * (T - p.T0);
     real ux, uy, uz;
     collide_flow<real>(f, p.ext_fx, p.ext_fy, Fz, p, ux, uy, uz);

@@ -43,13 +43,15 @@ class Params(ctypes.Structure):
         ("omega_f", ctypes.c_double * 15), ("omega_g", ctypes.c_double * 15),
         ("gbeta", ctypes.c_double), ("T_hot", ctypes.c_double), ("T_cold", ctypes.c_double),
         ("cs2_phi", ctypes.c_double), ("ext_force", ctypes.c_double * 3), ("U0", ctypes.c_double),
+        ("heat_source", ctypes.c_double),
         ("e4_mode", ctypes.c_int), ("adiabatic_mode", ctypes.c_int), ("boundary", ctypes.c_int),
     ]
 
     def as_dict(self):
         return dict(omega_f=list(self.omega_f), omega_g=list(self.omega_g), gbeta=self.gbeta,
                     T_hot=self.T_hot, T_cold=self.T_cold, cs2_phi=self.cs2_phi,
-                    ext_force=list(self.ext_force), U0=self.U0, e4_mode=self.e4_mode,
+                    ext_force=list(self.ext_force), U0=self.U0, heat_source=self.heat_source,
+                    e4_mode=self.e4_mode,
                     adiabatic_mode=self.adiabatic_mode, boundary=self.boundary)
 
 

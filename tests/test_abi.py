@@ -32,8 +32,8 @@ def test_library_exports_every_declared_entry_point():
 
 
 def test_structure_sizes_match_header_layout():
-    # lbm_params: 15+15+4+3+1 doubles then 3 ints (+4 bytes padding)
-    assert ctypes.sizeof(binding.Params) == (15 + 15 + 4 + 3 + 1) * 8 + 16
+    # lbm_params: 15+15+4+3+2 doubles then 3 ints (+4 bytes padding)
+    assert ctypes.sizeof(binding.Params) == (15 + 15 + 4 + 3 + 2) * 8 + 16
     assert ctypes.sizeof(binding.Nu) == 11 * 8
 
 

@@ -27,6 +27,7 @@ def lbm_mod():
 def params_of(p: "oracle.Problem"):
     return dict(omega_f=p.omega_f, omega_g=p.omega_g, gbeta=p.gbeta, T_hot=p.T_hot,
                 T_cold=p.T_cold, cs2_phi=p.cs2_phi, ext_force=list(p.ext_force), U0=p.U0,
+                heat_source=p.heat_source,
                 e4_mode=p.e4_mode, adiabatic_mode=p.adiabatic_mode, boundary=p.boundary)
 
 
@@ -180,6 +181,82 @@ def test_fp32_random_state_one_step(case):
     F1, G1 = p.step(f, g)
     f1, g1 = sim.get_populations()
     assert_fp32_close(p, f1, g1, F1, G1)
+
+
+# ------------------------------------------------------------------------------------
+# A uniform heat source R (Eq. 4; Sec. 2.2 and App. C): both lattices, every boundary
+# mode, FP64 and FP32
+# ------------------------------------------------------------------------------------
+
+HEAT_CASES = [
+    (13, 7, 5, 15, oracle.BC_CAVITY, 1, 0, 2e-3),
+    (13, 7, 5, 7, oracle.BC_CAVITY, 0, 0, -1.5e-3),
+    (33, 17, 9, 15, oracle.BC_PERIODIC, 1, 0, 4e-3),
+    (8, 5, 7, 7, oracle.BC_XWALLS, 1, 1, 1e-3),
+    (6, 9, 10, 15, oracle.BC_ADIABATIC_BOX, 0, 1, 3e-3),
+]
+
+
+def _heat_problem(case, seed):
+    p = _case_problem(case[:7], seed)
+    p.heat_source = case[7]
+    return p
+
+
+@pytest.mark.parametrize("case", HEAT_CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}-q{c[3]}-bc{c[4]}-R{c[7]:g}" for c in HEAT_CASES])
+def test_fp64_heat_source_steps(case):
+    lbm = lbm_mod()
+    p = _heat_problem(case, 500 + case[0])
+    F, G = random_state(p, 21 + case[1])
+    sim = gpu_for(p, lbm.FP64)
+    assert sim.params()["heat_source"] == case[7]
+    sim.set_populations(F, G)
+    for n in (1, 5):
+        sim.step(n)
+        F, G = p.run(F, G, n)
+        f, g = sim.get_populations()
+        assert np.abs(f - F).max() <= FP64_TOL and np.abs(g - G).max() <= FP64_TOL
+    fl, fr = sim.fields(), p.fields(F, G)
+    for k in fl:
+        assert np.abs(fl[k] - fr[k]).max() <= 1e-12, k
+    nu, ref = sim.nusselt(), p.nusselt(F, G)
+    for k in ("hot_wall_mean", "cold_wall_mean", "mid_mean", "mid_max", "mid_min", "umax", "wmax"):
+        assert nu[k] == pytest.approx(ref[k], rel=1e-9, abs=1e-11), k
+
+
+@pytest.mark.parametrize("case", HEAT_CASES[:3], ids=[f"q{c[3]}-bc{c[4]}" for c in HEAT_CASES[:3]])
+def test_fp32_heat_source_one_step(case):
+    lbm = lbm_mod()
+    p = _heat_problem(case, 700 + case[0])
+    F, G = random_state(p, 31 + case[2])
+    sim = gpu_for(p, lbm.FP32)
+    sim.set_populations(F, G)
+    f, g = sim.get_populations()
+    sim.step(1)
+    F1, G1 = p.step(f, g)
+    f1, g1 = sim.get_populations()
+    assert_fp32_close(p, f1, g1, F1, G1)
+
+
+def test_heat_source_closed_box_total_scalar():
+    """Adiabatic box, no flow forcing: the total scalar grows by exactly N R per step."""
+    lbm = lbm_mod()
+    n, R = 10, 2.5e-3
+    p = oracle.Problem(n, n, n, q_g=15, boundary=oracle.BC_ADIABATIC_BOX, gbeta=0.0,
+                       T_hot=0.5, T_cold=-0.5, U0=0.05, heat_source=R)
+    sim = gpu_for(p, lbm.FP64, noise_amp=0.0)
+    T0 = sim.fields()["T"].sum()
+    sim.step(40)
+    assert sim.fields()["T"].sum() - T0 == pytest.approx(40 * n ** 3 * R, rel=1e-10)
+
+
+def test_non_finite_heat_source_is_rejected():
+    lbm = lbm_mod()
+    p = oracle.Problem.cavity(8, 1e3)
+    d = params_of(p)
+    d["heat_source"] = float("nan")
+    with pytest.raises(lbm.LBMError):
+        lbm.LBM((8, 8, 8), 15, params=d, precision=lbm.FP64)
 
 
 # ------------------------------------------------------------------------------------
