@@ -256,6 +256,107 @@ def time_to_steady(lbm, q, max_steps, threshold=1e-6, chunk=1000):
             "w_max": nu["wmax"]}
 
 
+def batch_variant(lbm, steps, warmup, peak, converge_steps=0):
+    """The batched form: 64 cavities (edge 32/48/64/96, Ra log-uniform in [1e3, 1e6],
+    Pr in {0.71, 1, 7}, seed 1), FP32, D3Q15 + D3Q15, one persistent kernel launch per
+    step captured in graphs of 100 steps, tiling chosen by the autotuner; against the
+    same members advanced with one single-cavity kernel launch per member and step.
+    Throughput counts the node updates actually done (members that diverge stop)."""
+    import torch
+    from paper_1710_04751_gb300.workloads import cavity_sweep
+    members = cavity_sweep(64, seed=1)
+    b = lbm.Batch(members, precision=lbm.FP32, residual_interval=RESIDUAL_INTERVAL,
+                  autotune_steps=0)
+    trials = b.autotune(trial_steps=5)
+    tuned_nodes = b.active_nodes  # every member is active while the tuner times the kernels
+    stream = torch.cuda.current_stream()
+    ncell = [m["grid"][0] ** 3 for m in members]
+
+    def timed(mode, n):
+        before = [s["steps"] for s in b.status()]
+        t = time_steps_mode(b, n, stream, mode)
+        after = [s["steps"] for s in b.status()]
+        lups = sum(c * (a - s0) for c, a, s0 in zip(ncell, after, before))
+        return lups / t / 1e6, t
+
+    b.step(warmup)
+    res = {}
+    for mode in ("graph", "launch", "sequential"):
+        mlups, t = timed(mode, steps)
+        res[mode] = {"value": round(mlups, 1), "unit": "MLUPS", "seconds": round(t, 4)}
+    st = b.status()
+    tiling = b.tiling
+    best = min(trials, key=lambda t: t["ms_per_step"])
+    bpn = bytes_per_node(15)
+    achieved = bpn * tuned_nodes / (best["ms_per_step"] * 1e-3) / 1e9
+    out = {
+        "workload": "64 cubic cavities, edge from {32,48,64,96}, Ra log-uniform [1e3,1e6], "
+                    "Pr from {0.71,1,7}, seed 1; FP32, D3Q15+D3Q15",
+        "nodes": sum(ncell), "steps": steps, "warmup": warmup,
+        "batched_graph": res["graph"], "batched_launch_per_step": res["launch"],
+        "sequential_per_cavity_launches": res["sequential"],
+        "speedup_vs_sequential": round(res["graph"]["value"] / res["sequential"]["value"], 3),
+        "tiling": tiling,
+        "autotune": [{k: t[k] for k in ("threads", "min_blocks", "mapping", "blocks_per_sm")}
+                     | {"ms": round(t["ms_per_step"], 4)} for t in trials],
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "kernel": "batch_step_kernel<float,15>",
+                     "bytes_per_node": bpn, "kernel_ms": round(best["ms_per_step"], 4),
+                     "nodes_per_launch": tuned_nodes},
+        "states_after": {k: sum(1 for s in st if s["state"] == k)
+                         for k in ("active", "converged", "diverged")},
+    }
+    b.close()
+    if converge_steps > 0:
+        out["to_convergence"] = batch_to_convergence(lbm, members, converge_steps)
+    return out
+
+
+def time_steps_mode(b, steps, stream, mode):
+    import torch
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    b.step(steps, mode=mode)
+    end.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def batch_to_convergence(lbm, members, max_steps, tol=1e-6):
+    """Every member of the sweep from rest until its own max |dT| over 100 steps falls
+    below tol (FP32 floor: see time_to_steady) or it diverges, up to max_steps."""
+    import torch
+    b = lbm.Batch(members, precision=lbm.FP32, residual_interval=RESIDUAL_INTERVAL,
+                  steady_tol=tol)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done_at = []
+    while b.steps_done < max_steps and b.active_nodes > 0:
+        b.step(min(10_000, max_steps - b.steps_done))
+        done_at.append((b.steps_done, round(time.perf_counter() - t0, 2), b.active_nodes))
+    dt = time.perf_counter() - t0
+    st = b.status()
+    conv = [s["steps"] for s in st if s["state"] == "converged"]
+    nus = []
+    for i, s in enumerate(st):
+        if s["state"] == "converged":
+            nu = b.member(i).nusselt()
+            nus.append({"n": members[i]["grid"][0], "Ra": round(members[i]["Ra"], 1),
+                        "Pr": members[i]["Pr"], "steps": s["steps"],
+                        "Nu_hot": round(nu["hot_wall_mean"], 5)})
+    ncell = [m["grid"][0] ** 3 for m in members]
+    lups = sum(c * s["steps"] for c, s in zip(ncell, st))
+    b.close()
+    return {"tol": tol, "max_steps": max_steps, "seconds": round(dt, 2),
+            "converged": len(conv), "diverged": sum(1 for s in st if s["state"] == "diverged"),
+            "active": sum(1 for s in st if s["state"] == "active"),
+            "steps_min_median_max": [min(conv), sorted(conv)[len(conv) // 2], max(conv)] if conv else None,
+            "node_updates": lups, "mlups": round(lups / dt / 1e6, 1),
+            "progress": done_at[:: max(1, len(done_at) // 12)], "converged_members": nus}
+
+
 def cpu_baseline(sample_steps=3, q=15):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of the same
     workload (the 128^3 Ra = 1e5 cavity, a few steps from its initial state)."""
@@ -348,6 +449,8 @@ def gpu_arm(args):
             "D3Q15+D3Q15": time_to_steady(lbm, 15, args.steady_max_steps),
             "D3Q15+D3Q7": time_to_steady(lbm, 7, args.steady_max_steps),
         }
+    if not args.no_batch:
+        line["batch"] = batch_variant(lbm, args.batch_steps, 3, peak, args.batch_converge_steps)
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e_variant(lbm, 15, args.e2e_reps, device)
     if rank == 0 and not args.no_cpu_baseline:
@@ -419,6 +522,10 @@ def main(argv=None):
     ap.add_argument("--no-steady", action="store_true",
                     help="skip the run of both variants from rest to steady state")
     ap.add_argument("--steady-max-steps", type=int, default=400_000)
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-cavity batched form")
+    ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--batch-converge-steps", type=int, default=0,
+                    help="also run the 64 cavities from rest to their own convergence (max steps)")
     ap.add_argument("--ref-budget", type=float, default=90.0,
                     help="seconds the reference arm spends on warm-up + timed steps")
     ap.add_argument("--traffic-q15", type=float, default=None,

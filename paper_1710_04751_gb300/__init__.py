@@ -7,3 +7,4 @@ from .lbm import (  # noqa: F401
     BC_XWALLS, BF16_DEV, D3Q7, D3Q15, EXPORTS, FP16_DEV, FP32, FP64, LBM, LBMError, arena_bytes, default_options,
     derive_params, library_path, load, nusselt_noalloc,
 )
+from .batch import Batch  # noqa: F401

@@ -35,7 +35,8 @@ def sources():
 def _deps():
     files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC)
                          if f.endswith((".cuh", ".h"))]
-    files.append(os.path.join(ROOT, "include", "lbm.h"))
+    inc = os.path.join(ROOT, "include")
+    files += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     files.append(os.path.abspath(__file__))
     return files
 

@@ -9,65 +9,21 @@
 #include <string>
 #include <thread>
 
-#include "lbm.h"
-#include "internal.h"
+#include "context.h"
 
 using namespace lbm;
-
-struct lbm_ctx {
-    lbm_grid grid;
-    int Q;
-    int precision;
-    lbm_params params;
-    lbm_options opt;
-    int64_t ncell, plane;
-    size_t rsize;
-    int device;
-    cudaStream_t stream;
-    void* arena;
-    bool own_arena;
-    size_t arena_bytes;
-    DevState dev;
-    int cur;              // buffer holding the current state
-    int64_t steps;
-    double last_residual; // < 0: none recorded yet
-    unsigned long long* host_bits;  // pinned: residual bits + flag
-    std::string err;
-};
 
 static thread_local std::string g_err;
 
 void lbm::set_last_error(const char* msg) { g_err = msg; }
 
-static int fail(lbm_ctx* ctx, int code, const char* fmt, const char* detail = nullptr) {
+int lbm::record_error(std::string* slot, int code, const char* fmt, const char* detail) {
     char buf[512];
     snprintf(buf, sizeof buf, fmt, detail ? detail : "");
-    if (ctx) ctx->err = buf;
+    if (slot) *slot = buf;
     g_err = buf;
     return code;
 }
-
-#define CUDA_OR_FAIL(ctx, call)                                                     \
-    do {                                                                            \
-        cudaError_t e_ = (call);                                                    \
-        if (e_ != cudaSuccess)                                                      \
-            return fail((ctx), LBM_ECUDA, "CUDA error in " #call ": %s",            \
-                        cudaGetErrorString(e_));                                    \
-    } while (0)
-
-// Keeps the caller's current device and restores it on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-        else prev = -1;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
-static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 extern "C" void lbm_default_options(lbm_options* o) {
     if (!o) return;
@@ -152,17 +108,6 @@ static bool valid_precision(int p) {
     return p == LBM_FP64 || p == LBM_FP32 || p == LBM_FP16_DEV || p == LBM_BF16_DEV;
 }
 
-// Run fn(S{}) with S the storage type of the precision.
-template <typename Fn>
-static int with_storage(int precision, Fn&& fn) {
-    switch (precision) {
-    case LBM_FP64: return fn(double{});
-    case LBM_FP32: return fn(float{});
-    case LBM_FP16_DEV: return fn(__half{});
-    default: return fn(__nv_bfloat16{});
-    }
-}
-
 static Layout layout_of(const lbm_grid* g, int q, int precision) {
     const int64_t ncell = (int64_t)g->nx * g->ny * g->nz;
     const int64_t plane = plane_of(ncell);
@@ -188,8 +133,12 @@ extern "C" size_t lbm_arena_bytes(const lbm_grid* grid, int lattice, int precisi
     return layout_of(grid, lattice, precision).total;
 }
 
+size_t lbm::context_arena_bytes(const lbm_grid* g, int q, int precision) {
+    return layout_of(g, q, precision).total;
+}
+
 template <typename real>
-static DevParams<real> dev_params(const lbm_ctx* c) {
+DevParams<real> lbm::dev_params(const lbm_ctx* c) {
     DevParams<real> p;
     memset(&p, 0, sizeof p);
     const lbm_params& P = c->params;
@@ -235,15 +184,19 @@ static DevParams<real> dev_params(const lbm_ctx* c) {
     p.plane = c->plane;
     return p;
 }
+template DevParams<double> lbm::dev_params<double>(const lbm_ctx*);
+template DevParams<float> lbm::dev_params<float>(const lbm_ctx*);
 
-// Wait for all work on the context's stream, polling with the context's time bound.
-static int wait_stream(lbm_ctx* c) {
+// Wait for all work on a stream, polling an event with a time bound.
+int lbm::wait_stream_for(cudaStream_t stream, double timeout_s, std::string* slot) {
     cudaEvent_t ev;
-    CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    cudaError_t e = cudaEventRecord(ev, c->stream);
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess)
+        return record_error(slot, LBM_ECUDA, "CUDA error in cudaEventCreate: %s", cudaGetErrorString(e));
+    e = cudaEventRecord(ev, stream);
     if (e != cudaSuccess) {
         cudaEventDestroy(ev);
-        return fail(c, LBM_ECUDA, "CUDA error in cudaEventRecord: %s", cudaGetErrorString(e));
+        return record_error(slot, LBM_ECUDA, "CUDA error in cudaEventRecord: %s", cudaGetErrorString(e));
     }
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
@@ -251,12 +204,12 @@ static int wait_stream(lbm_ctx* c) {
         if (e == cudaSuccess) break;
         if (e != cudaErrorNotReady) {
             cudaEventDestroy(ev);
-            return fail(c, LBM_ECUDA, "CUDA error while waiting: %s", cudaGetErrorString(e));
+            return record_error(slot, LBM_ECUDA, "CUDA error while waiting: %s", cudaGetErrorString(e));
         }
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (el > c->opt.timeout_s) {
+        if (el > timeout_s) {
             cudaEventDestroy(ev);
-            return fail(c, LBM_ETIMEOUT, "timed out waiting for the GPU%s");
+            return record_error(slot, LBM_ETIMEOUT, "timed out waiting for the GPU%s");
         }
         std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
     }
@@ -406,6 +359,7 @@ static int run_steps(lbm_ctx* c, int64_t n, bool* checked) {
 
 extern "C" int lbm_step(lbm_ctx* c, int64_t n) {
     if (!c || n < 0) return fail(c, LBM_EINVAL, "invalid context or step count%s");
+    if (c->owner) return fail(c, LBM_EINVAL, "a batch member is advanced by lbm_batch_step%s");
     DeviceGuard g(c->device);
     bool checked = false;
     int rc = with_storage(c->precision,
@@ -567,7 +521,11 @@ extern "C" int lbm_synchronize(lbm_ctx* c) {
 }
 
 extern "C" void lbm_destroy(lbm_ctx* c) {
-    if (!c) return;
+    if (!c || c->owner) return;  // batch members go with their batch
+    lbm::destroy_context(c);
+}
+
+void lbm::destroy_context(lbm_ctx* c) {
     {
         DeviceGuard g(c->device);
         wait_stream(c);

@@ -1,0 +1,96 @@
+// context.h -- the library's private view of a context (include/lbm.h declares it opaque)
+// and the helpers the C ABI translation units share (not installed).
+#pragma once
+
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "internal.h"
+#include "lbm.h"
+
+struct lbm_batch;
+
+struct lbm_ctx {
+    lbm_grid grid;
+    int Q;
+    int precision;
+    lbm_params params;
+    lbm_options opt;
+    int64_t ncell, plane;
+    size_t rsize;
+    int device;
+    cudaStream_t stream;
+    void* arena;
+    bool own_arena;
+    size_t arena_bytes;
+    lbm::DevState dev;
+    int cur;              // buffer holding the current state
+    int64_t steps;
+    double last_residual; // < 0: none recorded yet
+    unsigned long long* host_bits;  // pinned: residual bits + flag
+    lbm_batch* owner;     // non-NULL: a member of a batch, stepped by the batch only
+    std::string err;
+};
+
+namespace lbm {
+
+// Formats the message (fmt holds one %s for detail), stores it in *slot (if any) and as
+// the thread's last error, and returns code.
+int record_error(std::string* slot, int code, const char* fmt, const char* detail = nullptr);
+
+inline int fail(lbm_ctx* ctx, int code, const char* fmt, const char* detail = nullptr) {
+    return record_error(ctx ? &ctx->err : nullptr, code, fmt, detail);
+}
+
+// Waits for all work queued on `stream`, polling an event, for at most timeout_s seconds.
+int wait_stream_for(cudaStream_t stream, double timeout_s, std::string* err_slot);
+
+inline int wait_stream(lbm_ctx* c) { return wait_stream_for(c->stream, c->opt.timeout_s, &c->err); }
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Kernel parameters of a context in the arithmetic type `real`.
+template <typename real>
+DevParams<real> dev_params(const lbm_ctx* c);
+
+// Frees a context (lbm_destroy without the batch-member check).
+void destroy_context(lbm_ctx* c);
+
+// Bytes of the device arena of one context.
+size_t context_arena_bytes(const lbm_grid* g, int q, int precision);
+
+// Run fn(S{}) with S the storage type of the precision.
+template <typename Fn>
+int with_storage(int precision, Fn&& fn) {
+    switch (precision) {
+    case LBM_FP64: return fn(double{});
+    case LBM_FP32: return fn(float{});
+    case LBM_FP16_DEV: return fn(__half{});
+    default: return fn(__nv_bfloat16{});
+    }
+}
+
+}  // namespace lbm
+
+#define CUDA_OR_FAIL(ctx, call)                                                     \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            return ::lbm::fail((ctx), LBM_ECUDA, "CUDA error in " #call ": %s",     \
+                               cudaGetErrorString(e_));                             \
+    } while (0)
+
+// Keeps the caller's current device and restores it on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};

@@ -290,7 +290,26 @@ class LBM:
     def synchronize(self):
         self._check(self._L.lbm_synchronize(self._ctx))
 
+    @classmethod
+    def _view(cls, handle, owner):
+        """A member of a batch as an LBM object (not owned: the batch frees it)."""
+        self = object.__new__(cls)
+        self._L = load()
+        self._ctx = ctypes.c_void_p(handle)
+        self._owner = owner
+        self.grid = tuple(owner._grids[owner._handles.index(handle)])
+        self.lattice = owner.lattice
+        self.precision = owner.precision
+        self.device = owner.device
+        self._stream = owner._stream
+        self._arena = None
+        return self
+
     def close(self):
+        if getattr(self, "_owner", None) is not None:
+            self._ctx = ctypes.c_void_p()
+            self._owner = None
+            return
         if getattr(self, "_ctx", None) is not None and self._ctx.value:
             self._L.lbm_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()

@@ -10,31 +10,42 @@ import pytest
 
 import oracle
 import paper_1710_04751_gb300 as lbm
+from paper_1710_04751_gb300 import batch as batch_binding
 from paper_1710_04751_gb300 import lbm as binding
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
-                      "lbm.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header):
+    text = open(os.path.join(INCLUDE, header)).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text)))
 
 
-def test_library_exports_every_declared_entry_point():
+@pytest.mark.parametrize("header,exports", [("lbm.h", binding.EXPORTS),
+                                            ("lbm_batch.h", batch_binding.EXPORTS)])
+def test_library_exports_every_declared_entry_point(header, exports):
     L = binding.load()
-    names = declared_functions()
+    names = declared_functions(header)
     assert len(names) >= 16
     for n in names:
         assert hasattr(L, n), n
-    assert sorted(names) == sorted(binding.EXPORTS)
+    assert sorted(names) == sorted(exports)
+
+
+def test_every_header_is_checked():
+    assert sorted(f for f in os.listdir(INCLUDE) if f.endswith(".h")) == ["lbm.h", "lbm_batch.h"]
 
 
 def test_structure_sizes_match_header_layout():
     # lbm_params: 15+15+4+3+2 doubles then 3 ints (+4 bytes padding)
     assert ctypes.sizeof(binding.Params) == (15 + 15 + 4 + 3 + 2) * 8 + 16
     assert ctypes.sizeof(binding.Nu) == 11 * 8
+    # lbm_batch_options: int (+4), u64, double, int (+4), double, 3 pointers/sizes, int,
+    # the 4-int tiling, (+4) double
+    assert ctypes.sizeof(batch_binding.BatchOptions) == 96
+    assert ctypes.sizeof(batch_binding.Tiling) == 16
+    assert ctypes.sizeof(batch_binding.Trial) == 24
 
 
 @pytest.mark.parametrize("n,Ra", [(32, 1e3), (128, 1e5), (256, 1e6), (91, 1e4)])
