@@ -297,7 +297,7 @@ def batch_variant(lbm, steps, warmup, peak, converge_steps=0):
         "sequential_per_cavity_launches": res["sequential"],
         "speedup_vs_sequential": round(res["graph"]["value"] / res["sequential"]["value"], 3),
         "tiling": tiling,
-        "autotune": [{k: t[k] for k in ("threads", "min_blocks", "mapping", "blocks_per_sm")}
+        "autotune": [{k: t[k] for k in ("threads", "min_blocks", "mapping", "blocks_per_sm", "tile_factor")}
                      | {"ms": round(t["ms_per_step"], 4)} for t in trials],
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "kernel": "batch_step_kernel<float,15>",
@@ -309,6 +309,8 @@ def batch_variant(lbm, steps, warmup, peak, converge_steps=0):
     b.close()
     if converge_steps > 0:
         out["to_convergence"] = batch_to_convergence(lbm, members, converge_steps)
+        out["to_convergence_sequential"] = batch_to_convergence(lbm, members, converge_steps,
+                                                                mode="sequential")
     return out
 
 
@@ -324,9 +326,11 @@ def time_steps_mode(b, steps, stream, mode):
     return start.elapsed_time(end) / 1e3
 
 
-def batch_to_convergence(lbm, members, max_steps, tol=1e-6):
+def batch_to_convergence(lbm, members, max_steps, tol=1e-6, mode="graph"):
     """Every member of the sweep from rest until its own max |dT| over 100 steps falls
-    below tol (FP32 floor: see time_to_steady) or it diverges, up to max_steps."""
+    below tol (FP32 floor: see time_to_steady) or it diverges, up to max_steps; `mode`
+    "sequential" advances the same members with one single-cavity launch per member and
+    step (the plain method, cavity after cavity) under the same stopping rule."""
     import torch
     b = lbm.Batch(members, precision=lbm.FP32, residual_interval=RESIDUAL_INTERVAL,
                   steady_tol=tol)
@@ -334,7 +338,7 @@ def batch_to_convergence(lbm, members, max_steps, tol=1e-6):
     t0 = time.perf_counter()
     done_at = []
     while b.steps_done < max_steps and b.active_nodes > 0:
-        b.step(min(10_000, max_steps - b.steps_done))
+        b.step(min(10_000, max_steps - b.steps_done), mode=mode)
         done_at.append((b.steps_done, round(time.perf_counter() - t0, 2), b.active_nodes))
     dt = time.perf_counter() - t0
     st = b.status()
@@ -349,7 +353,7 @@ def batch_to_convergence(lbm, members, max_steps, tol=1e-6):
     ncell = [m["grid"][0] ** 3 for m in members]
     lups = sum(c * s["steps"] for c, s in zip(ncell, st))
     b.close()
-    return {"tol": tol, "max_steps": max_steps, "seconds": round(dt, 2),
+    return {"mode": mode, "tol": tol, "max_steps": max_steps, "seconds": round(dt, 2),
             "converged": len(conv), "diverged": sum(1 for s in st if s["state"] == "diverged"),
             "active": sum(1 for s in st if s["state"] == "active"),
             "steps_min_median_max": [min(conv), sorted(conv)[len(conv) // 2], max(conv)] if conv else None,

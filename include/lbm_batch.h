@@ -17,9 +17,10 @@
  *
  * Tiling.  The tile shape and the block shape are chosen by measurement (an autotuner
  * that times every candidate on the batch itself, lbm_batch_autotune) or set by the
- * caller.  Candidates: threads per block (= nodes per tile) 128 or 256, the register
- * budget the kernel is built for (min_blocks), tiles of consecutive nodes or of whole
- * x-rows, and a persistent grid (blocks_per_sm blocks per SM) or one block per tile.
+ * caller.  Candidates: threads per block 128 or 256, the register budget the kernel is
+ * built for (min_blocks), tiles of consecutive nodes or of whole x-rows, 1, 2 or 4 nodes
+ * per thread and tile, and a persistent grid (blocks_per_sm blocks per SM, taking tiles
+ * from a queue) or one block per tile.
  *
  * Errors and threading follow include/lbm.h: LBM_OK or a negative LBM_E* code, the
  * message in lbm_batch_last_error; a batch is not thread-safe.
@@ -37,8 +38,8 @@ typedef struct lbm_batch lbm_batch;
 
 /* Member states (lbm_batch_status). */
 enum { LBM_MEMBER_ACTIVE = 0, LBM_MEMBER_CONVERGED = 1, LBM_MEMBER_DIVERGED = 2 };
-/* Tile shapes: `threads` consecutive nodes of one cavity, or whole x-rows (as many as
- * fit in `threads`; a row longer than `threads` is cut into segments). */
+/* Tile shapes: threads * tile_factor consecutive nodes of one cavity, or whole x-rows
+ * (as many as fit in that budget; a longer row is cut into segments). */
 enum { LBM_TILE_LINEAR = 0, LBM_TILE_ROWS = 1 };
 /* How lbm_batch_step_with launches: captured graphs of the persistent kernel (the
  * default), one persistent-kernel launch per step, or, for comparison, one lbm_step
@@ -46,13 +47,15 @@ enum { LBM_TILE_LINEAR = 0, LBM_TILE_ROWS = 1 };
 enum { LBM_BATCH_GRAPH = 0, LBM_BATCH_LAUNCH = 1, LBM_BATCH_SEQUENTIAL = 2 };
 
 typedef struct {
-    int threads;       /* threads per block = nodes per tile: 128 or 256 */
+    int threads;       /* threads per block: 128 or 256 */
     int min_blocks;    /* resident blocks per SM the kernel build is constrained to (its
                           register budget).  FP32, D3Q15: 5 or 6 (128 threads), 2 or 3
                           (256); FP32, D3Q7: 6 or 7 (128), 2 or 3 (256); FP64: 1 */
     int mapping;       /* LBM_TILE_LINEAR or LBM_TILE_ROWS */
     int blocks_per_sm; /* persistent blocks per SM (1 .. the build's occupancy);
                           0 = one block per tile (not persistent) */
+    int tile_factor;   /* nodes per tile = threads * tile_factor (1, 2 or 4): each thread
+                          updates tile_factor nodes of a tile, one after another */
 } lbm_batch_tiling;
 
 typedef struct {

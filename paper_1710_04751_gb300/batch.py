@@ -25,7 +25,7 @@ EXPORTS = (
 
 class Tiling(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("min_blocks", ctypes.c_int), ("mapping", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("tile_factor", ctypes.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -211,9 +211,9 @@ class Batch:
         self._check(self._L.lbm_batch_set_tiling(self._b, ctypes.byref(t)))
 
     def autotune(self, trial_steps=3):
-        trials = (Trial * 64)()
+        trials = (Trial * 128)()
         n = ctypes.c_int()
-        self._check(self._L.lbm_batch_autotune(self._b, int(trial_steps), trials, 64, ctypes.byref(n)))
+        self._check(self._L.lbm_batch_autotune(self._b, int(trial_steps), trials, 128, ctypes.byref(n)))
         return [dict(t.tiling.as_dict(), ms_per_step=t.ms_per_step) for t in trials[:n.value]]
 
     def synchronize(self):

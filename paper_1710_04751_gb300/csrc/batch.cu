@@ -28,7 +28,7 @@ struct BatchMember {
     int pad;
 };
 
-// A run of `count` nodes of one member starting at node c0 (count <= threads per block).
+// A run of `count` nodes of one member starting at node c0 (count <= nodes per tile).
 struct BatchTile {
     int member, c0, count, pad;
 };
@@ -124,9 +124,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
         int claim = 0;
         if (threadIdx.x == 0) claim = atomicAdd(queue + parity, 1);
         const BatchMember<S>& m = member_of<S>(cache, members, tile.member, cache_all, loaded);
-        if ((int)threadIdx.x < tile.count) {
-            if constexpr (SWEEP) batch_node<S, Q>(m, sweep_params<S>(base, m.p), tile.c0 + threadIdx.x, parity);
-            else batch_node<S, Q>(m, m.p, tile.c0 + threadIdx.x, parity);
+        for (int c = threadIdx.x; c < tile.count; c += THREADS) {
+            if constexpr (SWEEP) batch_node<S, Q>(m, sweep_params<S>(base, m.p), tile.c0 + c, parity);
+            else batch_node<S, Q>(m, m.p, tile.c0 + c, parity);
         }
         __syncthreads();  // every thread has read next_tile for this iteration
         if (threadIdx.x == 0) next_tile = claim;
@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(256)
             cur = tile.member;
         }
         const BatchMember<S>& m = member_of<S>(cache, members, tile.member, cache_all, loaded);
-        if ((int)threadIdx.x < tile.count) {
-            const int64_t c = tile.c0 + threadIdx.x;
+        for (int n = threadIdx.x; n < tile.count; n += blockDim.x) {
+            const int64_t c = tile.c0 + n;
             const S* G = m.G[parity];
             real T = real(0);
 #pragma unroll
@@ -297,8 +297,9 @@ static bool member_fits(const lbm_grid& g) {
 }
 
 // Tiles of one member for a mapping and block size, appended to out (or counted).
-static int64_t member_tiles(const lbm_grid& g, int member, int threads, int mapping,
+static int64_t member_tiles(const lbm_grid& g, int member, int tile_nodes, int mapping,
                             BatchTile* out) {
+    const int threads = tile_nodes;
     const int nx = g.nx;
     const int64_t ncell = (int64_t)g.nx * g.ny * g.nz, rows = (int64_t)g.ny * g.nz;
     int64_t n = 0;
@@ -320,7 +321,7 @@ static int64_t member_tiles(const lbm_grid& g, int member, int threads, int mapp
 
 static int64_t max_tile_count(int count, const lbm_grid* grids) {
     int64_t best = 0;
-    for (int threads : {128, 256})
+    for (int threads : {128, 256})  // the smallest tiles give the most
         for (int mapping : {LBM_TILE_LINEAR, LBM_TILE_ROWS}) {
             int64_t n = 0;
             for (int m = 0; m < count; ++m) n += member_tiles(grids[m], m, threads, mapping, nullptr);
@@ -407,7 +408,8 @@ static int rebuild_tiles(lbm_batch* b) {
     int64_t n = 0;
     for (int m = 0; m < b->count; ++m)
         if (b->state[m] == LBM_MEMBER_ACTIVE)
-            n += member_tiles(b->members[m]->grid, m, b->tiling.threads, b->tiling.mapping,
+            n += member_tiles(b->members[m]->grid, m, b->tiling.threads * b->tiling.tile_factor,
+                              b->tiling.mapping,
                               b->h_tiles + n);
     b->n_tiles = (int)n;
     *b->h_ntiles = (int)n;
@@ -426,7 +428,8 @@ static int apply_tiling(lbm_batch* b, const lbm_batch_tiling& t) {
     const Variant* v = nullptr;
     for (int i = 0; i < nv; ++i)
         if (vs[i].threads == t.threads && vs[i].min_blocks == t.min_blocks) v = &vs[i];
-    if (!v || (t.mapping != LBM_TILE_LINEAR && t.mapping != LBM_TILE_ROWS) || t.blocks_per_sm < 0)
+    if (!v || (t.mapping != LBM_TILE_LINEAR && t.mapping != LBM_TILE_ROWS) || t.blocks_per_sm < 0 ||
+        (t.tile_factor != 1 && t.tile_factor != 2 && t.tile_factor != 4))
         return bfail(b, LBM_EINVAL, "tiling is not a candidate of this precision and lattice%s");
     int cache_all = 0;
     const size_t smem = smem_for(b, t.blocks_per_sm, &cache_all);
@@ -732,7 +735,7 @@ extern "C" int lbm_batch_create(int count, const lbm_grid* grids, int lattice,
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, vs[0].fn, vs[0].threads,
                                                       smem_for(b, 1, &cache_all));
         rc = apply_tiling(b, lbm_batch_tiling{vs[0].threads, vs[0].min_blocks, LBM_TILE_LINEAR,
-                                              std::max(1, occ)});
+                                              std::max(1, occ), 1});
         if (rc == LBM_OK && o.autotune_steps > 0)
             rc = lbm_batch_autotune(b, o.autotune_steps, nullptr, 0, nullptr);
     }
@@ -830,8 +833,9 @@ extern "C" int lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_trial
         BATCH_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, vs[v].fn, vs[v].threads, smem));
         if (occ < 1) continue;
         for (int mapping : {LBM_TILE_LINEAR, LBM_TILE_ROWS})
-            for (int bps : {occ, 0})
-                res.push_back(lbm_batch_trial{{vs[v].threads, vs[v].min_blocks, mapping, bps}, 0.0});
+            for (int factor : {1, 2, 4})
+                for (int bps : {occ, 0})
+                    res.push_back(lbm_batch_trial{{vs[v].threads, vs[v].min_blocks, mapping, bps, factor}, 0.0});
     }
     cudaEvent_t e0, e1;
     BATCH_CUDA(b, cudaEventCreate(&e0));

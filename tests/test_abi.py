@@ -42,10 +42,10 @@ def test_structure_sizes_match_header_layout():
     assert ctypes.sizeof(binding.Params) == (15 + 15 + 4 + 3 + 2) * 8 + 16
     assert ctypes.sizeof(binding.Nu) == 11 * 8
     # lbm_batch_options: int (+4), u64, double, int (+4), double, 3 pointers/sizes, int,
-    # the 4-int tiling, (+4) double
+    # the 5-int tiling, double
     assert ctypes.sizeof(batch_binding.BatchOptions) == 96
-    assert ctypes.sizeof(batch_binding.Tiling) == 16
-    assert ctypes.sizeof(batch_binding.Trial) == 24
+    assert ctypes.sizeof(batch_binding.Tiling) == 20
+    assert ctypes.sizeof(batch_binding.Trial) == 32
 
 
 @pytest.mark.parametrize("n,Ra", [(32, 1e3), (128, 1e5), (256, 1e6), (91, 1e4)])

@@ -126,7 +126,7 @@ def test_modes_and_tilings_are_bitwise_equal():
     want = [ref.member(i).get_populations() for i in range(len(members))]
     for t in trials:
         for mode in ("graph", "launch"):
-            tiling = {k: t[k] for k in ("threads", "min_blocks", "mapping", "blocks_per_sm")}
+            tiling = {k: t[k] for k in ("threads", "min_blocks", "mapping", "blocks_per_sm", "tile_factor")}
             b = lbm.Batch(members, precision=lbm.FP32, residual_interval=10, tiling=tiling)
             assert b.tiling == tiling
             b.step(30, mode=mode)
@@ -216,10 +216,14 @@ def test_invalid_batches_are_rejected():
     with pytest.raises(lbm.LBMError):
         lbm.Batch(one, residual_interval=7)
     with pytest.raises(lbm.LBMError):
-        lbm.Batch(one, tiling={"threads": 96, "min_blocks": 1, "mapping": 0, "blocks_per_sm": 1})
+        lbm.Batch(one, tiling={"threads": 96, "min_blocks": 1, "mapping": 0, "blocks_per_sm": 1,
+                               "tile_factor": 1})
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch(one, tiling={"threads": 128, "min_blocks": 6, "mapping": 0, "blocks_per_sm": 1,
+                               "tile_factor": 3})
     b = lbm.Batch(one, autotune_steps=0)
     with pytest.raises(lbm.LBMError):
-        b.set_tiling(threads=128, min_blocks=6, mapping=0, blocks_per_sm=10_000)
+        b.set_tiling(threads=128, min_blocks=6, mapping=0, blocks_per_sm=10_000, tile_factor=1)
     b.close()
 
 
@@ -229,11 +233,14 @@ def test_autotuner_times_every_candidate_and_keeps_the_fastest():
     b = lbm.Batch(members, precision=lbm.FP32, autotune_steps=0)
     f0 = [b.member(i).get_populations() for i in range(3)]
     trials = b.autotune(trial_steps=2)
-    assert len(trials) == 16  # 4 kernel builds x 2 tile shapes x persistent / one block per tile
-    assert len({(t["threads"], t["min_blocks"], t["mapping"], t["blocks_per_sm"] > 0) for t in trials}) == 16
+    # 4 kernel builds x 2 tile shapes x 3 tile sizes x persistent / one block per tile
+    assert len(trials) == 48
+    assert len({(t["threads"], t["min_blocks"], t["mapping"], t["tile_factor"], t["blocks_per_sm"] > 0)
+                for t in trials}) == 48
     assert all(t["ms_per_step"] > 0 for t in trials)
     best = min(trials, key=lambda t: t["ms_per_step"])
-    assert b.tiling == {k: best[k] for k in ("threads", "min_blocks", "mapping", "blocks_per_sm")}
+    assert b.tiling == {k: best[k] for k in ("threads", "min_blocks", "mapping", "blocks_per_sm",
+                                             "tile_factor")}
     for i in range(3):  # tuning leaves the state alone
         f, g = b.member(i).get_populations()
         assert np.array_equal(f, f0[i][0]) and np.array_equal(g, f0[i][1])
