@@ -28,13 +28,19 @@ def nvcc():
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liblbm.so")
 
 
+def _walk(exts):
+    out = []
+    for d, _, files in os.walk(CSRC):
+        out += [os.path.join(d, f) for f in files if f.endswith(exts)]
+    return sorted(out)
+
+
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    return _walk((".cu",))
 
 
 def _deps():
-    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC)
-                         if f.endswith((".cuh", ".h"))]
+    files = sources() + _walk((".cuh", ".h"))
     inc = os.path.join(ROOT, "include")
     files += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     files.append(os.path.abspath(__file__))
@@ -56,7 +62,7 @@ def build(force=False, verbose=False, extra_flags=()):
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(BUILD, os.path.relpath(src, CSRC).replace(os.sep, "_") + ".o")
         cmd = [cc] + ARCH + NVCC_FLAGS + list(extra_flags) + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd))

@@ -1,0 +1,60 @@
+// api_nn.cu -- the C ABI of include/lbm_net.h.
+#include <mutex>
+
+#include "../context.h"
+#include "lbm_net.h"
+#include "nn.h"
+
+using namespace lbm;
+
+namespace {
+
+// Per-device error word the network kernels write on a timeout.
+__device__ int nn_error_word;
+
+int* error_word() {
+    static int* ptr[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    if (!ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, nn_error_word) != cudaSuccess) return nullptr;
+        ptr[dev] = static_cast<int*>(p);
+    }
+    return ptr[dev];
+}
+
+// Waits for the stream and turns a recorded kernel timeout into LBM_ETIMEOUT.
+int finish(cudaStream_t st, int* err) {
+    int rc = wait_stream_for(st, 600.0, nullptr);
+    if (rc != LBM_OK) return rc;
+    int h = 0;
+    if (cudaMemcpy(&h, err, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return record_error(nullptr, LBM_ECUDA, "reading the network error word failed%s");
+    if (h != 0) {
+        cudaMemset(err, 0, sizeof(int));
+        return record_error(nullptr, LBM_ETIMEOUT, "a wait inside a tensor-core kernel timed out%s");
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" int lbm_nn_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, void* C,
+                                int64_t ldc, int M, int N, int K, int out_mode, int splits,
+                                void* cuda_stream) {
+    if (!A || !B || !C || ldc < N)
+        return record_error(nullptr, LBM_EINVAL, "NULL operand or ldc < N%s");
+    int* err = error_word();
+    if (!err) return record_error(nullptr, LBM_ECUDA, "no CUDA device%s");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const cudaError_t e = nn::gemm_bf16(static_cast<const __nv_bfloat16*>(A), lda,
+                                        static_cast<const __nv_bfloat16*>(B), ldb, C, ldc, M, N, K,
+                                        out_mode, splits, err, st);
+    if (e == cudaErrorInvalidValue)
+        return record_error(nullptr, LBM_EINVAL, "invalid GEMM shape, stride, alignment or mode%s");
+    if (e != cudaSuccess) return record_error(nullptr, LBM_ECUDA, "GEMM launch failed: %s", cudaGetErrorString(e));
+    return finish(st, err);
+}

@@ -1,0 +1,237 @@
+// gemm.cu -- BF16 GEMM with FP32 accumulation on the tcgen05 tensor cores:
+//   C[M][N] (+)= sum_k A[m][k] * B[n][k]      (both operands K-major, row-major storage)
+// One CTA of 128 threads computes a 128 x BN tile: warp 0 lane 0 streams 128 x 64 and
+// BN x 64 operand tiles into a 4-stage shared-memory ring with TMA (128-byte swizzle);
+// warp 1 lane 0 issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a TMEM
+// accumulator and frees each stage with tcgen05.commit; then all four warps read the
+// accumulator back (warp w owns TMEM lanes 32w..32w+31 = rows 32w..32w+31) and store it.
+// grid.z splits K; the split results are added with FP32 atomics.  Rows, columns and K
+// beyond the operands' extents read as zeros (TMA out-of-bounds fill) and are not stored.
+// Every wait is bounded (2 s): on a timeout the kernel records an error code, lets its
+// copies and MMAs drain, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "nn.h"
+#include "tc.cuh"
+
+namespace lbm {
+namespace nn {
+
+constexpr int BM = 128, BK = 64, STAGES = 4;
+
+template <int BN>
+struct GemmSmem {
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int BYTES = 1024 + STAGES * STAGE + 256;  // + alignment + barriers
+    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+struct GemmArgs {
+    int M, N, K;
+    int kblocks_per_split;
+    int out_mode;  // GEMM_F32, GEMM_BF16, GEMM_F32_ATOMIC
+    void* C;
+    long long ldc;
+    int* err;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA,
+                        const __grid_constant__ CUtensorMap tmB, GemmArgs args) {
+    using L = GemmSmem<BN>;
+    extern __shared__ uint8_t gemm_smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L::STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ volatile int failed;
+
+    // a CTA that starts after another one timed out does nothing
+    if (*static_cast<volatile int*>(args.err) != 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int kb_total = (args.K + BK - 1) / BK;
+    const int kb0 = blockIdx.z * args.kblocks_per_split;
+    const int nkb = min(args.kblocks_per_split, kb_total - kb0);
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(done, 1);
+        mbar_fence_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, L::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0;  // producer: stages loaded
+    if (nkb > 0 && warp == 0 && lane == 0) {
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % STAGES;
+            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (i >= STAGES && !mbar_wait(empty + s, ph ^ 1u, args.err, 1, &failed)) {
+                failed = 1;
+                break;
+            }
+            if (failed) break;
+            uint8_t* a = smem + s * L::STAGE;
+            mbar_expect_tx(full + s, L::STAGE);
+            tma_load_2d(a, &tmA, full + s, (kb0 + i) * BK, m0);
+            tma_load_2d(a + L::A_BYTES, &tmB, full + s, (kb0 + i) * BK, n0);
+            ++issued;
+        }
+    } else if (nkb > 0 && warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_bf16_f32(BM, BN);
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % STAGES;
+            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (failed || !mbar_wait(full + s, ph, args.err, 2, &failed)) {
+                failed = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a = smem_u32(smem + s * L::STAGE), b = a + L::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(tmem, sdesc_k_sw128(a + kk * 32), sdesc_k_sw128(b + kk * 32), idesc,
+                         (i > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(empty + s);
+        }
+        mma_commit(done);  // also when stopped early: every issued MMA drains before dealloc
+    }
+    __syncwarp();
+    // the accumulator is complete (or the MMA thread gave up) once `done` fires
+    if (nkb > 0 && !mbar_wait(done, 0, args.err, 3)) failed = 1;  // no early exit: MMAs drain
+    __syncthreads();
+    const bool ok = nkb > 0 && !failed;  // block-uniform
+    if (warp == 0 && lane == 0 && failed) {
+        // let every TMA copy this CTA started land before its shared memory goes away
+        for (int i = max(0, issued - STAGES); i < issued; ++i)
+            mbar_wait(full + (i % STAGES), (uint32_t)(i / STAGES) & 1u, args.err, 4);
+    }
+    tc_fence_after();
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            if (row < args.M) {
+                const int col0 = n0 + c;
+                if (args.out_mode == GEMM_BF16) {
+                    __nv_bfloat16* C = static_cast<__nv_bfloat16*>(args.C) + row * args.ldc;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (col0 + j < args.N) C[col0 + j] = __float2bfloat16_rn(v[j]);
+                } else if (args.out_mode == GEMM_F32) {
+                    float* C = static_cast<float*>(args.C) + row * args.ldc;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (col0 + j < args.N) C[col0 + j] = v[j];
+                } else {
+                    float* C = static_cast<float*>(args.C) + row * args.ldc;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (col0 + j < args.N) atomicAdd(C + col0 + j, v[j]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, L::TMEM_COLS);
+}
+
+// -------------------------------------------------------------------------------------
+// host side
+// -------------------------------------------------------------------------------------
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Row-major BF16 matrix [rows][cols] with row stride ld (elements), read in boxes of
+// box_rows x 64 with the 128-byte swizzle.
+static bool make_map(CUtensorMap* map, const void* base, int rows, int cols, long long ld,
+                     int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+static cudaError_t launch(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& a,
+                          int splits, cudaStream_t st) {
+    using L = GemmSmem<BN>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(gemm_bf16_tn_kernel<BN>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+    });
+    if (attr != cudaSuccess) return attr;
+    const dim3 grid((a.M + BM - 1) / BM, (a.N + BN - 1) / BN, splits);
+    gemm_bf16_tn_kernel<BN><<<grid, 128, L::BYTES, st>>>(ta, tb, a);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B,
+                      long long ldb, void* C, long long ldc, int M, int N, int K, int out_mode,
+                      int splits, int* err, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0 || (lda % 8) || (ldb % 8) || lda < K || ldb < K || splits < 1 ||
+        ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || out_mode < GEMM_F32 || out_mode > GEMM_F32_ATOMIC)
+        return cudaErrorInvalidValue;
+    const int BN = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+    const int kb_total = (K + BK - 1) / BK;
+    splits = splits > kb_total ? kb_total : splits;
+    const int per = (kb_total + splits - 1) / splits;
+    splits = (kb_total + per - 1) / per;  // every split gets at least one K block
+    if (splits > 1 && out_mode != GEMM_F32_ATOMIC) return cudaErrorInvalidValue;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, A, M, K, lda, BM) || !make_map(&tb, B, N, K, ldb, BN))
+        return cudaErrorInvalidValue;
+    GemmArgs a{M, N, K, per, out_mode, C, ldc, err};
+    switch (BN) {
+    case 32: return launch<32>(ta, tb, a, splits, st);
+    case 64: return launch<64>(ta, tb, a, splits, st);
+    case 128: return launch<128>(ta, tb, a, splits, st);
+    default: return launch<256>(ta, tb, a, splits, st);
+    }
+}
+
+}  // namespace nn
+}  // namespace lbm
