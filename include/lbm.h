@@ -161,6 +161,16 @@ int lbm_residual(lbm_ctx* ctx, double* max_dT);
 int lbm_get_populations(lbm_ctx* ctx, double* f, double* g);
 int lbm_set_populations(lbm_ctx* ctx, const double* f, const double* g);
 
+/* Set the stored populations to the equilibria of given fields: f to the populations
+ * whose central moments are the flow collision's equilibria at (rho, u) (App. A:
+ * Maxwellian, c_s^2 = 1/3), g to those whose central moments are the equilibria of
+ * Eq. (15) at (T, u).  rho, ux, uy, uz, T: caller-owned DEVICE arrays of ncell FP64
+ * values (layout above; rho NULL means rho = 1), read on the context's stream before the
+ * call returns.  Restarts the residual snapshot.  Starting the solver from a predicted
+ * steady state (the learned warm start, include/lbm_net.h) uses this. */
+int lbm_set_fields(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                   const double* uz, const double* T);
+
 /* Parameters in use, step counter, last error message, stream wait, destruction. */
 int lbm_get_params(const lbm_ctx* ctx, lbm_params* out);
 int64_t lbm_steps_done(const lbm_ctx* ctx);

@@ -35,6 +35,67 @@ int lbm_nn_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, voi
                      int64_t ldc, int M, int N, int K, int out_mode, int splits,
                      void* cuda_stream);
 
+/* ---- the network ------------------------------------------------------------------- */
+
+typedef struct lbm_net lbm_net;
+
+typedef struct {
+    int n;            /* grid edge the network is built for: a multiple of 8, 8..256 */
+    int max_batch;    /* samples per call at most */
+    int c1, c2, c3;   /* channels at the three levels n, n/2, n/4 (multiples of 8;
+                         c1 <= 64) */
+    uint64_t seed;    /* He-normal initial weights from splitmix64 + Box-Muller */
+    float lr, beta1, beta2, eps;  /* Adam (Kingma & Ba 2015) */
+    void* cuda_stream;            /* cudaStream_t or NULL */
+} lbm_net_config;
+
+/* n 64, max_batch 2, channels 32/64/128 (1.85 M parameters), seed 1, lr 1e-3,
+ * betas 0.9 / 0.999, eps 1e-8, NULL stream. */
+void lbm_net_default_config(lbm_net_config* cfg);
+
+/* Architecture (a U-Net): conv 4->c1, c1->c1 | avg-pool | c1->c2, c2->c2 | avg-pool |
+ * c2->c3, c3->c3, c3->c3 | nearest up, concat | c3+c2->c2, c2->c2 | up, concat |
+ * c2+c1->c1, c1->c1 | 1x1 c1->4.  Every conv 3x3x3 with zero padding, bias and ReLU; the
+ * 1x1 head is linear.  Inputs per voxel: distance to the nearest wall / n, heated-face
+ * mask (+1 on the hot layer, -1 on the cold one), and the sample's two encoded scalars
+ * (lbm_net_encode).  Outputs per voxel: u_x, u_y, u_z divided by U0, and 2 T. */
+int lbm_net_create(const lbm_net_config* cfg, lbm_net** out);
+void lbm_net_destroy(lbm_net* net);
+int64_t lbm_net_param_count(const lbm_net* net);
+
+/* The two encoded scalars of a sample: (log10 Ra - 4.5) / 1.5, (log10 Pr - 0.345) / 0.5. */
+void lbm_net_encode(double Ra, double Pr, float* out2);
+
+/* Parameters (grads = 0) or the gradients of the last lbm_net_gradients /
+ * lbm_net_train_step (grads = 1) to a HOST array of param_count floats: per conv layer
+ * W [cout][27 cin] (column (kz*3 + ky)*3 + kx)*cin + ci for the input at
+ * (z + kz - 1, y + ky - 1, x + kx - 1)) then b [cout]; then the head W [4][c1], b [4]. */
+int lbm_net_get_params(lbm_net* net, float* host, int64_t count, int grads);
+int lbm_net_set_params(lbm_net* net, const float* host, int64_t count);
+
+/* Predictions for `batch` samples: scalars = HOST array [batch][2] (lbm_net_encode);
+ * out = DEVICE array [batch][n^3][4] FP32, voxel ((b*n + z)*n + y)*n + x. */
+int lbm_net_forward(lbm_net* net, int batch, const float* scalars, float* out);
+/* Forward and backward without an update: *loss (HOST, may be NULL) = mean squared
+ * error against targets (DEVICE, [batch][n^3][4]); gradients via lbm_net_get_params. */
+int lbm_net_gradients(lbm_net* net, int batch, const float* scalars, const float* targets,
+                      double* loss);
+/* lbm_net_gradients followed by one Adam update of every parameter. */
+int lbm_net_train_step(lbm_net* net, int batch, const float* scalars, const float* targets,
+                       double* loss);
+const char* lbm_net_last_error(const lbm_net* net);
+
+/* ---- the bridge to the solver ------------------------------------------------------- */
+
+/* Training targets of a context's current state into a DEVICE array [ncell][4] FP32:
+ * (u_x, u_y, u_z) / U0 and 2 T, u and T as lbm_fields defines them. */
+int lbm_net_targets(lbm_ctx* ctx, float* out);
+/* Start a context from a prediction: pred = DEVICE array [m^3][4] on a cell-centred m^3
+ * grid covering the cavity, resampled trilinearly onto the context's grid (identity
+ * when m equals it), scaled back (u = p U0, T = p / 2), and set as equilibria with
+ * rho = 1 (lbm_set_fields). */
+int lbm_net_warm_start(lbm_ctx* ctx, const float* pred, int m);
+
 #ifdef __cplusplus
 }
 #endif

@@ -502,6 +502,22 @@ extern "C" int lbm_set_populations(lbm_ctx* c, const double* f, const double* g)
     });
 }
 
+extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* ux, const double* uy,
+                              const double* uz, const double* T) {
+    if (!c || !ux || !uy || !uz || !T) return fail(c, LBM_EINVAL, "NULL argument%s");
+    DeviceGuard gd(c->device);
+    int rc = with_storage(c->precision, [&](auto tag) {
+        using S = decltype(tag);
+        const ParamsOf<S> p = dev_params<typename Storage<S>::real>(c);
+        CUDA_OR_FAIL(c, launch_set_fields<S>(c->dev, c->cur, p, rho, ux, uy, uz, T, c->stream));
+        CUDA_OR_FAIL(c, launch_residual<S>(c->dev, c->cur, p, 0, c->stream));
+        return LBM_OK;
+    });
+    if (rc != LBM_OK) return rc;
+    c->last_residual = -1.0;
+    return wait_stream(c);
+}
+
 extern "C" int lbm_get_params(const lbm_ctx* c, lbm_params* out) {
     if (!c || !out) return LBM_EINVAL;
     *out = c->params;

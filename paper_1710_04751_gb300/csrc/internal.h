@@ -81,6 +81,13 @@ cudaError_t launch_nusselt_into(const S* F, const S* G, const ParamsOf<S>& p, do
                                 int Q, int blocks, double* partials, double* result,
                                 cudaStream_t st);
 
+// Populations of buffer `cur` set to the equilibria of the given device fields (rho NULL:
+// 1), in every storage form.
+template <typename S>
+cudaError_t launch_set_fields(const DevState& s, int cur, const ParamsOf<S>& p, const double* rho,
+                              const double* ux, const double* uy, const double* uz,
+                              const double* T, cudaStream_t st);
+
 // Message returned by lbm_last_error(NULL) on this thread.
 void set_last_error(const char* msg);
 

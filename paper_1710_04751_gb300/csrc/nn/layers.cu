@@ -1,0 +1,489 @@
+// layers.cu -- the non-GEMM kernels of the warm-start network.  Activations are
+// channels-last, [voxel][channel] with voxel = ((b * n + z) * n + y) * n + x, BF16 where a
+// GEMM reads them and FP32 for gradients.  A 3x3x3 convolution with zero padding is the
+// GEMM of its im2col matrix: row = output voxel, column k = tap * cin + ci with
+// tap = (kz * 3 + ky) * 3 + kx reading the input at (z + kz - 1, y + ky - 1, x + kx - 1),
+// columns padded with zeros to a multiple of 64.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "nn.h"
+
+namespace lbm {
+namespace nn {
+
+__device__ __forceinline__ int64_t vox(int b, int z, int y, int x, int n) {
+    return (((int64_t)b * n + z) * n + y) * n + x;
+}
+
+static unsigned blocks_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)(b > 1048576 ? 1048576 : b);
+}
+
+// ---- im2col --------------------------------------------------------------------------
+// 8 channels (16 bytes) per thread when cin % 8 == 0, else one element per thread.
+__global__ void im2col8_kernel(const __nv_bfloat16* __restrict__ X, int B, int n, int cin, int Kp,
+                               __nv_bfloat16* __restrict__ Xcol) {
+    const int kq = Kp / 8;
+    const int64_t total = (int64_t)B * n * n * n * kq;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = q / kq;
+        const int k = (int)(q - m * kq) * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (k < 27 * cin) {
+            const int tap = k / cin, ci = k - tap * cin;
+            const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
+            const int x = (int)(m % n), y = (int)((m / n) % n), z = (int)((m / ((int64_t)n * n)) % n);
+            const int b = (int)(m / ((int64_t)n * n * n));
+            const int sz = z + kz - 1, sy = y + ky - 1, sx = x + kx - 1;
+            if ((unsigned)sz < (unsigned)n && (unsigned)sy < (unsigned)n && (unsigned)sx < (unsigned)n)
+                v = *reinterpret_cast<const uint4*>(X + vox(b, sz, sy, sx, n) * cin + ci);
+        }
+        *reinterpret_cast<uint4*>(Xcol + m * Kp + k) = v;
+    }
+}
+
+__global__ void im2col1_kernel(const __nv_bfloat16* __restrict__ X, int B, int n, int cin, int Kp,
+                               __nv_bfloat16* __restrict__ Xcol) {
+    const int64_t total = (int64_t)B * n * n * n * Kp;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = q / Kp;
+        const int k = (int)(q - m * Kp);
+        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+        if (k < 27 * cin) {
+            const int tap = k / cin, ci = k - tap * cin;
+            const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
+            const int x = (int)(m % n), y = (int)((m / n) % n), z = (int)((m / ((int64_t)n * n)) % n);
+            const int b = (int)(m / ((int64_t)n * n * n));
+            const int sz = z + kz - 1, sy = y + ky - 1, sx = x + kx - 1;
+            if ((unsigned)sz < (unsigned)n && (unsigned)sy < (unsigned)n && (unsigned)sx < (unsigned)n)
+                v = X[vox(b, sz, sy, sx, n) * cin + ci];
+        }
+        Xcol[m * Kp + k] = v;
+    }
+}
+
+cudaError_t im2col(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_bfloat16* Xcol,
+                   cudaStream_t st) {
+    const int64_t M = (int64_t)B * n * n * n;
+    if (cin % 8 == 0)
+        im2col8_kernel<<<blocks_for(M * (Kp / 8), 256), 256, 0, st>>>(X, B, n, cin, Kp, Xcol);
+    else
+        im2col1_kernel<<<blocks_for(M * Kp, 256), 256, 0, st>>>(X, B, n, cin, Kp, Xcol);
+    return cudaGetLastError();
+}
+
+// ---- col2im (adjoint of im2col) ------------------------------------------------------
+// dX[v][ci] (+)= sum over taps of dXcol[u][tap * cin + ci], u the voxel whose tap reads v.
+__global__ void col2im_kernel(const __nv_bfloat16* __restrict__ dXcol, int B, int n, int cin,
+                              int Kp, float* __restrict__ dX, int accumulate) {
+    const int64_t total = (int64_t)B * n * n * n * cin;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = q / cin;
+        const int ci = (int)(q - v * cin);
+        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)((v / ((int64_t)n * n)) % n);
+        const int b = (int)(v / ((int64_t)n * n * n));
+        float s = 0.f;
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+            const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
+            const int uz = z - kz + 1, uy = y - ky + 1, ux = x - kx + 1;
+            if ((unsigned)uz < (unsigned)n && (unsigned)uy < (unsigned)n && (unsigned)ux < (unsigned)n)
+                s += __bfloat162float(dXcol[vox(b, uz, uy, ux, n) * Kp + tap * cin + ci]);
+        }
+        dX[q] = accumulate ? dX[q] + s : s;
+    }
+}
+
+cudaError_t col2im(const __nv_bfloat16* dXcol, int B, int n, int cin, int Kp, float* dX,
+                   int accumulate, cudaStream_t st) {
+    const int64_t total = (int64_t)B * n * n * n * cin;
+    col2im_kernel<<<blocks_for(total, 256), 256, 0, st>>>(dXcol, B, n, cin, Kp, dX, accumulate);
+    return cudaGetLastError();
+}
+
+// ---- transpose of a BF16 matrix (32 x 32 tiles through shared memory) -----------------
+__global__ void transpose_kernel(const __nv_bfloat16* __restrict__ in, int64_t R, int64_t C,
+                                 int64_t ld_in, __nv_bfloat16* __restrict__ out, int64_t ld_out) {
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) tile[i][threadIdx.x] = in[r * ld_in + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[c * ld_out + r] = tile[threadIdx.x][i];
+    }
+}
+
+cudaError_t transpose(const __nv_bfloat16* in, int64_t R, int64_t C, int64_t ld_in,
+                      __nv_bfloat16* out, int64_t ld_out, cudaStream_t st) {
+    const int64_t gy = (R + 31) / 32, gx = (C + 31) / 32;
+    if (gy > 65535) {  // long matrices: in slabs of 65535 tile rows
+        for (int64_t r = 0; r < R; r += 65535 * 32) {
+            const int64_t rr = R - r < 65535 * 32 ? R - r : 65535 * 32;
+            cudaError_t e = transpose(in + r * ld_in, rr, C, ld_in, out + r, ld_out, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    transpose_kernel<<<dim3((unsigned)gx, (unsigned)gy), dim3(32, 8), 0, st>>>(in, R, C, ld_in, out,
+                                                                            ld_out);
+    return cudaGetLastError();
+}
+
+// ---- bias + ReLU -------------------------------------------------------------------------
+__global__ void bias_relu_kernel(const float* __restrict__ Y, const float* __restrict__ bias,
+                                 int64_t M, int C, __nv_bfloat16* __restrict__ A, int64_t ldA,
+                                 int c_off) {
+    const int64_t total = M * C;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = q / C;
+        const int c = (int)(q - m * C);
+        A[m * ldA + c_off + c] = __float2bfloat16_rn(fmaxf(Y[q] + bias[c], 0.f));
+    }
+}
+
+cudaError_t bias_relu(const float* Y, const float* bias, int64_t M, int C, __nv_bfloat16* A,
+                      int64_t ldA, int c_off, cudaStream_t st) {
+    bias_relu_kernel<<<blocks_for(M * C, 256), 256, 0, st>>>(Y, bias, M, C, A, ldA, c_off);
+    return cudaGetLastError();
+}
+
+// dZ = dA where A > 0 (BF16, the GEMM operand), db[c] += sum_m dZ (FP32 per block, then
+// one atomic per channel and block).  C <= 256, blockDim = 256.
+__global__ void relu_bwd_kernel(const float* __restrict__ dA, const __nv_bfloat16* __restrict__ A,
+                                int64_t ldA, int a_off, int64_t M, int C,
+                                __nv_bfloat16* __restrict__ dZ, float* __restrict__ db) {
+    __shared__ float acc[256];
+    for (int c = threadIdx.x; c < C; c += blockDim.x) acc[c] = 0.f;
+    __syncthreads();
+    const int64_t total = M * C;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = q / C;
+        const int c = (int)(q - m * C);
+        const float g = __bfloat162float(A[m * ldA + a_off + c]) > 0.f ? dA[q] : 0.f;
+        dZ[q] = __float2bfloat16_rn(g);
+        atomicAdd(&acc[c], g);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(db + c, acc[c]);
+}
+
+cudaError_t relu_bwd(const float* dA, const __nv_bfloat16* A, int64_t ldA, int a_off, int64_t M,
+                     int C, __nv_bfloat16* dZ, float* db, cudaStream_t st) {
+    if (C > 256) return cudaErrorInvalidValue;
+    const int64_t total = M * C;
+    unsigned blocks = blocks_for(total, 256);
+    if (blocks > 4096) blocks = 4096;
+    relu_bwd_kernel<<<blocks, 256, 0, st>>>(dA, A, ldA, a_off, M, C, dZ, db);
+    return cudaGetLastError();
+}
+
+// ---- 2x average pooling and nearest upsampling (n = the fine grid) ---------------------
+__global__ void avgpool_kernel(const __nv_bfloat16* __restrict__ X, int B, int n, int C,
+                               __nv_bfloat16* __restrict__ P) {
+    const int h = n / 2;
+    const int64_t total = (int64_t)B * h * h * h * C;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = q / C;
+        const int c = (int)(q - v * C);
+        const int x = (int)(v % h), y = (int)((v / h) % h), z = (int)((v / ((int64_t)h * h)) % h);
+        const int b = (int)(v / ((int64_t)h * h * h));
+        float s = 0.f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d)
+            s += __bfloat162float(X[vox(b, 2 * z + (d >> 2), 2 * y + ((d >> 1) & 1), 2 * x + (d & 1), n) * C + c]);
+        P[q] = __float2bfloat16_rn(0.125f * s);
+    }
+}
+
+__global__ void avgpool_bwd_kernel(const float* __restrict__ dP, int B, int n, int C,
+                                   float* __restrict__ dX, int accumulate) {
+    const int h = n / 2;
+    const int64_t total = (int64_t)B * n * n * n * C;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = q / C;
+        const int c = (int)(q - v * C);
+        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)((v / ((int64_t)n * n)) % n);
+        const int b = (int)(v / ((int64_t)n * n * n));
+        const float g = 0.125f * dP[vox(b, z / 2, y / 2, x / 2, h) * C + c];
+        dX[q] = accumulate ? dX[q] + g : g;
+    }
+}
+
+// U[fine voxel][c_off + c] = X[coarse voxel][c] (U has row stride ldU)
+__global__ void upsample_kernel(const __nv_bfloat16* __restrict__ X, int B, int n, int C,
+                                __nv_bfloat16* __restrict__ U, int64_t ldU, int c_off) {
+    const int h = n / 2;
+    const int64_t total = (int64_t)B * n * n * n * C;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = q / C;
+        const int c = (int)(q - v * C);
+        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)((v / ((int64_t)n * n)) % n);
+        const int b = (int)(v / ((int64_t)n * n * n));
+        U[v * ldU + c_off + c] = X[vox(b, z / 2, y / 2, x / 2, h) * C + c];
+    }
+}
+
+// dX[coarse][c] = sum of the 8 fine children dU[child][c_off + c]
+__global__ void upsample_bwd_kernel(const float* __restrict__ dU, int64_t ldU, int c_off, int B,
+                                    int n, int C, float* __restrict__ dX) {
+    const int h = n / 2;
+    const int64_t total = (int64_t)B * h * h * h * C;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = q / C;
+        const int c = (int)(q - v * C);
+        const int x = (int)(v % h), y = (int)((v / h) % h), z = (int)((v / ((int64_t)h * h)) % h);
+        const int b = (int)(v / ((int64_t)h * h * h));
+        float s = 0.f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d)
+            s += dU[vox(b, 2 * z + (d >> 2), 2 * y + ((d >> 1) & 1), 2 * x + (d & 1), n) * ldU + c_off + c];
+        dX[q] = s;
+    }
+}
+
+cudaError_t avgpool(const __nv_bfloat16* X, int B, int n, int C, __nv_bfloat16* P, cudaStream_t st) {
+    const int64_t total = (int64_t)B * (n / 2) * (n / 2) * (n / 2) * C;
+    avgpool_kernel<<<blocks_for(total, 256), 256, 0, st>>>(X, B, n, C, P);
+    return cudaGetLastError();
+}
+cudaError_t avgpool_bwd(const float* dP, int B, int n, int C, float* dX, int accumulate, cudaStream_t st) {
+    const int64_t total = (int64_t)B * n * n * n * C;
+    avgpool_bwd_kernel<<<blocks_for(total, 256), 256, 0, st>>>(dP, B, n, C, dX, accumulate);
+    return cudaGetLastError();
+}
+cudaError_t upsample(const __nv_bfloat16* X, int B, int n, int C, __nv_bfloat16* U, int64_t ldU,
+                     int c_off, cudaStream_t st) {
+    const int64_t total = (int64_t)B * n * n * n * C;
+    upsample_kernel<<<blocks_for(total, 256), 256, 0, st>>>(X, B, n, C, U, ldU, c_off);
+    return cudaGetLastError();
+}
+cudaError_t upsample_bwd(const float* dU, int64_t ldU, int c_off, int B, int n, int C, float* dX,
+                         cudaStream_t st) {
+    const int64_t total = (int64_t)B * (n / 2) * (n / 2) * (n / 2) * C;
+    upsample_bwd_kernel<<<blocks_for(total, 256), 256, 0, st>>>(dU, ldU, c_off, B, n, C, dX);
+    return cudaGetLastError();
+}
+
+// ---- channel slices (concatenation) -------------------------------------------------------
+__global__ void copy_channels_kernel(const __nv_bfloat16* __restrict__ S, int64_t M, int C,
+                                     __nv_bfloat16* __restrict__ D, int64_t ldD, int c_off) {
+    const int64_t total = M * C;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = q / C;
+        D[m * ldD + c_off + (q - m * C)] = S[q];
+    }
+}
+// dS[m][c] (+)= dD[m][c_off + c]
+__global__ void slice_grad_kernel(const float* __restrict__ dD, int64_t ldD, int c_off, int64_t M,
+                                  int C, float* __restrict__ dS, int accumulate) {
+    const int64_t total = M * C;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = q / C;
+        const float g = dD[m * ldD + c_off + (q - m * C)];
+        dS[q] = accumulate ? dS[q] + g : g;
+    }
+}
+cudaError_t copy_channels(const __nv_bfloat16* S, int64_t M, int C, __nv_bfloat16* D, int64_t ldD,
+                          int c_off, cudaStream_t st) {
+    copy_channels_kernel<<<blocks_for(M * C, 256), 256, 0, st>>>(S, M, C, D, ldD, c_off);
+    return cudaGetLastError();
+}
+cudaError_t slice_grad(const float* dD, int64_t ldD, int c_off, int64_t M, int C, float* dS,
+                       int accumulate, cudaStream_t st) {
+    slice_grad_kernel<<<blocks_for(M * C, 256), 256, 0, st>>>(dD, ldD, c_off, M, C, dS, accumulate);
+    return cudaGetLastError();
+}
+
+// ---- the 1x1 output head (C -> 4, linear) ---------------------------------------------------
+__global__ void head_kernel(const __nv_bfloat16* __restrict__ A, int64_t M, int C,
+                            const float* __restrict__ W, const float* __restrict__ b,
+                            float* __restrict__ out) {
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        float o[4] = {b[0], b[1], b[2], b[3]};
+        for (int c = 0; c < C; ++c) {
+            const float a = __bfloat162float(A[m * C + c]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o[j] += W[j * C + c] * a;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[m * 4 + j] = o[j];
+    }
+}
+
+// dA[m][c] = sum_j dOut[m][j] W[j][c]; dW[j][c] += sum_m dOut[m][j] A[m][c]; db[j] += sum_m dOut
+// (block partial sums in shared memory, one atomic per entry and block).  C <= 64.
+__global__ void head_bwd_kernel(const float* __restrict__ dOut, const __nv_bfloat16* __restrict__ A,
+                                int64_t M, int C, const float* __restrict__ W, float* __restrict__ dA,
+                                float* __restrict__ dW, float* __restrict__ db) {
+    __shared__ float sW[4 * 64], sb[4];
+    for (int i = threadIdx.x; i < 4 * C; i += blockDim.x) sW[i] = 0.f;
+    if (threadIdx.x < 4) sb[threadIdx.x] = 0.f;
+    __syncthreads();
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const float g[4] = {dOut[m * 4], dOut[m * 4 + 1], dOut[m * 4 + 2], dOut[m * 4 + 3]};
+        for (int c = 0; c < C; ++c) {
+            const float a = __bfloat162float(A[m * C + c]);
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                s += g[j] * W[j * C + c];
+                atomicAdd(&sW[j * C + c], g[j] * a);
+            }
+            dA[m * C + c] = s;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) atomicAdd(&sb[j], g[j]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * C; i += blockDim.x) atomicAdd(dW + i, sW[i]);
+    if (threadIdx.x < 4) atomicAdd(db + threadIdx.x, sb[threadIdx.x]);
+}
+
+cudaError_t head_fwd(const __nv_bfloat16* A, int64_t M, int C, const float* W, const float* b,
+                     float* out, cudaStream_t st) {
+    head_kernel<<<blocks_for(M, 256), 256, 0, st>>>(A, M, C, W, b, out);
+    return cudaGetLastError();
+}
+cudaError_t head_bwd(const float* dOut, const __nv_bfloat16* A, int64_t M, int C, const float* W,
+                     float* dA, float* dW, float* db, cudaStream_t st) {
+    if (C > 64) return cudaErrorInvalidValue;
+    unsigned blocks = blocks_for(M, 256);
+    if (blocks > 2048) blocks = 2048;
+    head_bwd_kernel<<<blocks, 256, 0, st>>>(dOut, A, M, C, W, dA, dW, db);
+    return cudaGetLastError();
+}
+
+// ---- loss: mean squared error over all outputs ------------------------------------------------
+// dOut = 2 (out - target) / count; *loss += sum (out - target)^2 / count (FP64 atomics).
+__global__ void mse_kernel(const float* __restrict__ out, const float* __restrict__ target,
+                           int64_t count, float* __restrict__ dOut, double* __restrict__ loss) {
+    __shared__ double red[8];
+    double s = 0.0;
+    const double inv = 1.0 / (double)count;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const float d = out[q] - target[q];
+        dOut[q] = (float)(2.0 * inv) * d;
+        s += (double)d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) atomicAdd(loss, v * inv);
+    }
+}
+
+cudaError_t mse(const float* out, const float* target, int64_t count, float* dOut, double* loss,
+                cudaStream_t st) {
+    unsigned blocks = blocks_for(count, 256);
+    if (blocks > 2048) blocks = 2048;
+    mse_kernel<<<blocks, 256, 0, st>>>(out, target, count, dOut, loss);
+    return cudaGetLastError();
+}
+
+// ---- Adam (Kingma & Ba 2015) on FP32 master values ------------------------------------------
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+cudaError_t adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                 float eps, int step, cudaStream_t st) {
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    adam_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+// ---- weights -----------------------------------------------------------------------------------
+// W [cout][K27] FP32 -> Wb [cout][Kp] BF16 (zero K padding) and WbT [Kp][cout] BF16.
+__global__ void pack_weights_kernel(const float* __restrict__ W, int cout, int K27, int Kp,
+                                    __nv_bfloat16* __restrict__ Wb, __nv_bfloat16* __restrict__ WbT) {
+    const int64_t total = (int64_t)cout * Kp;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int co = (int)(q / Kp), k = (int)(q % Kp);
+        const __nv_bfloat16 w = __float2bfloat16_rn(k < K27 ? W[(int64_t)co * K27 + k] : 0.f);
+        Wb[q] = w;
+        WbT[(int64_t)k * cout + co] = w;
+    }
+}
+cudaError_t pack_weights(const float* W, int cout, int K27, int Kp, __nv_bfloat16* Wb,
+                         __nv_bfloat16* WbT, cudaStream_t st) {
+    pack_weights_kernel<<<blocks_for((int64_t)cout * Kp, 256), 256, 0, st>>>(W, cout, K27, Kp, Wb, WbT);
+    return cudaGetLastError();
+}
+
+// dWT [Kp][cout] -> gW [cout][K27]
+__global__ void unpack_grad_kernel(const float* __restrict__ dWT, int cout, int K27,
+                                   float* __restrict__ gW) {
+    const int64_t total = (int64_t)cout * K27;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int co = (int)(q / K27), k = (int)(q % K27);
+        gW[q] = dWT[(int64_t)k * cout + co];
+    }
+}
+cudaError_t unpack_grad(const float* dWT, int cout, int K27, float* gW, cudaStream_t st) {
+    unpack_grad_kernel<<<blocks_for((int64_t)cout * K27, 256), 256, 0, st>>>(dWT, cout, K27, gW);
+    return cudaGetLastError();
+}
+
+// ---- input features ----------------------------------------------------------------------------
+// channel 0: distance to the nearest wall / n (half-way walls: node i is i + 1/2 from the
+// low wall); 1: heated-face mask (+1 on the hot layer x = n-1, -1 on the cold layer x = 0);
+// 2, 3: the sample's normalised log10 Ra and log10 Pr.
+__global__ void features_kernel(int B, int n, const float* __restrict__ scalars,
+                                __nv_bfloat16* __restrict__ X) {
+    const int64_t total = (int64_t)B * n * n * n;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)((v / ((int64_t)n * n)) % n);
+        const int b = (int)(v / ((int64_t)n * n * n));
+        float d = fminf(x + 0.5f, n - 0.5f - x);
+        d = fminf(d, fminf(y + 0.5f, n - 0.5f - y));
+        d = fminf(d, fminf(z + 0.5f, n - 0.5f - z));
+        const float mask = x == n - 1 ? 1.f : (x == 0 ? -1.f : 0.f);
+        X[v * 4 + 0] = __float2bfloat16_rn(d / n);
+        X[v * 4 + 1] = __float2bfloat16_rn(n == 1 ? 0.f : mask);
+        X[v * 4 + 2] = __float2bfloat16_rn(scalars[2 * b]);
+        X[v * 4 + 3] = __float2bfloat16_rn(scalars[2 * b + 1]);
+    }
+}
+cudaError_t features(int B, int n, const float* scalars, __nv_bfloat16* X, cudaStream_t st) {
+    features_kernel<<<blocks_for((int64_t)B * n * n * n, 256), 256, 0, st>>>(B, n, scalars, X);
+    return cudaGetLastError();
+}
+
+}  // namespace nn
+}  // namespace lbm

@@ -21,3 +21,44 @@ cudaError_t gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16
 
 }  // namespace nn
 }  // namespace lbm
+
+namespace lbm {
+namespace nn {
+
+// layers.cu (channels-last activations, see there)
+cudaError_t im2col(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_bfloat16* Xcol,
+                   cudaStream_t st);
+cudaError_t col2im(const __nv_bfloat16* dXcol, int B, int n, int cin, int Kp, float* dX,
+                   int accumulate, cudaStream_t st);
+cudaError_t transpose(const __nv_bfloat16* in, int64_t R, int64_t C, int64_t ld_in,
+                      __nv_bfloat16* out, int64_t ld_out, cudaStream_t st);
+cudaError_t bias_relu(const float* Y, const float* bias, int64_t M, int C, __nv_bfloat16* A,
+                      int64_t ldA, int c_off, cudaStream_t st);
+cudaError_t relu_bwd(const float* dA, const __nv_bfloat16* A, int64_t ldA, int a_off, int64_t M,
+                     int C, __nv_bfloat16* dZ, float* db, cudaStream_t st);
+cudaError_t avgpool(const __nv_bfloat16* X, int B, int n, int C, __nv_bfloat16* P, cudaStream_t st);
+cudaError_t avgpool_bwd(const float* dP, int B, int n, int C, float* dX, int accumulate,
+                        cudaStream_t st);
+cudaError_t upsample(const __nv_bfloat16* X, int B, int n, int C, __nv_bfloat16* U, int64_t ldU,
+                     int c_off, cudaStream_t st);
+cudaError_t upsample_bwd(const float* dU, int64_t ldU, int c_off, int B, int n, int C, float* dX,
+                         cudaStream_t st);
+cudaError_t copy_channels(const __nv_bfloat16* S, int64_t M, int C, __nv_bfloat16* D, int64_t ldD,
+                          int c_off, cudaStream_t st);
+cudaError_t slice_grad(const float* dD, int64_t ldD, int c_off, int64_t M, int C, float* dS,
+                       int accumulate, cudaStream_t st);
+cudaError_t head_fwd(const __nv_bfloat16* A, int64_t M, int C, const float* W, const float* b,
+                     float* out, cudaStream_t st);
+cudaError_t head_bwd(const float* dOut, const __nv_bfloat16* A, int64_t M, int C, const float* W,
+                     float* dA, float* dW, float* db, cudaStream_t st);
+cudaError_t mse(const float* out, const float* target, int64_t count, float* dOut, double* loss,
+                cudaStream_t st);
+cudaError_t adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
+                 float b2, float eps, int step, cudaStream_t st);
+cudaError_t pack_weights(const float* W, int cout, int K27, int Kp, __nv_bfloat16* Wb,
+                         __nv_bfloat16* WbT, cudaStream_t st);
+cudaError_t unpack_grad(const float* dWT, int cout, int K27, float* gW, cudaStream_t st);
+cudaError_t features(int B, int n, const float* scalars, __nv_bfloat16* X, cudaStream_t st);
+
+}  // namespace nn
+}  // namespace lbm

@@ -24,7 +24,7 @@ EXPORTS = (
     "lbm_default_options", "lbm_derive_params", "lbm_arena_bytes", "lbm_create",
     "lbm_create_params", "lbm_step", "lbm_fields", "lbm_nusselt", "lbm_residual",
     "lbm_get_populations", "lbm_set_populations", "lbm_get_params", "lbm_steps_done",
-    "lbm_last_error", "lbm_synchronize", "lbm_destroy", "lbm_nusselt_noalloc",
+    "lbm_last_error", "lbm_synchronize", "lbm_destroy", "lbm_nusselt_noalloc", "lbm_set_fields",
 )
 
 
@@ -109,6 +109,7 @@ def load(build_if_missing=True):
     L.lbm_get_populations.argtypes = [ctypes.c_void_p, _D, _D]
     L.lbm_set_populations.argtypes = [ctypes.c_void_p, _D, _D]
     L.lbm_get_params.argtypes = [ctypes.c_void_p, P(Params)]
+    L.lbm_set_fields.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 5
     L.lbm_steps_done.argtypes = [ctypes.c_void_p]
     L.lbm_steps_done.restype = ctypes.c_int64
     L.lbm_last_error.argtypes = [ctypes.c_void_p]
@@ -274,6 +275,18 @@ class LBM:
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(15, nz, ny, nx)
         g = np.ascontiguousarray(g, dtype=np.float64).reshape(self.lattice, nz, ny, nx)
         self._check(self._L.lbm_set_populations(self._ctx, _dp(f), _dp(g)))
+
+    def set_fields(self, ux, uy, uz, T, rho=None):
+        """Populations at the equilibria of the fields: torch CUDA float64 tensors of
+        shape (nz, ny, nx) on this context's device (rho None: 1)."""
+        import torch
+        arrs = [rho, ux, uy, uz, T]
+        for a in arrs:
+            if a is not None and (a.dtype != torch.float64 or not a.is_cuda or not a.is_contiguous()
+                                  or a.numel() != self.ncell):
+                raise ValueError("fields must be contiguous CUDA float64 tensors of ncell values")
+        ptr = [ctypes.c_void_p(a.data_ptr()) if a is not None else None for a in arrs]
+        self._check(self._L.lbm_set_fields(self._ctx, *ptr))
 
     def params(self):
         return self.params_struct().as_dict()

@@ -9,8 +9,18 @@ GEMM_F32, GEMM_BF16, GEMM_F32_ADD = 0, 1, 2
 
 # Every entry point include/lbm_net.h declares (checked by tests/test_abi.py).
 EXPORTS = (
-    "lbm_nn_gemm_bf16",
+    "lbm_nn_gemm_bf16", "lbm_net_default_config", "lbm_net_create", "lbm_net_destroy",
+    "lbm_net_param_count", "lbm_net_encode", "lbm_net_get_params", "lbm_net_set_params",
+    "lbm_net_forward", "lbm_net_gradients", "lbm_net_train_step", "lbm_net_last_error",
+    "lbm_net_targets", "lbm_net_warm_start",
 )
+
+
+class NetConfig(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("max_batch", ctypes.c_int), ("c1", ctypes.c_int),
+                ("c2", ctypes.c_int), ("c3", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("cuda_stream", ctypes.c_void_p)]
 
 _bound = False
 
@@ -21,7 +31,26 @@ def _lib():
     if _bound:
         return L
     vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    P = ctypes.POINTER
     L.lbm_nn_gemm_bf16.argtypes = [vp, i64, vp, i64, vp, i64, i32, i32, i32, i32, i32, vp]
+    L.lbm_net_default_config.argtypes = [P(NetConfig)]
+    L.lbm_net_default_config.restype = None
+    L.lbm_net_create.argtypes = [P(NetConfig), P(vp)]
+    L.lbm_net_destroy.argtypes = [vp]
+    L.lbm_net_destroy.restype = None
+    L.lbm_net_param_count.argtypes = [vp]
+    L.lbm_net_param_count.restype = i64
+    L.lbm_net_encode.argtypes = [ctypes.c_double, ctypes.c_double, P(ctypes.c_float)]
+    L.lbm_net_encode.restype = None
+    L.lbm_net_get_params.argtypes = [vp, vp, i64, i32]
+    L.lbm_net_set_params.argtypes = [vp, vp, i64]
+    L.lbm_net_forward.argtypes = [vp, i32, vp, vp]
+    L.lbm_net_gradients.argtypes = [vp, i32, vp, vp, P(ctypes.c_double)]
+    L.lbm_net_train_step.argtypes = [vp, i32, vp, vp, P(ctypes.c_double)]
+    L.lbm_net_last_error.argtypes = [vp]
+    L.lbm_net_last_error.restype = ctypes.c_char_p
+    L.lbm_net_targets.argtypes = [vp, vp]
+    L.lbm_net_warm_start.argtypes = [vp, vp, i32]
     _bound = True
     return L
 
@@ -44,3 +73,112 @@ def gemm_bf16(A, B, C, out_mode=GEMM_F32, splits=1, K=None):
     _check(_lib().lbm_nn_gemm_bf16(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
                                    C.data_ptr(), C.stride(0), M, N, K, out_mode, splits,
                                    _stream(C)))
+
+
+def encode(Ra, Pr):
+    """The network's two scalar inputs for (Ra, Pr) (lbm_net_encode)."""
+    out = (ctypes.c_float * 2)()
+    _lib().lbm_net_encode(float(Ra), float(Pr), out)
+    return [out[0], out[1]]
+
+
+def _scalars(samples):
+    import numpy as np
+    arr = np.ascontiguousarray(np.asarray(samples, dtype=np.float32).reshape(-1, 2))
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def targets(sim):
+    """Training targets of an LBM context's state: CUDA float32 [ncell][4] with
+    (u_x, u_y, u_z) / U0 and 2 T."""
+    import torch
+    out = torch.empty((sim.ncell, 4), dtype=torch.float32, device=sim.device)
+    sim._check(_lib().lbm_net_targets(sim._ctx, out.data_ptr()))
+    return out
+
+
+def warm_start(sim, pred, m):
+    """Start an LBM context from a prediction pred (CUDA float32 [m^3][4])."""
+    import torch
+    pred = pred.to(torch.float32).contiguous()
+    if pred.numel() != 4 * m ** 3:
+        raise ValueError("pred must hold m^3 x 4 values")
+    sim._check(_lib().lbm_net_warm_start(sim._ctx, pred.data_ptr(), int(m)))
+
+
+class Net:
+    """The warm-start network on the current CUDA device (include/lbm_net.h)."""
+
+    def __init__(self, n=64, max_batch=2, channels=(32, 64, 128), seed=1, lr=1e-3,
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise LBMError(-3, "no CUDA device: the network has no CPU path")
+        L = _lib()
+        self._L = L
+        c = NetConfig()
+        L.lbm_net_default_config(ctypes.byref(c))
+        c.n, c.max_batch = int(n), int(max_batch)
+        c.c1, c.c2, c.c3 = (int(v) for v in channels)
+        c.seed, c.lr = int(seed) & (2 ** 64 - 1), float(lr)
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        c.cuda_stream = self._stream.cuda_stream
+        self.n, self.max_batch, self.channels = c.n, c.max_batch, (c.c1, c.c2, c.c3)
+        self._net = ctypes.c_void_p()
+        rc = L.lbm_net_create(ctypes.byref(c), ctypes.byref(self._net))
+        if rc != LBM_OK:
+            raise LBMError(rc, L.lbm_last_error(None).decode())
+
+    def _check(self, rc):
+        if rc != LBM_OK:
+            raise LBMError(rc, self._L.lbm_net_last_error(self._net).decode())
+
+    @property
+    def param_count(self):
+        return int(self._L.lbm_net_param_count(self._net))
+
+    def get_params(self, grads=False):
+        import numpy as np
+        out = np.empty(self.param_count, dtype=np.float32)
+        self._check(self._L.lbm_net_get_params(self._net, out.ctypes.data, out.size, int(grads)))
+        return out
+
+    def set_params(self, flat):
+        import numpy as np
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(self._L.lbm_net_set_params(self._net, flat.ctypes.data, flat.size))
+
+    def forward(self, scalars):
+        """Predictions [B][n^3][4] (CUDA float32) for encoded scalars [B][2]."""
+        import torch
+        arr, ptr = _scalars(scalars)
+        out = torch.empty((arr.shape[0], self.n ** 3, 4), dtype=torch.float32, device="cuda")
+        self._check(self._L.lbm_net_forward(self._net, arr.shape[0], ptr, out.data_ptr()))
+        return out
+
+    def gradients(self, scalars, targets):
+        arr, ptr = _scalars(scalars)
+        loss = ctypes.c_double()
+        t = targets.contiguous()
+        self._check(self._L.lbm_net_gradients(self._net, arr.shape[0], ptr, t.data_ptr(),
+                                              ctypes.byref(loss)))
+        return loss.value
+
+    def train_step(self, scalars, targets):
+        arr, ptr = _scalars(scalars)
+        loss = ctypes.c_double()
+        t = targets.contiguous()
+        self._check(self._L.lbm_net_train_step(self._net, arr.shape[0], ptr, t.data_ptr(),
+                                               ctypes.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "_net", None) is not None and self._net.value:
+            self._L.lbm_net_destroy(self._net)
+            self._net = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

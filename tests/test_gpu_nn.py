@@ -86,3 +86,175 @@ def test_gemm_rejects_bad_arguments():
     with pytest.raises(LBMError):  # row stride not a multiple of 8
         At = torch.zeros((128, 70), dtype=torch.bfloat16, device="cuda")
         net.gemm_bf16(At, B.cuda(), C, net.GEMM_F32, K=64)
+
+
+# ------------------------------------------------------------------------------------
+# The network against the FP64 oracle (oracle/nn_oracle.py) on a small grid
+#
+# Forward: the oracle run with the CUDA path's BF16 roundings (inputs, weights, every
+# stored activation) differs from the kernels only by accumulation order, so the
+# relative L2 error of the output is bounded by 1e-2 (a few BF16 ulps propagated);
+# without the roundings (pure FP64) by 5e-2.  Gradients: relative L2 error per layer
+# 5e-2 against the rounded oracle (the kernels also round the backward GEMM operands).
+# ------------------------------------------------------------------------------------
+
+SMALL = dict(n=8, channels=(8, 16, 16))
+
+
+def _small_net(seed=3, batch=2):
+    from paper_1710_04751_gb300 import net
+    return net.Net(n=SMALL["n"], max_batch=batch, channels=SMALL["channels"], seed=seed, lr=1e-3)
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def test_forward_against_oracle():
+    from oracle import nn_oracle as nno
+    netw = _small_net()
+    c1, c2, c3 = SMALL["channels"]
+    n = SMALL["n"]
+    flat = netw.get_params().astype(np.float64)
+    # non-zero biases so that they are exercised
+    flat_b = flat.copy()
+    rng = np.random.default_rng(5)
+    layers, head = nno.unflatten(flat, c1, c2, c3)
+    layers = [(w, 0.05 * torch_mod().as_tensor(rng.standard_normal(b.shape[0]))) for w, b in layers]
+    flat_b = nno.flatten(layers, (head[0], 0.1 * torch_mod().ones(4, dtype=torch_mod().float64)))
+    netw.set_params(flat_b)
+    flat_b = netw.get_params().astype(np.float64)  # the FP32 values the GPU holds
+    scal = np.array([[0.3, -0.5], [-0.8, 0.6]])
+    got = netw.forward(scal).cpu().double().numpy()
+    layers, head = nno.unflatten(flat_b, c1, c2, c3)
+    ref_q = nno.forward(layers, head, scal, n, bf16=True).numpy()
+    ref = nno.forward(layers, head, scal, n, bf16=False).numpy()
+    assert got.shape == (2, n ** 3, 4)
+    assert _rel(got, ref_q) <= 1e-2
+    assert _rel(got, ref) <= 5e-2
+    netw.close()
+
+
+def test_gradients_against_oracle():
+    torch = torch_mod()
+    from oracle import nn_oracle as nno
+    netw = _small_net(seed=4)
+    c1, c2, c3 = SMALL["channels"]
+    n = SMALL["n"]
+    rng = np.random.default_rng(6)
+    scal = np.array([[0.1, 0.4], [0.7, -0.3]])
+    tgt = 0.5 * rng.standard_normal((2, n ** 3, 4))
+    loss = netw.gradients(scal, torch.as_tensor(tgt, dtype=torch.float32).cuda())
+    g = netw.get_params(grads=True).astype(np.float64)
+    flat = netw.get_params().astype(np.float64)
+    tgt32 = tgt.astype(np.float32).astype(np.float64)
+    ref_loss, ref_g, _ = nno.loss_and_grads(flat, scal, tgt32, n, c1, c2, c3, bf16=True)
+    assert loss == pytest.approx(ref_loss, rel=1e-2)
+    off = 0
+    for ci, co, _ in nno.layer_shapes(c1, c2, c3):
+        for size in (co * 27 * ci, co):
+            assert _rel(g[off:off + size], ref_g[off:off + size]) <= 5e-2, (ci, co, size)
+            off += size
+    assert _rel(g[off:], ref_g[off:]) <= 5e-2  # head
+    netw.close()
+
+
+def test_train_step_is_one_adam_update():
+    torch = torch_mod()
+    from oracle import nn_oracle as nno
+    netw = _small_net(seed=5)
+    n = SMALL["n"]
+    scal = np.array([[0.2, 0.2], [-0.5, 0.9]])
+    tgt = torch.as_tensor(np.random.default_rng(7).standard_normal((2, n ** 3, 4)),
+                          dtype=torch.float32).cuda()
+    p0 = netw.get_params().astype(np.float64)
+    netw.gradients(scal, tgt)
+    g = netw.get_params(grads=True).astype(np.float64)
+    netw.train_step(scal, tgt)  # same batch, same parameters: the same gradient
+    p1 = netw.get_params().astype(np.float64)
+    want, _, _ = nno.adam(p0, g, np.zeros_like(p0), np.zeros_like(p0), 1, lr=1e-3)
+    # FP32 arithmetic; entries whose gradient is tiny may differ in sign of a rounding
+    big = np.abs(g) > 1e-6
+    assert np.abs(p1 - want)[big].max() <= 1e-6
+    netw.close()
+
+
+def test_loss_falls_when_fitting_one_sample():
+    torch = torch_mod()
+    netw = _small_net(seed=6, batch=1)
+    n = SMALL["n"]
+    c = (np.arange(n) + 0.5) / n
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    tgt = np.stack([np.sin(np.pi * x) * z, 0 * x, -np.sin(np.pi * z) * x, x - 0.5], -1)
+    t = torch.as_tensor(tgt.reshape(1, -1, 4), dtype=torch.float32).cuda()
+    losses = [netw.train_step([[0.1, 0.1]], t) for _ in range(300)]
+    assert losses[-1] < 0.1 * losses[0]
+    netw.close()
+
+
+# ------------------------------------------------------------------------------------
+# The bridge to the solver
+# ------------------------------------------------------------------------------------
+
+def _ctx(grid, seed=1, precision=None):
+    import paper_1710_04751_gb300 as lbm
+    return lbm.LBM(grid, 15, Ra=1e4, Pr=0.71, precision=lbm.FP64 if precision is None else precision,
+                   seed=seed)
+
+
+def test_set_fields_against_oracle_equilibria():
+    torch = torch_mod()
+    from oracle import formb
+    import oracle
+    sim = _ctx((5, 4, 3))
+    rng = np.random.default_rng(8)
+    shape = (3, 4, 5)
+    rho = 1 + 0.05 * rng.standard_normal(shape)
+    u = 0.05 * rng.standard_normal((3,) + shape)
+    T = rng.uniform(-0.5, 0.5, shape)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    sim.set_fields(dev(u[0]), dev(u[1]), dev(u[2]), dev(T), rho=dev(rho))
+    f, g = sim.get_populations()
+    cs2 = sim.params()["cs2_phi"]
+    for k, j, i in [(0, 0, 0), (2, 3, 4), (1, 2, 1), (2, 0, 3)]:
+        uu = u[:, k, j, i]
+        assert np.abs(f[:, k, j, i] - formb.flow_equilibrium(rho[k, j, i], uu)).max() <= 1e-13
+        assert np.abs(g[:, k, j, i] - formb.thermal_equilibrium(T[k, j, i], uu, 15, cs2)).max() <= 1e-13
+    sim.close()
+
+
+def test_targets_against_oracle_fields():
+    import oracle
+    sim = _ctx((8, 8, 8), seed=2)
+    sim.step(40)
+    from paper_1710_04751_gb300 import net
+    got = net.targets(sim).cpu().double().numpy()
+    F, G = sim.get_populations()
+    p = oracle.Problem.cavity(8, 1e4)
+    fl = p.fields(F, G)
+    U0 = sim.params()["U0"]
+    want = np.stack([fl["ux"] / U0, fl["uy"] / U0, fl["uz"] / U0, 2 * fl["T"]], -1).reshape(-1, 4)
+    assert np.abs(got - want).max() <= 1e-6 * max(1.0, np.abs(want).max())
+    sim.close()
+
+
+@pytest.mark.parametrize("m,grid", [(8, (8, 8, 8)), (4, (8, 6, 5))])
+def test_warm_start_sets_the_equilibria_of_the_resampled_prediction(m, grid):
+    torch = torch_mod()
+    from oracle import formb, nn_oracle as nno
+    from paper_1710_04751_gb300 import net
+    sim = _ctx(grid)
+    rng = np.random.default_rng(9)
+    pred = rng.uniform(-1, 1, (m ** 3, 4)).astype(np.float32)
+    net.warm_start(sim, torch.as_tensor(pred).cuda(), m)
+    f, g = sim.get_populations()
+    U0, cs2 = sim.params()["U0"], sim.params()["cs2_phi"]
+    nx, ny, nz = grid
+    fields = nno.trilinear(pred.astype(np.float64), m, nx, ny, nz)
+    for (k, j, i) in [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (nz // 2, 1, nx // 2)]:
+        uu = fields[k, j, i, :3] * U0
+        T = 0.5 * fields[k, j, i, 3]
+        assert np.abs(f[:, k, j, i] - formb.flow_equilibrium(1.0, uu)).max() <= 1e-12
+        assert np.abs(g[:, k, j, i] - formb.thermal_equilibrium(T, uu, 15, cs2)).max() <= 1e-12
+    sim.close()
