@@ -171,6 +171,17 @@ int lbm_set_populations(lbm_ctx* ctx, const double* f, const double* g);
 int lbm_set_fields(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
                    const double* uz, const double* T);
 
+/* lbm_set_fields followed by `iterations` rounds of one time step and a re-imposition
+ * of the given u and T that keeps each node's departure from equilibrium (its stresses
+ * and heat fluxes) and its rho: p <- p - p_eq(current u, T) + p_eq(given u, T).  The
+ * non-equilibrium parts thereby adapt to the given fields -- the iterative consistent
+ * initialisation of Mei, Luo, Lallemand & d'Humieres (Computers & Fluids 35, 2006),
+ * applied to u and T.  An odd count is rounded up to the next even one (the state then
+ * stays in its buffer, which batch members need).  The rounds are not counted by
+ * lbm_steps_done.  iterations = 0 is lbm_set_fields. */
+int lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                    const double* uz, const double* T, int iterations);
+
 /* Parameters in use, step counter, last error message, stream wait, destruction. */
 int lbm_get_params(const lbm_ctx* ctx, lbm_params* out);
 int64_t lbm_steps_done(const lbm_ctx* ctx);

@@ -80,6 +80,8 @@ int lbm_net_forward(lbm_net* net, int batch, const float* scalars, float* out);
  * error against targets (DEVICE, [batch][n^3][4]); gradients via lbm_net_get_params. */
 int lbm_net_gradients(lbm_net* net, int batch, const float* scalars, const float* targets,
                       double* loss);
+/* The Adam learning rate of the following updates (> 0). */
+int lbm_net_set_lr(lbm_net* net, float lr);
 /* lbm_net_gradients followed by one Adam update of every parameter. */
 int lbm_net_train_step(lbm_net* net, int batch, const float* scalars, const float* targets,
                        double* loss);
@@ -93,8 +95,9 @@ int lbm_net_targets(lbm_ctx* ctx, float* out);
 /* Start a context from a prediction: pred = DEVICE array [m^3][4] on a cell-centred m^3
  * grid covering the cavity, resampled trilinearly onto the context's grid (identity
  * when m equals it), scaled back (u = p U0, T = p / 2), and set as equilibria with
- * rho = 1 (lbm_set_fields). */
-int lbm_net_warm_start(lbm_ctx* ctx, const float* pred, int m);
+ * rho = 1 followed by `iterations` rounds of the consistent initialisation
+ * (lbm_init_fields). */
+int lbm_net_warm_start(lbm_ctx* ctx, const float* pred, int m, int iterations);
 
 #ifdef __cplusplus
 }

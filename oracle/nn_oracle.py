@@ -171,3 +171,38 @@ def trilinear(pred, m, nx, ny, nz):
                                 acc += wt * P[lo[2] + dz, lo[1] + dy, lo[0] + dx]
                 out[k, j, i] = acc
     return out
+
+
+def consistent_init(problem, fields, iterations, rho=None):
+    """The consistent initialisation the solver header specifies, in the oracle: the
+    populations of the equilibria of `fields` (ux, uy, uz, T arrays [nz][ny][nx]), then
+    `iterations` (rounded up to even) rounds of one oracle step and
+    p <- p - p_eq(current u, T) + p_eq(given u, T) at every node, rho kept.  Equilibria
+    from oracle/formb.py; u and T of a stored state as the oracle's fields() defines them."""
+    from oracle import formb
+    nx, ny, nz = problem.nx, problem.ny, problem.nz
+    q = problem.q_g
+    cs2 = problem.cs2_phi
+    ux, uy, uz, T = (np.asarray(fields[k], dtype=np.float64) for k in ("ux", "uy", "uz", "T"))
+    F = np.empty((15, nz, ny, nx))
+    G = np.empty((q, nz, ny, nx))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                u = (ux[k, j, i], uy[k, j, i], uz[k, j, i])
+                r = 1.0 if rho is None else rho[k, j, i]
+                F[:, k, j, i] = formb.flow_equilibrium(r, u)
+                G[:, k, j, i] = formb.thermal_equilibrium(T[k, j, i], u, q, cs2)
+    for _ in range(iterations + (iterations & 1)):
+        F, G = problem.step(F, G)
+        cur = problem.fields(F, G)
+        for k in range(nz):
+            for j in range(ny):
+                for i in range(nx):
+                    r = cur["rho"][k, j, i]
+                    uc = (cur["ux"][k, j, i], cur["uy"][k, j, i], cur["uz"][k, j, i])
+                    ut = (ux[k, j, i], uy[k, j, i], uz[k, j, i])
+                    F[:, k, j, i] += formb.flow_equilibrium(r, ut) - formb.flow_equilibrium(r, uc)
+                    G[:, k, j, i] += (formb.thermal_equilibrium(T[k, j, i], ut, q, cs2)
+                                      - formb.thermal_equilibrium(cur["T"][k, j, i], uc, q, cs2))
+    return F, G

@@ -504,12 +504,24 @@ extern "C" int lbm_set_populations(lbm_ctx* c, const double* f, const double* g)
 
 extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* ux, const double* uy,
                               const double* uz, const double* T) {
-    if (!c || !ux || !uy || !uz || !T) return fail(c, LBM_EINVAL, "NULL argument%s");
+    return lbm_init_fields(c, rho, ux, uy, uz, T, 0);
+}
+
+extern "C" int lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, const double* uy,
+                               const double* uz, const double* T, int iterations) {
+    if (!c || !ux || !uy || !uz || !T || iterations < 0)
+        return fail(c, LBM_EINVAL, "NULL argument or negative iterations%s");
     DeviceGuard gd(c->device);
     int rc = with_storage(c->precision, [&](auto tag) {
         using S = decltype(tag);
         const ParamsOf<S> p = dev_params<typename Storage<S>::real>(c);
         CUDA_OR_FAIL(c, launch_set_fields<S>(c->dev, c->cur, p, rho, ux, uy, uz, T, c->stream));
+        const int rounds = iterations + (iterations & 1);  // even: the state stays in its buffer
+        for (int it = 0; it < rounds; ++it) {
+            CUDA_OR_FAIL(c, launch_step<S>(c->dev, c->cur, p, c->stream));
+            c->cur ^= 1;
+            CUDA_OR_FAIL(c, launch_reimpose<S>(c->dev, c->cur, p, ux, uy, uz, T, c->stream));
+        }
         CUDA_OR_FAIL(c, launch_residual<S>(c->dev, c->cur, p, 0, c->stream));
         return LBM_OK;
     });

@@ -88,6 +88,11 @@ cudaError_t launch_set_fields(const DevState& s, int cur, const ParamsOf<S>& p, 
                               const double* ux, const double* uy, const double* uz,
                               const double* T, cudaStream_t st);
 
+// p <- p - p_eq(current u, T) + p_eq(target u, T) on buffer `cur` (rho kept).
+template <typename S>
+cudaError_t launch_reimpose(const DevState& s, int cur, const ParamsOf<S>& p, const double* ux,
+                            const double* uy, const double* uz, const double* T, cudaStream_t st);
+
 // Message returned by lbm_last_error(NULL) on this thread.
 void set_last_error(const char* msg);
 

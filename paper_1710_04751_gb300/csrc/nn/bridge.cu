@@ -73,8 +73,9 @@ extern "C" int lbm_net_targets(lbm_ctx* c, float* out) {
     return wait_stream(c);
 }
 
-extern "C" int lbm_net_warm_start(lbm_ctx* c, const float* pred, int m) {
-    if (!c || !pred || m < 1) return fail(c, LBM_EINVAL, "NULL prediction or grid size < 1%s");
+extern "C" int lbm_net_warm_start(lbm_ctx* c, const float* pred, int m, int iterations) {
+    if (!c || !pred || m < 1 || iterations < 0)
+        return fail(c, LBM_EINVAL, "NULL prediction, grid size < 1 or negative iterations%s");
     if (!(c->params.U0 > 0)) return fail(c, LBM_EINVAL, "the context has no velocity scale U0%s");
     DeviceGuard g(c->device);
     const int64_t n = c->ncell;
@@ -85,8 +86,9 @@ extern "C" int lbm_net_warm_start(lbm_ctx* c, const float* pred, int m) {
     resample_kernel<<<blocks, 256, 0, c->stream>>>(pred, m, c->grid.nx, c->grid.ny, c->grid.nz,
                                                    c->params.U0, buf, buf + n, buf + 2 * n, buf + 3 * n);
     e = cudaGetLastError();
-    int rc = e == cudaSuccess ? lbm_set_fields(c, nullptr, buf, buf + n, buf + 2 * n, buf + 3 * n)
-                              : fail(c, LBM_ECUDA, "resampling failed: %s", cudaGetErrorString(e));
-    cudaFree(buf);  // lbm_set_fields waited for the stream
+    int rc = e == cudaSuccess
+                 ? lbm_init_fields(c, nullptr, buf, buf + n, buf + 2 * n, buf + 3 * n, iterations)
+                 : fail(c, LBM_ECUDA, "resampling failed: %s", cudaGetErrorString(e));
+    cudaFree(buf);  // lbm_init_fields waited for the stream
     return rc;
 }

@@ -38,6 +38,7 @@ struct GemmArgs {
     void* C;
     long long ldc;
     int* err;
+    int vec;       // C and its rows are 16-byte aligned: whole 16-column chunks use vector stores
 };
 
 template <int BN>
@@ -131,16 +132,33 @@ __global__ void __launch_bounds__(128, 1)
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
             if (row < args.M) {
                 const int col0 = n0 + c;
+                const bool full = args.vec && col0 + 16 <= args.N;  // 16-byte stores
                 if (args.out_mode == GEMM_BF16) {
                     __nv_bfloat16* C = static_cast<__nv_bfloat16*>(args.C) + row * args.ldc;
+                    if (full) {
+                        uint4 pk[2];
+                        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(pk);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (col0 + j < args.N) C[col0 + j] = __float2bfloat16_rn(v[j]);
+                        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        reinterpret_cast<uint4*>(C + col0)[0] = pk[0];
+                        reinterpret_cast<uint4*>(C + col0)[1] = pk[1];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (col0 + j < args.N) C[col0 + j] = __float2bfloat16_rn(v[j]);
+                    }
                 } else if (args.out_mode == GEMM_F32) {
                     float* C = static_cast<float*>(args.C) + row * args.ldc;
+                    if (full) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (col0 + j < args.N) C[col0 + j] = v[j];
+                        for (int j = 0; j < 4; ++j)
+                            reinterpret_cast<float4*>(C + col0)[j] =
+                                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (col0 + j < args.N) C[col0 + j] = v[j];
+                    }
                 } else {
                     float* C = static_cast<float*>(args.C) + row * args.ldc;
 #pragma unroll
@@ -224,7 +242,9 @@ cudaError_t gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16
     CUtensorMap ta, tb;
     if (!make_map(&ta, A, M, K, lda, BM) || !make_map(&tb, B, N, K, ldb, BN))
         return cudaErrorInvalidValue;
-    GemmArgs a{M, N, K, per, out_mode, C, ldc, err};
+    const long long esz = out_mode == GEMM_BF16 ? 2 : 4;
+    const int vec = ((uintptr_t)C % 16 == 0) && ((ldc * esz) % 16 == 0);
+    GemmArgs a{M, N, K, per, out_mode, C, ldc, err, vec};
     switch (BN) {
     case 32: return launch<32>(ta, tb, a, splits, st);
     case 64: return launch<64>(ta, tb, a, splits, st);

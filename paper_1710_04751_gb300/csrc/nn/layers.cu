@@ -76,36 +76,6 @@ cudaError_t im2col(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_b
     return cudaGetLastError();
 }
 
-// ---- col2im (adjoint of im2col) ------------------------------------------------------
-// dX[v][ci] (+)= sum over taps of dXcol[u][tap * cin + ci], u the voxel whose tap reads v.
-__global__ void col2im_kernel(const __nv_bfloat16* __restrict__ dXcol, int B, int n, int cin,
-                              int Kp, float* __restrict__ dX, int accumulate) {
-    const int64_t total = (int64_t)B * n * n * n * cin;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = q / cin;
-        const int ci = (int)(q - v * cin);
-        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)((v / ((int64_t)n * n)) % n);
-        const int b = (int)(v / ((int64_t)n * n * n));
-        float s = 0.f;
-#pragma unroll 1
-        for (int tap = 0; tap < 27; ++tap) {
-            const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
-            const int uz = z - kz + 1, uy = y - ky + 1, ux = x - kx + 1;
-            if ((unsigned)uz < (unsigned)n && (unsigned)uy < (unsigned)n && (unsigned)ux < (unsigned)n)
-                s += __bfloat162float(dXcol[vox(b, uz, uy, ux, n) * Kp + tap * cin + ci]);
-        }
-        dX[q] = accumulate ? dX[q] + s : s;
-    }
-}
-
-cudaError_t col2im(const __nv_bfloat16* dXcol, int B, int n, int cin, int Kp, float* dX,
-                   int accumulate, cudaStream_t st) {
-    const int64_t total = (int64_t)B * n * n * n * cin;
-    col2im_kernel<<<blocks_for(total, 256), 256, 0, st>>>(dXcol, B, n, cin, Kp, dX, accumulate);
-    return cudaGetLastError();
-}
-
 // ---- transpose of a BF16 matrix (32 x 32 tiles through shared memory) -----------------
 __global__ void transpose_kernel(const __nv_bfloat16* __restrict__ in, int64_t R, int64_t C,
                                  int64_t ld_in, __nv_bfloat16* __restrict__ out, int64_t ld_out) {
@@ -426,21 +396,36 @@ cudaError_t adam(float* p, const float* g, float* m, float* v, int64_t n, float 
 }
 
 // ---- weights -----------------------------------------------------------------------------------
-// W [cout][K27] FP32 -> Wb [cout][Kp] BF16 (zero K padding) and WbT [Kp][cout] BF16.
-__global__ void pack_weights_kernel(const float* __restrict__ W, int cout, int K27, int Kp,
-                                    __nv_bfloat16* __restrict__ Wb, __nv_bfloat16* __restrict__ WbT) {
-    const int64_t total = (int64_t)cout * Kp;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+// W [cout][27 cin] FP32 -> Wb [cout][Kp] BF16 (zero K padding), the forward operand, and
+// Wf [cin][Kpf] BF16 with Wf[ci][t * cout + co] = W[co][(26 - t) * cin + ci]: the weights of
+// the convolution that maps the output gradient to the input gradient (every tap
+// mirrored, input and output channels exchanged; zero padding to Kpf).
+__global__ void pack_weights_kernel(const float* __restrict__ W, int cin, int cout, int Kp,
+                                    int Kpf, __nv_bfloat16* __restrict__ Wb,
+                                    __nv_bfloat16* __restrict__ Wf) {
+    const int K27 = 27 * cin;
+    const int64_t n1 = (int64_t)cout * Kp, n2 = (int64_t)cin * Kpf;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n1 + n2;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const int co = (int)(q / Kp), k = (int)(q % Kp);
-        const __nv_bfloat16 w = __float2bfloat16_rn(k < K27 ? W[(int64_t)co * K27 + k] : 0.f);
-        Wb[q] = w;
-        WbT[(int64_t)k * cout + co] = w;
+        if (q < n1) {
+            const int co = (int)(q / Kp), k = (int)(q % Kp);
+            Wb[q] = __float2bfloat16_rn(k < K27 ? W[(int64_t)co * K27 + k] : 0.f);
+        } else if (Wf) {
+            const int64_t r = q - n1;
+            const int ci = (int)(r / Kpf), k = (int)(r % Kpf);
+            float w = 0.f;
+            if (k < 27 * cout) {
+                const int t = k / cout, co = k % cout;
+                w = W[(int64_t)co * K27 + (26 - t) * cin + ci];
+            }
+            Wf[r] = __float2bfloat16_rn(w);
+        }
     }
 }
-cudaError_t pack_weights(const float* W, int cout, int K27, int Kp, __nv_bfloat16* Wb,
-                         __nv_bfloat16* WbT, cudaStream_t st) {
-    pack_weights_kernel<<<blocks_for((int64_t)cout * Kp, 256), 256, 0, st>>>(W, cout, K27, Kp, Wb, WbT);
+cudaError_t pack_weights(const float* W, int cin, int cout, int Kp, int Kpf, __nv_bfloat16* Wb,
+                         __nv_bfloat16* Wf, cudaStream_t st) {
+    const int64_t total = (int64_t)cout * Kp + (int64_t)cin * Kpf;
+    pack_weights_kernel<<<blocks_for(total, 256), 256, 0, st>>>(W, cin, cout, Kp, Kpf, Wb, Wf);
     return cudaGetLastError();
 }
 

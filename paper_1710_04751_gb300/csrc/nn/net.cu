@@ -10,9 +10,10 @@
 //
 // every conv 3x3x3 with zero padding, bias and ReLU; pool = 2x average, up = 2x nearest.
 // Inputs: 4 channels (wall distance, heated-face mask, normalised log10 Ra and log10 Pr);
-// outputs: (u_x, u_y, u_z) / U0 and 2 T.  Each convolution is im2col + a tensor-core GEMM
-// (forward Y = Xcol W^T; weight gradient dW^T = Xcol^T dZ as a split-K GEMM; input
-// gradient dXcol = dZ W then col2im).  FP32 master weights, Adam, BF16 operand copies.
+// outputs: (u_x, u_y, u_z) / U0 and 2 T.  Each convolution is im2col + a tensor-core GEMM:
+// forward Y = Xcol W^T; weight gradient dW^T = Xcol^T dZ as a split-K GEMM; input
+// gradient dX = im2col(dZ) Wf^T, the convolution of the output gradient with the
+// mirrored, channel-exchanged weights Wf.  FP32 master weights, Adam, BF16 operand copies.
 #include <math.h>
 #include <string.h>
 
@@ -32,9 +33,9 @@ namespace {
 constexpr int kLayers = 11;
 
 struct Conv {
-    int cin, cout, level, K27, Kp;
+    int cin, cout, level, K27, Kp, Kpf;  // Kpf: padded 27 cout (input-gradient GEMM)
     float *W, *b, *gW, *gb, *mW, *vW, *mb, *vb, *dWT;
-    __nv_bfloat16 *Wb, *WbT;
+    __nv_bfloat16 *Wb, *Wf;
 };
 
 }  // namespace
@@ -50,7 +51,7 @@ struct lbm_net {
     float *dA10, *dA9, *dC1, *dS1, *dA8, *dA7, *dC2, *dS2, *dA6, *dA5, *dA4, *dP2, *dA2, *dP1, *dA0;
     float *out, *dOut, *scal;
     // scratch
-    __nv_bfloat16 *xcol, *xcolT, *dxcol, *dZ, *dZT;
+    __nv_bfloat16 *xcol, *xcolT, *dZ, *dZT;
     float* y;
     double* loss;
     int* err;
@@ -126,7 +127,7 @@ size_t carve(lbm_net* N, char* base) {
     for (int l = 0; l < kLayers; ++l) {
         Conv& k = N->conv[l];
         const int64_t M = B * N->V[k.level];
-        max_xcol = std::max(max_xcol, M * k.Kp);
+        max_xcol = std::max(max_xcol, M * std::max(k.Kp, k.Kpf));
         max_y = std::max(max_y, M * k.cout);
         const int64_t w = (int64_t)k.cout * k.K27;
         k.W = c.take<float>(w);
@@ -139,7 +140,7 @@ size_t carve(lbm_net* N, char* base) {
         k.vb = c.take<float>(k.cout);
         k.dWT = c.take<float>((int64_t)k.Kp * k.cout);
         k.Wb = c.take<__nv_bfloat16>((int64_t)k.cout * k.Kp);
-        k.WbT = c.take<__nv_bfloat16>((int64_t)k.Kp * k.cout);
+        k.Wf = c.take<__nv_bfloat16>((int64_t)k.cin * k.Kpf);
     }
     N->Wh = c.take<float>(4 * c1);
     N->bh = c.take<float>(4);
@@ -186,7 +187,6 @@ size_t carve(lbm_net* N, char* base) {
     N->scal = c.take<float>(2 * B);
     N->xcol = c.take<bf>(max_xcol);
     N->xcolT = c.take<bf>(max_xcol);
-    N->dxcol = c.take<bf>(max_xcol);
     N->dZ = c.take<bf>(max_y);
     N->dZT = c.take<bf>(max_y);
     N->y = c.take<float>(max_y);
@@ -224,10 +224,10 @@ int conv_bwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, const __nv_bfloat
     splits = std::max(1, std::min(splits, kb));
     NET_CUDA(N, gemm_bf16(N->xcolT, M, N->dZT, M, k.dWT, k.cout, k.Kp, k.cout, (int)M,
                           GEMM_F32_ATOMIC, splits, N->err, st));
-    if (dX) {
-        NET_CUDA(N, gemm_bf16(N->dZ, k.cout, k.WbT, k.cout, N->dxcol, k.Kp, (int)M, k.Kp, k.cout,
-                              GEMM_BF16, 1, N->err, st));
-        NET_CUDA(N, col2im(N->dxcol, B, n, k.cin, k.Kp, dX, accumulate, st));
+    if (dX) {  // dX = im2col(dZ) Wf^T (the xcol scratch is free again)
+        NET_CUDA(N, im2col(N->dZ, B, n, k.cout, k.Kpf, N->xcol, st));
+        NET_CUDA(N, gemm_bf16(N->xcol, k.Kpf, k.Wf, k.Kpf, dX, k.cin, (int)M, k.cin, k.Kpf,
+                              accumulate ? GEMM_F32_ATOMIC : GEMM_F32, 1, N->err, st));
     }
     return LBM_OK;
 }
@@ -312,7 +312,7 @@ int update(lbm_net* N) {
         const int64_t w = (int64_t)k.cout * k.K27;
         NET_CUDA(N, adam(k.W, k.gW, k.mW, k.vW, w, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
         NET_CUDA(N, adam(k.b, k.gb, k.mb, k.vb, k.cout, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
-        NET_CUDA(N, pack_weights(k.W, k.cout, k.K27, k.Kp, k.Wb, k.WbT, st));
+        NET_CUDA(N, pack_weights(k.W, k.cin, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, st));
     }
     NET_CUDA(N, adam(N->Wh, N->gWh, N->mWh, N->vWh, 4 * c.c1, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
     NET_CUDA(N, adam(N->bh, N->gbh, N->mbh, N->vbh, 4, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
@@ -387,8 +387,8 @@ extern "C" int lbm_net_create(const lbm_net_config* cfg, lbm_net** out) {
                      "invalid network: n a multiple of 8 in 8..256, channels multiples of 8 "
                      "(c1 <= 64, c2, c3 <= 256), max_batch >= 1%s");
     const double M0 = (double)c.max_batch * c.n * c.n * c.n;
-    if (M0 * pad64(27 * (c.c2 + c.c1)) > 2.0e9)
-        return nfail(nullptr, LBM_EINVAL, "n^3 * max_batch too large for 32-bit GEMM rows%s");
+    if (M0 > 2.0e9)  // GEMM rows and the weight-gradient K are 32-bit
+        return nfail(nullptr, LBM_EINVAL, "n^3 * max_batch must stay below 2^31%s");
     lbm_net* N = new (std::nothrow) lbm_net();
     if (!N) return nfail(nullptr, LBM_ENOMEM, "host allocation failed%s");
     N->cfg = c;
@@ -408,6 +408,7 @@ extern "C" int lbm_net_create(const lbm_net_config* cfg, lbm_net** out) {
         k.level = level[l];
         k.K27 = 27 * cin[l];
         k.Kp = pad64(k.K27);
+        k.Kpf = pad64(27 * cout[l]);
     }
     if (cudaGetDevice(&N->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&N->sm_count, cudaDevAttrMultiProcessorCount, N->device) != cudaSuccess) {
@@ -439,7 +440,7 @@ extern "C" int lbm_net_create(const lbm_net_config* cfg, lbm_net** out) {
         for (auto& w : host) w = (float)(sd * rng.normal());
         if (cudaMemcpy(k.W, host.data(), host.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
             rc = nfail(N, LBM_ECUDA, "weight upload failed%s");
-        else if (pack_weights(k.W, k.cout, k.K27, k.Kp, k.Wb, k.WbT, N->stream) != cudaSuccess)
+        else if (pack_weights(k.W, k.cin, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, N->stream) != cudaSuccess)
             rc = nfail(N, LBM_ECUDA, "weight packing failed%s");
     }
     if (rc == LBM_OK) {
@@ -494,7 +495,7 @@ extern "C" int lbm_net_set_params(lbm_net* N, const float* host, int64_t count) 
     NET_CUDA(N, e);
     for (int l = 0; l < kLayers; ++l) {
         Conv& k = N->conv[l];
-        NET_CUDA(N, pack_weights(k.W, k.cout, k.K27, k.Kp, k.Wb, k.WbT, N->stream));
+        NET_CUDA(N, pack_weights(k.W, k.cin, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, N->stream));
     }
     return wait_net(N);
 }
@@ -527,6 +528,12 @@ extern "C" int lbm_net_train_step(lbm_net* N, int batch, const float* scalars, c
     NET_RC(update(N));
     if (loss) NET_CUDA(N, cudaMemcpyAsync(loss, N->loss, 8, cudaMemcpyDeviceToHost, N->stream));
     return wait_net(N);
+}
+
+extern "C" int lbm_net_set_lr(lbm_net* N, float lr) {
+    if (!N || !(lr > 0)) return nfail(N, LBM_EINVAL, "NULL network or lr <= 0%s");
+    N->cfg.lr = lr;
+    return LBM_OK;
 }
 
 extern "C" void lbm_net_encode(double Ra, double Pr, float* out2) {

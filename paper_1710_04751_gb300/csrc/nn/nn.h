@@ -28,8 +28,6 @@ namespace nn {
 // layers.cu (channels-last activations, see there)
 cudaError_t im2col(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_bfloat16* Xcol,
                    cudaStream_t st);
-cudaError_t col2im(const __nv_bfloat16* dXcol, int B, int n, int cin, int Kp, float* dX,
-                   int accumulate, cudaStream_t st);
 cudaError_t transpose(const __nv_bfloat16* in, int64_t R, int64_t C, int64_t ld_in,
                       __nv_bfloat16* out, int64_t ld_out, cudaStream_t st);
 cudaError_t bias_relu(const float* Y, const float* bias, int64_t M, int C, __nv_bfloat16* A,
@@ -55,8 +53,8 @@ cudaError_t mse(const float* out, const float* target, int64_t count, float* dOu
                 cudaStream_t st);
 cudaError_t adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
                  float b2, float eps, int step, cudaStream_t st);
-cudaError_t pack_weights(const float* W, int cout, int K27, int Kp, __nv_bfloat16* Wb,
-                         __nv_bfloat16* WbT, cudaStream_t st);
+cudaError_t pack_weights(const float* W, int cin, int cout, int Kp, int Kpf, __nv_bfloat16* Wb,
+                         __nv_bfloat16* Wf, cudaStream_t st);
 cudaError_t unpack_grad(const float* dWT, int cout, int K27, float* gW, cudaStream_t st);
 cudaError_t features(int B, int n, const float* scalars, __nv_bfloat16* X, cudaStream_t st);
 

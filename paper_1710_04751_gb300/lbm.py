@@ -25,6 +25,7 @@ EXPORTS = (
     "lbm_create_params", "lbm_step", "lbm_fields", "lbm_nusselt", "lbm_residual",
     "lbm_get_populations", "lbm_set_populations", "lbm_get_params", "lbm_steps_done",
     "lbm_last_error", "lbm_synchronize", "lbm_destroy", "lbm_nusselt_noalloc", "lbm_set_fields",
+    "lbm_init_fields",
 )
 
 
@@ -110,6 +111,7 @@ def load(build_if_missing=True):
     L.lbm_set_populations.argtypes = [ctypes.c_void_p, _D, _D]
     L.lbm_get_params.argtypes = [ctypes.c_void_p, P(Params)]
     L.lbm_set_fields.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 5
+    L.lbm_init_fields.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 5 + [ctypes.c_int]
     L.lbm_steps_done.argtypes = [ctypes.c_void_p]
     L.lbm_steps_done.restype = ctypes.c_int64
     L.lbm_last_error.argtypes = [ctypes.c_void_p]
@@ -276,9 +278,10 @@ class LBM:
         g = np.ascontiguousarray(g, dtype=np.float64).reshape(self.lattice, nz, ny, nx)
         self._check(self._L.lbm_set_populations(self._ctx, _dp(f), _dp(g)))
 
-    def set_fields(self, ux, uy, uz, T, rho=None):
+    def set_fields(self, ux, uy, uz, T, rho=None, iterations=0):
         """Populations at the equilibria of the fields: torch CUDA float64 tensors of
-        shape (nz, ny, nx) on this context's device (rho None: 1)."""
+        shape (nz, ny, nx) on this context's device (rho None: 1); with iterations > 0
+        followed by that many rounds of the consistent initialisation (lbm_init_fields)."""
         import torch
         arrs = [rho, ux, uy, uz, T]
         for a in arrs:
@@ -286,7 +289,7 @@ class LBM:
                                   or a.numel() != self.ncell):
                 raise ValueError("fields must be contiguous CUDA float64 tensors of ncell values")
         ptr = [ctypes.c_void_p(a.data_ptr()) if a is not None else None for a in arrs]
-        self._check(self._L.lbm_set_fields(self._ctx, *ptr))
+        self._check(self._L.lbm_init_fields(self._ctx, *ptr, int(iterations)))
 
     def params(self):
         return self.params_struct().as_dict()

@@ -12,7 +12,7 @@ EXPORTS = (
     "lbm_nn_gemm_bf16", "lbm_net_default_config", "lbm_net_create", "lbm_net_destroy",
     "lbm_net_param_count", "lbm_net_encode", "lbm_net_get_params", "lbm_net_set_params",
     "lbm_net_forward", "lbm_net_gradients", "lbm_net_train_step", "lbm_net_last_error",
-    "lbm_net_targets", "lbm_net_warm_start",
+    "lbm_net_targets", "lbm_net_warm_start", "lbm_net_set_lr",
 )
 
 
@@ -50,7 +50,8 @@ def _lib():
     L.lbm_net_last_error.argtypes = [vp]
     L.lbm_net_last_error.restype = ctypes.c_char_p
     L.lbm_net_targets.argtypes = [vp, vp]
-    L.lbm_net_warm_start.argtypes = [vp, vp, i32]
+    L.lbm_net_warm_start.argtypes = [vp, vp, i32, i32]
+    L.lbm_net_set_lr.argtypes = [vp, ctypes.c_float]
     _bound = True
     return L
 
@@ -97,13 +98,14 @@ def targets(sim):
     return out
 
 
-def warm_start(sim, pred, m):
-    """Start an LBM context from a prediction pred (CUDA float32 [m^3][4])."""
+def warm_start(sim, pred, m, iterations=0):
+    """Start an LBM context from a prediction pred (CUDA float32 [m^3][4]), with
+    `iterations` rounds of the consistent initialisation."""
     import torch
     pred = pred.to(torch.float32).contiguous()
     if pred.numel() != 4 * m ** 3:
         raise ValueError("pred must hold m^3 x 4 values")
-    sim._check(_lib().lbm_net_warm_start(sim._ctx, pred.data_ptr(), int(m)))
+    sim._check(_lib().lbm_net_warm_start(sim._ctx, pred.data_ptr(), int(m), int(iterations)))
 
 
 class Net:
@@ -163,6 +165,9 @@ class Net:
         self._check(self._L.lbm_net_gradients(self._net, arr.shape[0], ptr, t.data_ptr(),
                                               ctypes.byref(loss)))
         return loss.value
+
+    def set_lr(self, lr):
+        self._check(self._L.lbm_net_set_lr(self._net, float(lr)))
 
     def train_step(self, scalars, targets):
         arr, ptr = _scalars(scalars)

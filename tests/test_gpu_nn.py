@@ -258,3 +258,25 @@ def test_warm_start_sets_the_equilibria_of_the_resampled_prediction(m, grid):
         assert np.abs(f[:, k, j, i] - formb.flow_equilibrium(1.0, uu)).max() <= 1e-12
         assert np.abs(g[:, k, j, i] - formb.thermal_equilibrium(T, uu, 15, cs2)).max() <= 1e-12
     sim.close()
+
+
+@pytest.mark.parametrize("iterations", [1, 4])
+def test_consistent_initialisation_against_oracle(iterations):
+    torch = torch_mod()
+    import oracle
+    from oracle import nn_oracle as nno
+    grid = (6, 5, 4)
+    sim = _ctx(grid)
+    p = oracle.Problem.cavity(6, 1e4, ny=5, nz=4)
+    rng = np.random.default_rng(10)
+    shape = (4, 5, 6)
+    fields = {"ux": 0.03 * rng.standard_normal(shape), "uy": 0.03 * rng.standard_normal(shape),
+              "uz": 0.03 * rng.standard_normal(shape), "T": rng.uniform(-0.5, 0.5, shape)}
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    sim.set_fields(dev(fields["ux"]), dev(fields["uy"]), dev(fields["uz"]), dev(fields["T"]),
+                   iterations=iterations)
+    f, g = sim.get_populations()
+    F, G = nno.consistent_init(p, fields, iterations)
+    assert np.abs(f - F).max() <= 1e-12 and np.abs(g - G).max() <= 1e-12
+    assert sim.steps_done == 0
+    sim.close()
