@@ -361,6 +361,73 @@ def batch_to_convergence(lbm, members, max_steps, tol=1e-6, mode="graph"):
             "progress": done_at[:: max(1, len(done_at) // 12)], "converged_members": nus}
 
 
+def measured_peak_tflops():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def net_variant():
+    """The warm-start network's tensor-core path: tcgen05 GEMM throughput (a large GEMM and
+    the network's own convolution shapes at 64^3, batch 2) against the measured BF16
+    peak, and the time of one training step and one forward pass at 64^3."""
+    import torch
+    from paper_1710_04751_gb300 import net
+    peak, kind = measured_peak_tflops()
+    gen = torch.Generator(device="cuda").manual_seed(0)
+
+    def gemm_rate(M, N, K, mode, splits=1, reps=5):
+        A = torch.randn((M, K), device="cuda", generator=gen).to(torch.bfloat16)
+        B = torch.randn((N, K), device="cuda", generator=gen).to(torch.bfloat16)
+        C = torch.zeros((M, N), device="cuda",
+                        dtype=torch.bfloat16 if mode == net.GEMM_BF16 else torch.float32)
+        net.gemm_bf16(A, B, C, mode, splits=splits)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 1e30
+        for _ in range(reps):
+            e0.record(st)
+            net.gemm_bf16(A, B, C, mode, splits=splits)
+            e1.record(st)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        tf = 2.0 * M * N * K / best / 1e12
+        return {"M": M, "N": N, "K": K, "ms": round(best * 1e3, 4), "tflops": round(tf, 1),
+                "frac": round(tf / peak, 4)}
+
+    M0 = 2 * 64 ** 3
+    out = {
+        "peak_tflops": peak, "peak_kind": kind,
+        "gemm_large": gemm_rate(65536, 256, 8192, net.GEMM_F32),
+        "conv_fwd_L9": gemm_rate(M0, 32, 2624, net.GEMM_F32),      # 96 -> 32 channels at 64^3
+        "conv_dgrad_L9": gemm_rate(M0, 96, 896, net.GEMM_F32),     # input gradient
+        "conv_wgrad_L9": gemm_rate(2624, 32, M0, net.GEMM_F32_ADD, splits=64),
+    }
+    for B in (2, 4):
+        netw = net.Net(n=64, max_batch=B, seed=1)
+        t = torch.randn((B, 64 ** 3, 4), device="cuda", generator=gen) * 0.3
+        sc = [[0.1, 0.2]] * B
+        netw.train_step(sc, t)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            netw.train_step(sc, t)
+        torch.cuda.synchronize()
+        ts = (time.perf_counter() - t0) / 5
+        t0 = time.perf_counter()
+        for _ in range(5):
+            netw.forward(sc)
+        torch.cuda.synchronize()
+        tf = (time.perf_counter() - t0) / 5
+        out[f"batch{B}"] = {"train_step_ms": round(ts * 1e3, 2), "forward_ms": round(tf * 1e3, 2)}
+        out["params"] = netw.param_count
+        netw.close()
+    return out
+
+
 def cpu_baseline(sample_steps=3, q=15):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of the same
     workload (the 128^3 Ra = 1e5 cavity, a few steps from its initial state)."""
@@ -454,7 +521,17 @@ def gpu_arm(args):
             "D3Q15+D3Q7": time_to_steady(lbm, 7, args.steady_max_steps),
         }
     if not args.no_batch:
-        line["batch"] = batch_variant(lbm, args.batch_steps, 3, peak, args.batch_converge_steps)
+        line["batch"] = batch_variant(lbm, args.batch_steps, RESIDUAL_INTERVAL, peak,
+                                      args.batch_converge_steps)
+    if not args.no_net:
+        line["net"] = net_variant()
+    if args.warmstart:
+        from paper_1710_04751_gb300 import warmstart
+        res, netw = warmstart.experiment(count_train=args.ws_train, count_test=args.ws_test,
+                                         count_big=args.ws_big, epochs=args.ws_epochs)
+        line["warmstart"] = {"train": res["train"], "test": res["test"]["summary"],
+                             "big": res["big"]["summary"] if res["big"] else None}
+        netw.close()
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e_variant(lbm, 15, args.e2e_reps, device)
     if rank == 0 and not args.no_cpu_baseline:
@@ -528,6 +605,13 @@ def main(argv=None):
     ap.add_argument("--steady-max-steps", type=int, default=400_000)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-cavity batched form")
     ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--no-net", action="store_true", help="skip the warm-start network timings")
+    ap.add_argument("--warmstart", action="store_true",
+                    help="also run the learned warm start end to end (about 15 minutes)")
+    ap.add_argument("--ws-train", type=int, default=400)
+    ap.add_argument("--ws-test", type=int, default=50)
+    ap.add_argument("--ws-big", type=int, default=8)
+    ap.add_argument("--ws-epochs", type=int, default=60)
     ap.add_argument("--batch-converge-steps", type=int, default=0,
                     help="also run the 64 cavities from rest to their own convergence (max steps)")
     ap.add_argument("--ref-budget", type=float, default=90.0,
