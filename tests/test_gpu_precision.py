@@ -99,3 +99,112 @@ def test_steady_nusselt_of_the_16bit_forms():
     for k in ("mid_mean", "hot_wall_mean"):
         assert out["FP16_DEV"][0][k] == pytest.approx(ref[k], rel=5e-3), k
         assert out["BF16_DEV"][0][k] == pytest.approx(ref[k], rel=2e-2), k
+
+
+# ------------------------------------------------------------------------------------
+# The pair kernel of the 16-bit forms: a cavity with an even nx updates two x-neighbours
+# per thread with packed FP32 pair arithmetic in every row away from the y and z walls
+# (the other rows, and odd nx, take the one-node update).  Random rates (all different),
+# both E forms, both adiabatic forms, a body force and a heat source.
+# ------------------------------------------------------------------------------------
+
+PAIR_CASES = [
+    # nx, ny, nz, q, adiabatic_mode, e4_mode, heat source R, body force
+    (2, 5, 4, 15, 1, 0, 0.0, False),     # one pair: lane .x at the cold face, .y at the hot face
+    (4, 3, 3, 7, 1, 1, 2e-3, True),      # a single interior row
+    (10, 6, 5, 15, 0, 1, -1e-3, True),
+    (66, 4, 5, 15, 1, 0, 0.0, False),    # 33 pairs: one 64-thread block per row, ragged
+    (130, 3, 4, 7, 1, 0, 1e-3, False),   # 65 pairs: two blocks per row
+    (64, 5, 3, 15, 1, 0, 0.0, True),     # 32 pairs: a 32-thread block per row
+]
+
+
+def _pair_problem(case, seed):
+    from tests.test_gpu_parity import _case_problem
+    nx, ny, nz, q, am, e4, R, force = case
+    p = _case_problem((nx, ny, nz, q, oracle.BC_CAVITY, am, e4), seed)
+    p.heat_source = R
+    if force:
+        p.ext_force = (1e-4, -2e-4, 5e-5)
+    if q == 7:
+        p.cs2_phi = 0.25
+    return p
+
+
+@pytest.mark.parametrize("prec_name", ["FP16_DEV", "BF16_DEV"])
+@pytest.mark.parametrize("case", PAIR_CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}-q{c[3]}" for c in PAIR_CASES])
+def test_pair_kernel_one_step_against_oracle(prec_name, case):
+    import paper_1710_04751_gb300 as lbm
+    p = _pair_problem(case, 900 + case[0] + case[2])
+    F, G = random_state(p, 60 + case[1])
+    sim = gpu_for(p, getattr(lbm, prec_name))
+    sim.set_populations(F, G)
+    f, g = sim.get_populations()
+    for _ in range(2):  # two steps, each from the GPU's own decoded state
+        sim.step(1)
+        F1, G1 = p.step(f, g)
+        f, g = sim.get_populations()
+        bf, bg = _bound(p, prec_name, F1, G1)
+        assert (np.abs(f - F1) <= bf).all(), np.max(np.abs(f - F1) / bf)
+        assert (np.abs(g - G1) <= bg).all(), np.max(np.abs(g - G1) / bg)
+
+
+@pytest.mark.parametrize("q", [15, 7])
+def test_pair_kernel_sampled_nodes_at_128(q):
+    # the benchmark's 16-bit workload: 128^3, Ra = 1e5, in the launch configuration the
+    # bench times; every corner, edge and face class plus random interior nodes
+    import paper_1710_04751_gb300 as lbm
+    from tests.test_gpu_fullsize import sample_nodes
+    n = 128
+    p = oracle.Problem.cavity(n, 1e5, q_g=q)
+    sim = lbm.LBM((n, n, n), q, Ra=1e5, Pr=0.71, Ma=0.05 * math.sqrt(3.0), precision=lbm.FP16_DEV)
+    sim.step(300)
+    f0, g0 = sim.get_populations()
+    sim.step(1)
+    f1, g1 = sim.get_populations()
+    wf = oracle.weights_flow()
+    wt = oracle.weights_thermal(q, p.cs2_phi)
+    floor_g = thermal_floor(q, p.cs2_phi, p.T_hot - p.T_cold)
+    e = EPS["FP16_DEV"]
+    for (i, j, k) in sample_nodes(n, 11 + q):
+        fr, gr = p.cell_update(f0, g0, i, j, k)
+        bf = e * np.abs(fr - wf) + FP32_REL * np.maximum(np.abs(fr), wf) + 2.0 ** -25
+        bg = e * np.abs(gr - wt * gr.sum()) + FP32_REL * np.maximum(np.abs(gr), floor_g) + 2.0 ** -25
+        assert (np.abs(f1[:, k, j, i] - fr) <= bf).all(), (i, j, k)
+        assert (np.abs(g1[:, k, j, i] - gr) <= bg).all(), (i, j, k)
+    assert abs(f1.sum() - f0.sum()) <= 1e-5 * f0.sum()
+
+
+# ------------------------------------------------------------------------------------
+# The staged row kernel of the 16-bit forms (bulk copies into shared-memory stages): the
+# cavity with nx a multiple of 8 from 16 to 512.  Rows per grid large enough that every
+# block's ring of stages wraps around many times.
+# ------------------------------------------------------------------------------------
+
+ROWS_CASES = [
+    # nx, ny, nz, q, adiabatic_mode, e4_mode, heat source R, body force
+    (16, 3, 3, 15, 1, 0, 0.0, False),    # one interior row
+    (24, 5, 4, 7, 1, 1, 1e-3, True),
+    (40, 6, 7, 15, 0, 0, -2e-3, True),
+    (16, 60, 40, 15, 1, 0, 0.0, False),  # 2400 rows: many rows per block
+    (16, 48, 50, 7, 1, 0, 0.0, False),
+    (512, 3, 4, 15, 1, 1, 0.0, True),    # the widest staged row
+]
+
+
+@pytest.mark.parametrize("prec_name", ["FP16_DEV", "BF16_DEV"])
+@pytest.mark.parametrize("case", ROWS_CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}-q{c[3]}" for c in ROWS_CASES])
+def test_rows_kernel_steps_against_oracle(prec_name, case):
+    import paper_1710_04751_gb300 as lbm
+    p = _pair_problem(case, 1300 + case[1] + case[2])
+    F, G = random_state(p, 70 + case[0])
+    sim = gpu_for(p, getattr(lbm, prec_name))
+    sim.set_populations(F, G)
+    f, g = sim.get_populations()
+    for _ in range(2):
+        sim.step(1)
+        F1, G1 = p.step(f, g)
+        f, g = sim.get_populations()
+        bf, bg = _bound(p, prec_name, F1, G1)
+        assert (np.abs(f - F1) <= bf).all(), np.max(np.abs(f - F1) / bf)
+        assert (np.abs(g - G1) <= bg).all(), np.max(np.abs(g - G1) / bg)
