@@ -41,9 +41,6 @@ struct DevState {
 
 constexpr int kPartialBlocks = 1024;   // max blocks of the face reduction
 constexpr int kResultDoubles = 16;
-// Bit of the context's error word (DevState::nonfinite, bit 0: a non-finite temperature)
-// set when a bounded wait of the staged step kernel ran out.
-constexpr int kStageTimeout = 2;
 
 // Launchers (return cudaGetLastError()), templated on the storage type S (double,
 // float, __half, __nv_bfloat16); arithmetic is Storage<S>::real.  `cur` selects the

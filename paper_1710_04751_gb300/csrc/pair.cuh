@@ -24,6 +24,10 @@
 #include "internal.h"
 #include "lattice.cuh"
 
+#ifndef LBM_PAIR_LEAN
+#define LBM_PAIR_LEAN 0
+#endif
+
 namespace lbm {
 
 // ---------------------------------------------------------------------------------
@@ -358,6 +362,142 @@ __device__ __forceinline__ void pair_collide_store(float2 (&f)[15], float2 (&g)[
         *reinterpret_cast<two*>(Gout + a * P + c0) = Pk::from_float2(fma2(q.nwg[a], T, g[a]));
 }
 
+
+// ---------------------------------------------------------------------------------
+// Lean form of pair_collide_store (built with LBM_PAIR_LEAN): the post-collision
+// populations are formed from the post-collision raw moments (m + the raw increment),
+// not added to the pulled populations, so a pulled vector is dead once its raw moments
+// are taken; the scalar collision runs before the flow collision.  Same state up to
+// rounding.
+// ---------------------------------------------------------------------------------
+
+// The populations whose raw moments are r (the inverse of raw15_2).
+__device__ __forceinline__ void populations15_2(const Raw15<float2>& r, float2 (&p)[15]) {
+    const float2 G0 = r.xxyy, Gx = r.xyy, Gy = r.xxy, Gz = r.xxz;
+    const float2 P0 = add2(G0, Gz), P0m = sub2(G0, Gz), Px = add2(Gx, r.xz), Pxm = sub2(Gx, r.xz);
+    const float2 Py = add2(Gy, r.yz), Pym = sub2(Gy, r.yz);
+    const float2 Pxy = add2(r.xy, r.xyz), Pxym = sub2(r.xy, r.xyz);
+    const float2 Q0 = add2(P0, Py), Q1 = sub2(P0, Py), X0 = add2(Px, Pxy), X1 = sub2(Px, Pxy);
+    const float2 Q2 = add2(P0m, Pym), Q3 = sub2(P0m, Pym), X2 = add2(Pxm, Pxym), X3 = sub2(Pxm, Pxym);
+    const float2 e = make_float2(0.125f, 0.125f), h = make_float2(0.5f, 0.5f);
+    p[7] = mul2(e, add2(Q0, X0));
+    p[8] = mul2(e, sub2(Q0, X0));
+    p[9] = mul2(e, add2(Q1, X1));
+    p[10] = mul2(e, sub2(Q1, X1));
+    p[11] = mul2(e, add2(Q2, X2));
+    p[12] = mul2(e, sub2(Q2, X2));
+    p[13] = mul2(e, add2(Q3, X3));
+    p[14] = mul2(e, sub2(Q3, X3));
+    const float2 px = sub2(r.xx, G0), qx = sub2(r.x, Gx);
+    const float2 py = sub2(r.yy, G0), qy = sub2(r.y, Gy);
+    const float2 pz = sub2(r.zz, G0), qz = sub2(r.z, Gz);
+    p[1] = mul2(h, add2(px, qx));
+    p[2] = mul2(h, sub2(px, qx));
+    p[3] = mul2(h, add2(py, qy));
+    p[4] = mul2(h, sub2(py, qy));
+    p[5] = mul2(h, add2(pz, qz));
+    p[6] = mul2(h, sub2(pz, qz));
+    p[0] = sub2(sub2(sub2(sub2(r.m0, px), py), pz), G0);
+}
+
+__device__ __forceinline__ Raw15<float2> add15_2(const Raw15<float2>& a, const Raw15<float2>& b) {
+    Raw15<float2> c;
+    c.m0 = add2(a.m0, b.m0); c.x = add2(a.x, b.x); c.y = add2(a.y, b.y); c.z = add2(a.z, b.z);
+    c.xy = add2(a.xy, b.xy); c.xz = add2(a.xz, b.xz); c.yz = add2(a.yz, b.yz);
+    c.xx = add2(a.xx, b.xx); c.yy = add2(a.yy, b.yy); c.zz = add2(a.zz, b.zz);
+    c.xyy = add2(a.xyy, b.xyy); c.xxy = add2(a.xxy, b.xxy); c.xxz = add2(a.xxz, b.xxz);
+    c.xyz = add2(a.xyz, b.xyz); c.xxyy = add2(a.xxyy, b.xxyy);
+    return c;
+}
+
+// Flow increments in raw moments (collide_flow2's d, shifted back by u).
+__device__ __forceinline__ Raw15<float2> flow_increment2(const Raw15<float2>& m, float2 inv_rho,
+                                                         float2 Fz, const PairParams& q,
+                                                         const Vel2& vu) {
+    const float2 rho = m.m0;
+    const Raw15<float2> k = shift15_2<true>(m, vel2_negated(vu));
+    Raw15<float2> d;
+    d.m0 = make_float2(0.f, 0.f);
+    d.x = q.fx;
+    d.y = q.fy;
+    d.z = Fz;
+    d.xy = mul2(q.nomf[4], k.xy);
+    d.xz = mul2(q.nomf[5], k.xz);
+    d.yz = mul2(q.nomf[6], k.yz);
+    const float2 sxy = add2(k.xx, k.yy);
+    const float2 d1 = mul2(q.nomf[7], sub2(k.xx, k.yy));
+    const float2 d2 = mul2(q.nomf[8], fma2(make_float2(-2.f, -2.f), k.zz, sxy));
+    const float2 dtr = fma2(q.omf9, rho, mul2(q.nomf[9], add2(sxy, k.zz)));
+    split_second_order2(d1, d2, dtr, d.xx, d.yy, d.zz);
+    d.xyy = fma2(q.nomf[10], k.xyy, mul2(q.cf3[0], q.fx));
+    d.xxy = fma2(q.nomf[11], k.xxy, mul2(q.cf3[1], q.fy));
+    d.xxz = fma2(q.nomf[12], k.xxz, mul2(q.cf3[2], Fz));
+    d.xyz = mul2(q.nomf[13], k.xyz);
+    const float2 E = q.e4_mode == 1 ? mul2(rho, make_float2(1.0f / 9.0f, 1.0f / 9.0f))
+                                    : mul2(mul2(add2(k.xx, d.xx), add2(k.yy, d.yy)), inv_rho);
+    d.xxyy = fma2(q.omf14, E, mul2(q.nomf[14], k.xxyy));
+    return shift15_2<false>(d, vu);
+}
+
+// Scalar D3Q15 increments in raw moments (collide_thermal15_2's d, shifted back by u).
+__device__ __forceinline__ Raw15<float2> thermal15_increment2(const Raw15<float2>& m, const Vel2& vu,
+                                                              const PairParams& q) {
+    const float2 phi = add2(m.m0, q.halfR);
+    const Raw15<float2> k = shift15_2<true>(m, vel2_negated(vu));
+    Raw15<float2> d;
+    d.m0 = q.R;
+    d.x = mul2(q.nomg[1], k.x);
+    d.y = mul2(q.nomg[2], k.y);
+    d.z = mul2(q.nomg[3], k.z);
+    d.xy = mul2(q.nomg[4], k.xy);
+    d.xz = mul2(q.nomg[5], k.xz);
+    d.yz = mul2(q.nomg[6], k.yz);
+    const float2 sxy = add2(k.xx, k.yy);
+    const float2 d1 = mul2(q.nomg[7], sub2(k.xx, k.yy));
+    const float2 d2 = mul2(q.nomg[8], fma2(make_float2(-2.f, -2.f), k.zz, sxy));
+    const float2 dtr = fma2(q.omg_tr, phi, mul2(q.nomg[9], add2(sxy, k.zz)));
+    split_second_order2(d1, d2, dtr, d.xx, d.yy, d.zz);
+    d.xyy = mul2(q.nomg[10], k.xyy);
+    d.xxy = mul2(q.nomg[11], k.xxy);
+    d.xxz = mul2(q.nomg[12], k.xxz);
+    d.xyz = mul2(q.nomg[13], k.xyz);
+    d.xxyy = fma2(q.omg_4, phi, mul2(q.nomg[14], k.xxyy));
+    return shift15_2<true>(d, vu);
+}
+
+template <typename S, int Q>
+__device__ __forceinline__ void pair_collide_store_lean(float2 (&f)[15], float2 (&g)[Q],
+                                                        S* __restrict__ Fout, S* __restrict__ Gout,
+                                                        float* __restrict__ Tout,
+                                                        const PairParams& q, int P, int c0) {
+    using Pk = Pack<S>;
+    using two = typename Pk::two;
+    float2 T = g[0];
+#pragma unroll
+    for (int a = 1; a < Q; ++a) T = add2(T, g[a]);
+    T = add2(T, q.halfR);
+    const float2 Fz = fma2(q.gbeta, sub2(T, q.T0), q.fz);
+    const Raw15<float2> mf = raw15_2(f);
+    const float2 inv_rho = make_float2(1.0f / mf.m0.x, 1.0f / mf.m0.y);
+    const Vel2 vu = vel2(mul2(add2(mf.x, q.halffx), inv_rho), mul2(add2(mf.y, q.halffy), inv_rho),
+                         mul2(fma2(make_float2(0.5f, 0.5f), Fz, mf.z), inv_rho));
+    // scalar collision first: its populations die here
+    if constexpr (Q == 15) {
+        const Raw15<float2> mg = raw15_2(g);
+        populations15_2(add15_2(mg, thermal15_increment2(mg, vu, q)), g);
+    } else {
+        collide_thermal7_2(g, vu, q);
+    }
+    *reinterpret_cast<float2*>(Tout + c0) = T;
+#pragma unroll
+    for (int a = 0; a < Q; ++a)
+        *reinterpret_cast<two*>(Gout + a * P + c0) = Pk::from_float2(fma2(q.nwg[a], T, g[a]));
+    populations15_2(add15_2(mf, flow_increment2(mf, inv_rho, Fz, q, vu)), f);
+#pragma unroll
+    for (int a = 0; a < 15; ++a)
+        *reinterpret_cast<two*>(Fout + a * P + c0) = Pk::from_float2(sub2(f[a], q.wf[a]));
+}
+
 // ---------------------------------------------------------------------------------
 // The update of nodes c0 (i = 2t) and c0 + 1 of a row away from the y and z walls.
 // lo: i = 0 is the first node (its +x links come through the cold face); hi: i + 1 is
@@ -428,7 +568,11 @@ __device__ __forceinline__ void pair_node(const S* __restrict__ Fin, const S* __
             f[a] = add2(make_float2(Pk::to_float(Fs[c0]), Pk::to_float(Fs[i1])), q.wf[a]);
         }
     }
+#if LBM_PAIR_LEAN
+    pair_collide_store_lean<S, Q>(f, g, Fout, Gout, Tout, q, P, c0);
+#else
     pair_collide_store<S, Q>(f, g, Fout, Gout, Tout, q, P, c0);
+#endif
 }
 
 }  // namespace lbm

@@ -2,15 +2,6 @@
 // arXiv:1710.04751 (the node update itself is node.cuh) and their launcher.
 #include "node.cuh"
 #include "pair.cuh"
-#include "rows.cuh"
-
-// The staged row kernel (rows.cuh) is built only with -DLBM_ROWS_KERNEL=1: measured slower
-// than the pair kernel at 128^3 (0.16-0.25 ms against 0.088 ms per step).
-#ifndef LBM_ROWS_KERNEL
-#define LBM_ROWS_KERNEL 0
-#endif
-
-#include <algorithm>
 
 namespace lbm {
 
@@ -148,56 +139,6 @@ static bool launch_pair(const DevState& s, int cur, const ParamsOf<S>& p, cudaSt
     }
 }
 
-// The staged row kernel (rows.cuh) of the 16-bit forms: the cavity with nx a multiple of 8
-// (16-byte aligned rows) up to kRowsMaxNx.  Grid: as many blocks as fit on the device
-// (cached per thread for the last shared-memory size and device), at most one per row.
-template <typename S, int Q>
-static cudaError_t launch_rows_q(const DevState& s, int cur, const ParamsOf<S>& p,
-                                 const PairParams& q, cudaStream_t st) {
-    constexpr int NST = LBM_ROWS_STAGES;
-    auto kern = step_rows_kernel<S, Q, NST>;
-    const RowLayout L = row_layout<Q>(p.nx);
-    const int smem = NST * L.stage + NST * 8;
-    struct Cache {
-        const void* kern = nullptr;
-        int dev = -1, smem = -1, grid = 0;
-    };
-    static thread_local Cache cache;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (cache.kern != (const void*)kern || cache.dev != dev || cache.smem != smem) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        int per_sm = 0, sms = 0;
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRowsThreads, smem);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        cache = {(const void*)kern, dev, smem, std::max(1, per_sm) * sms};
-    }
-    const int grid = std::min(p.ny * p.nz, cache.grid);
-    kern<<<grid, kRowsThreads, smem, st>>>(
-        static_cast<const S*>(s.F[cur]), static_cast<const S*>(s.G[cur]),
-        static_cast<const float*>(s.T[cur]), static_cast<S*>(s.F[cur ^ 1]),
-        static_cast<S*>(s.G[cur ^ 1]), static_cast<float*>(s.T[cur ^ 1]), p, q, s.nonfinite);
-    return cudaGetLastError();
-}
-
-// Launches the staged row kernel when it applies; returns false otherwise.
-template <typename S>
-static bool launch_rows(const DevState& s, int cur, const ParamsOf<S>& p, cudaStream_t st,
-                        cudaError_t* err) {
-    if constexpr (!Storage<S>::deviation) {
-        return false;
-    } else {
-        if (p.boundary != 0 || p.nx % 8 != 0 || p.nx < 16 || p.nx > kRowsMaxNx || p.ny < 3 ||
-            p.nz < 3 || 15 * p.plane >= (int64_t(1) << 31))
-            return false;
-        const PairParams q = make_pair_params(p, s.Q);
-        *err = s.Q == 15 ? launch_rows_q<S, 15>(s, cur, p, q, st) : launch_rows_q<S, 7>(s, cur, p, q, st);
-        return true;
-    }
-}
 
 template <typename S>
 cudaError_t launch_step(const DevState& s, int cur, const ParamsOf<S>& p, cudaStream_t st) {
@@ -207,10 +148,6 @@ cudaError_t launch_step(const DevState& s, int cur, const ParamsOf<S>& p, cudaSt
     S* Gout = static_cast<S*>(s.G[cur ^ 1]);
     const float* Tin = static_cast<const float*>(s.T[cur]);
     float* Tout = static_cast<float*>(s.T[cur ^ 1]);
-#if LBM_ROWS_KERNEL
-    cudaError_t e = cudaSuccess;
-    if (launch_rows<S>(s, cur, p, st, &e)) return e;
-#endif
     if (launch_pair<S>(s, cur, p, st)) return cudaGetLastError();
     if (p.boundary == 0 && p.ny <= 65535 && p.nz <= 65535 && 15 * p.plane < (int64_t(1) << 31)) {
         const int bx = 128;

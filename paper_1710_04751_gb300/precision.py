@@ -9,13 +9,16 @@ accuracy and what it saves in time:
         [--ref-Ra 1e5] [--max-steps 400000] [--fp64-seconds 60]
 
 Part 1, the large cavity (default 256^3, Ra = 1e6, Pr = 0.71, U0 = 0.05, D3Q15 flow and
-scalar): FP32, FP16 and BF16 from rest until max |dT| per 100 steps < 1e-6 (steps, wall
-seconds, steady Nusselt numbers, peak velocities, mid-plane fields; 16-bit against FP32),
+scalar): FP32, FP16 and BF16 from rest to the steady state (steps, wall seconds, steady
+Nusselt numbers, peak velocities, mid-plane fields; 16-bit against FP32),
 and an FP64 run of as many steps as fit in --fp64-seconds, against which the three are
 compared after the same number of steps.
 
 Part 2, the reference cavity (default 64^3, Ra = 1e5): FP64, FP32, FP16 and BF16 to the
-steady state (max |dT| per 100 steps < 1e-6); every form against FP64.
+steady state; every form against FP64.
+
+Steady state, for every form: the hot-wall Nusselt number changes by less than 1e-5
+(relative) over 10 000 steps (run_to_steady).
 
 Mid-plane fields: T and u on the symmetry plane y = L/2 (the mean of the two straddling
 layers for even n), errors as max and RMS of |difference| over the plane, T in units of
@@ -69,14 +72,17 @@ def nu_errors(a, b):
     return {k: float((a[k] - b[k]) / b[k]) if b[k] != 0 else float(a[k] - b[k]) for k in NU_KEYS}
 
 
-def run_to_steady(n, Ra, form, max_steps, threshold, chunk=2000):
-    """From rest until max |dT| per 100 steps < threshold (or max_steps)."""
+def run_to_steady(n, Ra, form, max_steps, nu_tol=1e-5, window=10_000, chunk=2000):
+    """From rest until the hot-wall Nusselt number changes by less than nu_tol (relative)
+    over `window` steps, or max_steps.  The same test ends every storage form: the
+    residual max |dT| per 100 steps has a rounding floor of about 2e-5 in FP16 and 2e-4 in
+    BF16, so a residual threshold below those is never met; it is reported too."""
     import torch
     sim = _new(n, Ra, form)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = -1.0
-    diverged = False
+    res, history = -1.0, []
+    diverged = converged = False
     while sim.steps_done < max_steps:
         try:
             sim.step(chunk)
@@ -86,16 +92,19 @@ def run_to_steady(n, Ra, form, max_steps, threshold, chunk=2000):
             diverged = True
             break
         res = sim.residual()
-        if 0 <= res < threshold:
+        history.append((sim.steps_done, sim.nusselt()["hot_wall_mean"]))
+        back = [h for s_, h in history if s_ <= sim.steps_done - window]
+        if back and abs(history[-1][1] - back[-1]) <= nu_tol * abs(history[-1][1]):
+            converged = True
             break
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     nu = sim.nusselt()
-    rec = {"form": form, "converged": bool(0 <= res < threshold), "diverged": diverged,
-           "steps": sim.steps_done,
-           "seconds": round(dt, 3), "residual_per_100": res, "threshold": threshold,
-           "nu": {k: nu[k] for k in NU_KEYS}, "positions": {k: nu[k] for k in
-                                                         ("mid_max_z", "mid_min_z", "umax_z", "wmax_x")}}
+    rec = {"form": form, "converged": converged, "diverged": diverged, "steps": sim.steps_done,
+           "seconds": round(dt, 3), "residual_per_100": res,
+           "criterion": f"|dNu_hot|/Nu_hot < {nu_tol:g} over {window} steps",
+           "nu": {k: nu[k] for k in NU_KEYS},
+           "positions": {k: nu[k] for k in ("mid_max_z", "mid_min_z", "umax_z", "wmax_x")}}
     return sim, rec
 
 
@@ -113,7 +122,7 @@ def large_cavity(n, Ra, max_steps, fp64_seconds):
     out = {"grid": n, "Ra": Ra, "Pr": PR, "U0": U0, "lattice": "D3Q15+D3Q15"}
     steady, planes = {}, {}
     for form in ("FP32", "FP16_DEV", "BF16_DEV"):
-        sim, rec = run_to_steady(n, Ra, form, max_steps, 1e-6)
+        sim, rec = run_to_steady(n, Ra, form, max_steps)
         rec["mlups"] = round(n ** 3 * rec["steps"] / rec["seconds"] / 1e6, 1)
         steady[form] = rec
         planes[form] = mid_plane(sim)
@@ -142,11 +151,11 @@ def large_cavity(n, Ra, max_steps, fp64_seconds):
     return out
 
 
-def reference_cavity(n, Ra, max_steps):
+def reference_cavity(n, Ra, ref_max_steps):
     out = {"grid": n, "Ra": Ra, "Pr": PR, "U0": U0, "lattice": "D3Q15+D3Q15"}
     steady, planes = {}, {}
     for form in FORMS:
-        sim, rec = run_to_steady(n, Ra, form, max_steps, 1e-6)
+        sim, rec = run_to_steady(n, Ra, form, ref_max_steps)
         steady[form] = rec
         planes[form] = mid_plane(sim)
         sim.close()
@@ -163,6 +172,9 @@ def main(argv=None):
     ap.add_argument("--ref-n", type=int, default=64)
     ap.add_argument("--ref-Ra", type=float, default=1e5)
     ap.add_argument("--max-steps", type=int, default=400_000)
+    ap.add_argument("--ref-max-steps", type=int, default=120_000,
+                    help="cap of the reference runs (the 64^3 Ra = 1e5 cavity leaves its steady "
+                         "state after about 1.3e5 steps)")
     ap.add_argument("--fp64-seconds", type=float, default=60.0)
     ap.add_argument("--skip-large", action="store_true")
     ap.add_argument("--skip-ref", action="store_true")
@@ -170,7 +182,7 @@ def main(argv=None):
     _lbm.load()
     res = {}
     if not args.skip_ref:
-        res["reference"] = reference_cavity(args.ref_n, args.ref_Ra, args.max_steps)
+        res["reference"] = reference_cavity(args.ref_n, args.ref_Ra, args.ref_max_steps)
         print(json.dumps({"reference": res["reference"]}), flush=True)
     if not args.skip_large:
         res["large"] = large_cavity(args.n, args.Ra, args.max_steps, args.fp64_seconds)
