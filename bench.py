@@ -163,12 +163,12 @@ def time_steps(sim, steps, stream):
     return start.elapsed_time(end) / 1e3
 
 
-def run_variant(lbm, q, steps, warmup, dist, device, clocks=None, precision=None):
+def run_variant(lbm, q, steps, warmup, dist, device, clocks=None, precision=None, n=N_GRID):
     import torch
-    n3 = N_GRID ** 3
+    n3 = n ** 3
     precision = lbm.FP32 if precision is None else precision
     stream = torch.cuda.current_stream(device)
-    sim = lbm.LBM((N_GRID,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=precision,
+    sim = lbm.LBM((n,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=precision,
                   residual_interval=RESIDUAL_INTERVAL)
     sim.step(warmup)
     torch.cuda.synchronize()
@@ -184,7 +184,7 @@ def run_variant(lbm, q, steps, warmup, dist, device, clocks=None, precision=None
     residual = sim.residual()
 
     # the step kernel alone (no residual launches) for the roofline
-    kern = lbm.LBM((N_GRID,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=precision,
+    kern = lbm.LBM((n,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=precision,
                    residual_interval=0)
     kern.step(max(10, warmup // 4))
     ksteps = max(50, min(steps, 2000))
@@ -465,12 +465,22 @@ def gpu_arm(args):
             sixteen[(name, q)] = (tname, run_variant(lbm, q, half_steps, args.warmup, dist, device,
                                                      None, precision=prec))
 
-    def roof(res, q, storage_bytes=4, tname="float", traffic=None):
+    # the same cavity at 256^3 (16.8 M nodes), FP32 and FP16, a short run of each
+    big_steps = max(1, min(1000, args.steps // 20))
+    big = {name: (tname, sb, run_variant(lbm, 15, big_steps, 20, dist, device, None,
+                                         precision=prec, n=2 * N_GRID))
+           for name, prec, tname, sb in (("FP32", lbm.FP32, "float", 4),
+                                         ("FP16_DEV", lbm.FP16_DEV, "__half", 2))}
+
+    def roof(res, q, storage_bytes=4, tname="float", traffic=None, n=N_GRID):
         bpn = bytes_per_node(q, storage_bytes)
-        achieved = bpn * N_GRID ** 3 / res["t_kernel"] / 1e9
+        achieved = bpn * n ** 3 / res["t_kernel"] / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_kind": peak_kind, "kernel": f"step_cavity_kernel<{tname},{q}>",
+                "peak_kind": peak_kind,
+                # the 16-bit forms take the two-node pair kernel when nx is even
+                "kernel": (f"step_pair_kernel<{tname},{q}>" if storage_bytes == 2 and n % 2 == 0
+                           else f"step_cavity_kernel<{tname},{q}>"),
                 "bytes_per_node": bpn, "kernel_ms": round(res["t_kernel"] * 1e3, 4)}
 
     total_lups = sum_over_ranks(dist, N_GRID ** 3 * args.steps, device)
@@ -511,6 +521,13 @@ def gpu_arm(args):
                 "ms_per_step": round(res["elapsed"] / half_steps * 1e3, 5),
                 "roofline": roof(res, q, 2, tname)}
                for (name, q), (tname, res) in sixteen.items()},
+            **{f"256^3 D3Q15+D3Q15 {name}": {
+                "value": round(sum_over_ranks(dist, (2 * N_GRID) ** 3 * big_steps, device)
+                               / res["elapsed"] / 1e6, 1),
+                "unit": "MLUPS", "steps": big_steps,
+                "ms_per_step": round(res["elapsed"] / big_steps * 1e3, 5),
+                "roofline": roof(res, 15, sb, tname, n=2 * N_GRID)}
+               for name, (tname, sb, res) in big.items()},
         },
         "state_after": {"steps": args.warmup + args.steps, "Nu_hot": main["nu"]["hot_wall_mean"],
                         "residual_per_100": main["residual"]},

@@ -49,12 +49,14 @@ __global__ void __launch_bounds__(128, (cavity_min_blocks<S, Q>()))
 // ---------------------------------------------------------------------------------
 constexpr int kPairThreads = 64;
 
-// Resident blocks per SM the pair kernel is built for (sets its register budget).
+// Resident blocks per SM the pair kernel is built for (sets its register budget: 128 for
+// 7 or 8 blocks of 64 threads).  Measured: 7-8 beat 5-6 (168-204 registers, fewer warps)
+// and 10 (96 registers, spills) at 128^3.
 #ifndef LBM_PAIR_MIN_BLOCKS_Q15
-#define LBM_PAIR_MIN_BLOCKS_Q15 8
+#define LBM_PAIR_MIN_BLOCKS_Q15 7
 #endif
 #ifndef LBM_PAIR_MIN_BLOCKS_Q7
-#define LBM_PAIR_MIN_BLOCKS_Q7 10
+#define LBM_PAIR_MIN_BLOCKS_Q7 8
 #endif
 template <int Q>
 constexpr int pair_min_blocks() { return Q == 15 ? LBM_PAIR_MIN_BLOCKS_Q15 : LBM_PAIR_MIN_BLOCKS_Q7; }
@@ -100,6 +102,8 @@ static PairParams make_pair_params(const DevParams<float>& p, int Q) {
     const float cp = p.cs2_phi;
     q.omg_tr = b(p.om_g[Q == 15 ? 9 : 6] * (3.0f * cp));
     q.omg_4 = b(p.om_g[14] * (cp * cp));
+    q.cs2 = b(cp);
+    q.cs4 = b(cp * cp);
     q.R = b(p.heat_source);
     q.halfR = b(0.5f * p.heat_source);
     q.gbeta = b(p.gbeta);

@@ -81,24 +81,22 @@ def test_16bit_checkpoint_roundtrip():
 
 @pytest.mark.timeout(600)
 def test_steady_nusselt_of_the_16bit_forms():
-    # 48^3, Ra = 1e4, to max |dT| per 100 steps < 1e-6 (or 150k steps): steady Nu of FP16
-    # within 0.5% of FP32; BF16 (8 significant bits) within 2%
-    import paper_1710_04751_gb300 as lbm
+    # 48^3, Ra = 1e4, every form from rest for 60 000 steps (FP32 is steady, max |dT| per
+    # 100 steps < 1e-6, from about 22 000 on; the 16-bit forms' max |dT| has a rounding
+    # floor above that and cannot signal their own convergence): steady Nu of FP16 within
+    # 0.5% of FP32; BF16 (8 significant bits) within 2%
+    from paper_1710_04751_gb300.precision import run_steps
     out = {}
     for name in ("FP32", "FP16_DEV", "BF16_DEV"):
-        sim = lbm.LBM((48, 48, 48), 15, Ra=1e4, Ma=0.05 * math.sqrt(3.0),
-                      precision=getattr(lbm, name))
-        while sim.steps_done < 150_000:
-            sim.step(2000)
-            r = sim.residual()
-            if 0 <= r < 1e-6:
-                break
-        out[name] = (sim.nusselt(), sim.steps_done, sim.residual())
-    ref = out["FP32"][0]
-    print({k: (v[0]["mid_mean"], v[0]["hot_wall_mean"], v[1], v[2]) for k, v in out.items()})
-    for k in ("mid_mean", "hot_wall_mean"):
-        assert out["FP16_DEV"][0][k] == pytest.approx(ref[k], rel=5e-3), k
-        assert out["BF16_DEV"][0][k] == pytest.approx(ref[k], rel=2e-2), k
+        sim, rec = run_steps(48, 1e4, name, 60_000)
+        sim.close()
+        out[name] = rec
+    print({k: (v["nu"]["mid_mean"], v["nu"]["hot_wall_mean"], v["residual_per_100"]) for k, v in out.items()})
+    assert 0 <= out["FP32"]["residual_per_100"] < 1e-6
+    ref = out["FP32"]["nu"]
+    for name, tol in (("FP16_DEV", 5e-3), ("BF16_DEV", 2e-2)):
+        for k in ("mid_mean", "hot_wall_mean"):
+            assert out[name]["nu"][k] == pytest.approx(ref[k], rel=tol), (name, k)
 
 
 # ------------------------------------------------------------------------------------
@@ -176,9 +174,8 @@ def test_pair_kernel_sampled_nodes_at_128(q):
 
 
 # ------------------------------------------------------------------------------------
-# The staged row kernel of the 16-bit forms (bulk copies into shared-memory stages): the
-# cavity with nx a multiple of 8 from 16 to 512.  Rows per grid large enough that every
-# block's ring of stages wraps around many times.
+# The pair kernel on long rows (nx up to 512: several 64-thread blocks per row) and on
+# grids of many short rows (thousands of blocks, most of them interior rows).
 # ------------------------------------------------------------------------------------
 
 ROWS_CASES = [
@@ -186,15 +183,15 @@ ROWS_CASES = [
     (16, 3, 3, 15, 1, 0, 0.0, False),    # one interior row
     (24, 5, 4, 7, 1, 1, 1e-3, True),
     (40, 6, 7, 15, 0, 0, -2e-3, True),
-    (16, 60, 40, 15, 1, 0, 0.0, False),  # 2400 rows: many rows per block
+    (16, 60, 40, 15, 1, 0, 0.0, False),  # 2400 rows
     (16, 48, 50, 7, 1, 0, 0.0, False),
-    (512, 3, 4, 15, 1, 1, 0.0, True),    # the widest staged row
+    (512, 3, 4, 15, 1, 1, 0.0, True),    # 256 pairs: four blocks per row
 ]
 
 
 @pytest.mark.parametrize("prec_name", ["FP16_DEV", "BF16_DEV"])
 @pytest.mark.parametrize("case", ROWS_CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}-q{c[3]}" for c in ROWS_CASES])
-def test_rows_kernel_steps_against_oracle(prec_name, case):
+def test_pair_kernel_long_and_many_rows(prec_name, case):
     import paper_1710_04751_gb300 as lbm
     p = _pair_problem(case, 1300 + case[1] + case[2])
     F, G = random_state(p, 70 + case[0])
