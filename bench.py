@@ -477,6 +477,7 @@ def gpu_arm(args):
         achieved = bpn * n ** 3 / res["t_kernel"] / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu)" if traffic is not None else None,
                 "peak_kind": peak_kind,
                 # the 16-bit forms take the two-node pair kernel when nx is even
                 "kernel": (f"step_pair_kernel<{tname},{q}>" if storage_bytes == 2 and n % 2 == 0
@@ -633,8 +634,11 @@ def main(argv=None):
                     help="also run the 64 cavities from rest to their own convergence (max steps)")
     ap.add_argument("--ref-budget", type=float, default=90.0,
                     help="seconds the reference arm spends on warm-up + timed steps")
-    ap.add_argument("--traffic-q15", type=float, default=None,
-                    help="ncu DRAM bytes per launch of the D3Q15 step kernel (reported as-is)")
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch of step_cavity_kernel<float,15>
+    # at 128^3 (ncu, profiles/step_cavity_kernel_q15_128cubed.md); to be retaken whenever
+    # that kernel changes
+    ap.add_argument("--traffic-q15", type=float, default=456.4e6,
+                    help="ncu DRAM bytes per launch of the FP32 D3Q15 step kernel at 128^3")
     ap.add_argument("--traffic-q7", type=float, default=None)
     args = ap.parse_args(argv)
     if args.impl == "reference":
