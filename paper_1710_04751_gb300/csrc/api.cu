@@ -450,8 +450,6 @@ static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const d
             CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dev.staging, gin + (int64_t)a * n, n * sizeof(double),
                                             cudaMemcpyHostToDevice, c->stream));
             CUDA_OR_FAIL(c, launch_accumulate_T(Tn, c->dev.staging, n, a == 0, c->stream));
-            int rc = wait_stream(c);
-            if (rc != LBM_OK) return rc;
         }
     }
     for (int side = 0; side < 2; ++side) {
@@ -473,17 +471,15 @@ static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const d
                 CUDA_OR_FAIL(c, cudaMemcpyAsync(dst, c->dev.staging, n * sizeof(double),
                                                 cudaMemcpyDeviceToHost, c->stream));
             }
-            // the staging plane is reused: finish this plane before the next one
-            int rc = wait_stream(c);
-            if (rc != LBM_OK) return rc;
+            // the staging plane is reused plane after plane: stream order keeps each copy
+            // behind the conversion that last used it, so no host wait is needed here
         }
     }
     if (upload) {
         CUDA_OR_FAIL(c, launch_residual<S>(c->dev, c->cur, p, 0, c->stream));
         c->last_residual = -1.0;
-        return wait_stream(c);
     }
-    return LBM_OK;
+    return wait_stream(c);  // the host arrays (download) or sources (upload) are done with
 }
 
 extern "C" int lbm_get_populations(lbm_ctx* c, double* f, double* g) {
