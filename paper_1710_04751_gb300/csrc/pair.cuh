@@ -530,6 +530,21 @@ __device__ __forceinline__ void pair_collide_store_lean(float2 (&f)[15], float2 
         *reinterpret_cast<two*>(Fout + a * P + c0) = Pk::from_float2(f[a]);
 }
 
+// The pair update after the pull: f holds the pulled flow deviations (f - w_a), g the pulled
+// scalar populations; the lean or the increment form per lattice (LBM_PAIR_LEAN_*).
+template <typename S, int Q>
+__device__ __forceinline__ void pair_finish(float2 (&f)[15], float2 (&g)[Q], S* __restrict__ Fout,
+                                            S* __restrict__ Gout, float* __restrict__ Tout,
+                                            const PairParams& q, int P, int c0) {
+    if constexpr (Q == 15 ? LBM_PAIR_LEAN_Q15 : LBM_PAIR_LEAN_Q7) {
+        pair_collide_store_lean<S, Q>(f, g, Fout, Gout, Tout, q, P, c0);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 15; ++a) f[a] = add2(f[a], q.wf[a]);
+        pair_collide_store<S, Q>(f, g, Fout, Gout, Tout, q, P, c0);
+    }
+}
+
 // ---------------------------------------------------------------------------------
 // The update of nodes c0 (i = 2t) and c0 + 1 of a row away from the y and z walls.
 // lo: i = 0 is the first node (its +x links come through the cold face); hi: i + 1 is
@@ -600,13 +615,7 @@ __device__ __forceinline__ void pair_node(const S* __restrict__ Fin, const S* __
             f[a] = make_float2(Pk::to_float(Fs[c0]), Pk::to_float(Fs[i1]));
         }
     }
-    if constexpr (Q == 15 ? LBM_PAIR_LEAN_Q15 : LBM_PAIR_LEAN_Q7) {
-        pair_collide_store_lean<S, Q>(f, g, Fout, Gout, Tout, q, P, c0);
-    } else {
-#pragma unroll
-        for (int a = 0; a < 15; ++a) f[a] = add2(f[a], q.wf[a]);
-        pair_collide_store<S, Q>(f, g, Fout, Gout, Tout, q, P, c0);
-    }
+    pair_finish<S, Q>(f, g, Fout, Gout, Tout, q, P, c0);
 }
 
 }  // namespace lbm
