@@ -126,3 +126,22 @@ def test_noalloc_nusselt_rejects_before_touching_the_device():
     rc = L.lbm_nusselt_noalloc(None, fake, 512, binding.FP32, ctypes.byref(small), 15,
                                ctypes.byref(p), None, ctypes.byref(nu))
     assert rc == binding.LBM_EINVAL
+
+
+def test_precision_study_error_measures():
+    # the host-side measures of the precision study: relative Nusselt / peak differences
+    # and max / RMS differences of the mid-plane fields (T in dT, |u| in U0)
+    import numpy as np
+    from paper_1710_04751_gb300 import precision
+    keys = precision.NU_KEYS
+    ref = {k: 2.0 for k in keys}
+    got = {k: 2.02 for k in keys}
+    err = precision.nu_errors(got, ref)
+    assert all(abs(err[k] - 0.01) < 1e-12 for k in keys)
+    a = {"T": np.zeros((4, 5)), "ux": np.zeros((4, 5)), "uy": np.zeros((4, 5)), "uz": np.zeros((4, 5))}
+    b = {k: v.copy() for k, v in a.items()}
+    b["T"][1, 2] = 0.3
+    b["ux"][0, 0], b["uz"][0, 0] = 3.0, 4.0
+    e = precision.plane_errors(a, b)
+    assert e["T_max"] == 0.3 and abs(e["T_rms"] - 0.3 / np.sqrt(20)) < 1e-15
+    assert e["u_max"] == 5.0 and abs(e["u_rms"] - 5.0 / np.sqrt(20)) < 1e-15
