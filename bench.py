@@ -256,6 +256,33 @@ def time_to_steady(lbm, q, max_steps, threshold=1e-6, chunk=1000):
             "w_max": nu["wmax"]}
 
 
+def time_to_steady_16bit(lbm, q, fp32, chunk=1000):
+    """The 16-bit storage forms on the same cavity and initial state, for the number of steps
+    the plain FP32 run needed (their max |dT| per 100 steps has a rounding floor above the
+    threshold, about 2e-5 in FP16 and 2e-4 in BF16, so they cannot end on it): wall seconds
+    against FP32's and their Nusselt numbers and peak velocities against FP32's."""
+    import torch
+    out = {}
+    keys = (("Nu_mean_mid", "mid_mean"), ("Nu_hot", "hot_wall_mean"), ("Nu_max", "mid_max"),
+            ("Nu_min", "mid_min"), ("u_max", "umax"), ("w_max", "wmax"))
+    for name in ("FP16_DEV", "BF16_DEV"):
+        sim = lbm.LBM((N_GRID,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0),
+                      precision=getattr(lbm, name), residual_interval=RESIDUAL_INTERVAL)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while sim.steps_done < fp32["steps"]:
+            sim.step(min(chunk, fp32["steps"] - sim.steps_done))
+            sim.residual()
+        dt = time.perf_counter() - t0
+        nu = sim.nusselt()
+        sim.close()
+        out[name] = {"steps": fp32["steps"], "seconds": round(dt, 2),
+                     "time_vs_fp32": round(dt / fp32["seconds"], 4),
+                     **{k: nu[src] for k, src in keys},
+                     "rel_diff_vs_fp32": {k: round((nu[src] - fp32[k]) / fp32[k], 5) for k, src in keys}}
+    return out
+
+
 def batch_variant(lbm, steps, warmup, peak, converge_steps=0):
     """The batched form: 64 cavities (edge 32/48/64/96, Ra log-uniform in [1e3, 1e6],
     Pr in {0.71, 1, 7}, seed 1), FP32, D3Q15 + D3Q15, one persistent kernel launch per
@@ -534,10 +561,14 @@ def gpu_arm(args):
                         "residual_per_100": main["residual"]},
     }
     if not args.no_steady:
+        tts15 = time_to_steady(lbm, 15, args.steady_max_steps)
         line["time_to_steady"] = {
-            "D3Q15+D3Q15": time_to_steady(lbm, 15, args.steady_max_steps),
+            "D3Q15+D3Q15": tts15,
             "D3Q15+D3Q7": time_to_steady(lbm, 7, args.steady_max_steps),
         }
+        if tts15["converged"]:
+            line["time_to_steady"]["D3Q15+D3Q15 16-bit, FP32's step count"] = \
+                time_to_steady_16bit(lbm, 15, tts15)
     if not args.no_batch:
         line["batch"] = batch_variant(lbm, args.batch_steps, RESIDUAL_INTERVAL, peak,
                                       args.batch_converge_steps)
