@@ -186,6 +186,24 @@ int lbm_set_fields(lbm_ctx* ctx, const double* rho, const double* ux, const doub
 int lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
                     const double* uz, const double* T, int iterations);
 
+/* Checkpoints (the paper has none; a restartable run needs one).  lbm_save writes to the
+ * file at `path`: a header (magic "LBMCKPT1", version 1, the grid, the scalar lattice, the
+ * storage precision, the model parameters as lbm_params, the step count), then the 15
+ * flow and the Q scalar populations as FP64 in the layout of lbm_get_populations
+ * (little-endian; the host's byte order, as both build hosts are).  The file is written
+ * completely or the call fails (LBM_EINVAL: cannot open or write; the partial file is
+ * removed).  lbm_checkpoint_info reads a file's header, so that a caller can create the
+ * matching context (lbm_create_params with the returned grid, lattice, parameters and
+ * precision); lbm_restore then loads the populations and the step count into such a
+ * context (LBM_EINVAL if its grid, lattice or precision differ, or the file is short or
+ * not a checkpoint).  Restoring into the same precision is exact for FP64 and FP32; the
+ * 16-bit forms re-encode each deviation once (within one 16-bit rounding).  Any pointer
+ * of lbm_checkpoint_info may be NULL. */
+int lbm_save(lbm_ctx* ctx, const char* path);
+int lbm_checkpoint_info(const char* path, lbm_grid* grid, int* lattice, int* precision,
+                        lbm_params* params, int64_t* steps);
+int lbm_restore(lbm_ctx* ctx, const char* path);
+
 /* Parameters in use, step counter, last error message, stream wait, destruction. */
 int lbm_get_params(const lbm_ctx* ctx, lbm_params* out);
 int64_t lbm_steps_done(const lbm_ctx* ctx);

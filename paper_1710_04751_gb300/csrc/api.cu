@@ -1,6 +1,7 @@
 // api.cu -- the C ABI declared in include/lbm.h: context life cycle, parameter
 // derivation (Sec. 3 of arXiv:1710.04751), the time-step loop and host transfers.
 #include <math.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -358,6 +359,7 @@ static int run_steps(lbm_ctx* c, int64_t n, bool* checked) {
 }
 
 extern "C" int lbm_step(lbm_ctx* c, int64_t n) {
+    NvtxRange nvtx("lbm_step");
     if (!c || n < 0) return fail(c, LBM_EINVAL, "invalid context or step count%s");
     if (c->owner) return fail(c, LBM_EINVAL, "a batch member is advanced by lbm_batch_step%s");
     DeviceGuard g(c->device);
@@ -395,6 +397,7 @@ static int run_fields(lbm_ctx* c, double* const* outs) {
 }
 
 extern "C" int lbm_fields(lbm_ctx* c, double* rho, double* ux, double* uy, double* uz, double* T) {
+    NvtxRange nvtx("lbm_fields");
     if (!c) return fail(c, LBM_EINVAL, "NULL context%s");
     DeviceGuard g(c->device);
     double* outs[5] = {rho, ux, uy, uz, T};
@@ -402,6 +405,7 @@ extern "C" int lbm_fields(lbm_ctx* c, double* rho, double* ux, double* uy, doubl
 }
 
 extern "C" int lbm_nusselt(lbm_ctx* c, lbm_nu* out) {
+    NvtxRange nvtx("lbm_nusselt");
     if (!c || !out) return fail(c, LBM_EINVAL, "NULL argument%s");
     if (c->grid.nx < 2) return fail(c, LBM_EINVAL, "lbm_nusselt needs nx >= 2%s");
     DeviceGuard g(c->device);
@@ -483,6 +487,7 @@ static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const d
 }
 
 extern "C" int lbm_get_populations(lbm_ctx* c, double* f, double* g) {
+    NvtxRange nvtx("lbm_get_populations");
     if (!c || !f || !g) return fail(c, LBM_EINVAL, "NULL argument%s");
     DeviceGuard gd(c->device);
     return with_storage(c->precision, [&](auto tag) {
@@ -491,6 +496,7 @@ extern "C" int lbm_get_populations(lbm_ctx* c, double* f, double* g) {
 }
 
 extern "C" int lbm_set_populations(lbm_ctx* c, const double* f, const double* g) {
+    NvtxRange nvtx("lbm_set_populations");
     if (!c || !f || !g) return fail(c, LBM_EINVAL, "NULL argument%s");
     DeviceGuard gd(c->device);
     return with_storage(c->precision, [&](auto tag) {
@@ -524,6 +530,112 @@ extern "C" int lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, 
     if (rc != LBM_OK) return rc;
     c->last_residual = -1.0;
     return wait_stream(c);
+}
+
+// ---------------------------------------------------------------------------------
+// Checkpoint files: header, then FP64 populations (flow planes, then scalar planes).
+// ---------------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];       // "LBMCKPT1"
+    uint32_t version;    // 1
+    int32_t lattice;     // Q of the scalar populations
+    int32_t precision;   // LBM_FP64 ... LBM_BF16_DEV
+    int32_t grid[3];
+    int64_t steps;
+    lbm_params params;
+};
+const char kCkptMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+
+bool read_header(FILE* fp, CkptHeader* h) {
+    return fread(h, sizeof *h, 1, fp) == 1 && memcmp(h->magic, kCkptMagic, 8) == 0 && h->version == 1 &&
+           (h->lattice == 15 || h->lattice == 7) && h->grid[0] > 0 && h->grid[1] > 0 && h->grid[2] > 0;
+}
+}  // namespace
+
+extern "C" int lbm_save(lbm_ctx* c, const char* path) {
+    NvtxRange nvtx("lbm_save");
+    if (!c || !path) return fail(c, LBM_EINVAL, "NULL argument%s");
+    const int64_t nf = 15 * c->ncell, ng = (int64_t)c->Q * c->ncell;
+    double* f = static_cast<double*>(malloc((size_t)(nf + ng) * sizeof(double)));
+    if (!f) return fail(c, LBM_ENOMEM, "no host memory for the checkpoint%s");
+    double* g = f + nf;
+    int rc = lbm_get_populations(c, f, g);
+    if (rc != LBM_OK) {
+        free(f);
+        return rc;
+    }
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.lattice = c->Q;
+    h.precision = c->precision;
+    h.grid[0] = c->grid.nx;
+    h.grid[1] = c->grid.ny;
+    h.grid[2] = c->grid.nz;
+    h.steps = c->steps;
+    h.params = c->params;
+    FILE* fp = fopen(path, "wb");
+    bool ok = fp && fwrite(&h, sizeof h, 1, fp) == 1 &&
+              fwrite(f, sizeof(double), (size_t)(nf + ng), fp) == (size_t)(nf + ng);
+    if (fp && fclose(fp) != 0) ok = false;
+    free(f);
+    if (!ok) {
+        remove(path);
+        return fail(c, LBM_EINVAL, "cannot write the checkpoint file%s");
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_checkpoint_info(const char* path, lbm_grid* grid, int* lattice, int* precision,
+                                   lbm_params* params, int64_t* steps) {
+    if (!path) return fail(nullptr, LBM_EINVAL, "NULL path%s");
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return fail(nullptr, LBM_EINVAL, "cannot open the checkpoint file%s");
+    CkptHeader h;
+    const bool ok = read_header(fp, &h);
+    fclose(fp);
+    if (!ok) return fail(nullptr, LBM_EINVAL, "not a checkpoint file%s");
+    if (grid) *grid = lbm_grid{h.grid[0], h.grid[1], h.grid[2]};
+    if (lattice) *lattice = h.lattice;
+    if (precision) *precision = h.precision;
+    if (params) *params = h.params;
+    if (steps) *steps = h.steps;
+    return LBM_OK;
+}
+
+extern "C" int lbm_restore(lbm_ctx* c, const char* path) {
+    NvtxRange nvtx("lbm_restore");
+    if (!c || !path) return fail(c, LBM_EINVAL, "NULL argument%s");
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return fail(c, LBM_EINVAL, "cannot open the checkpoint file%s");
+    CkptHeader h;
+    if (!read_header(fp, &h)) {
+        fclose(fp);
+        return fail(c, LBM_EINVAL, "not a checkpoint file%s");
+    }
+    if (h.grid[0] != c->grid.nx || h.grid[1] != c->grid.ny || h.grid[2] != c->grid.nz ||
+        h.lattice != c->Q || h.precision != c->precision) {
+        fclose(fp);
+        return fail(c, LBM_EINVAL, "the checkpoint's grid, lattice or precision differ from the context's%s");
+    }
+    const int64_t nf = 15 * c->ncell, ng = (int64_t)c->Q * c->ncell;
+    double* f = static_cast<double*>(malloc((size_t)(nf + ng) * sizeof(double)));
+    if (!f) {
+        fclose(fp);
+        return fail(c, LBM_ENOMEM, "no host memory for the checkpoint%s");
+    }
+    const bool ok = fread(f, sizeof(double), (size_t)(nf + ng), fp) == (size_t)(nf + ng);
+    fclose(fp);
+    if (!ok) {
+        free(f);
+        return fail(c, LBM_EINVAL, "the checkpoint file is short%s");
+    }
+    const int rc = lbm_set_populations(c, f, f + nf);
+    free(f);
+    if (rc == LBM_OK) c->steps = h.steps;
+    return rc;
 }
 
 extern "C" int lbm_get_params(const lbm_ctx* c, lbm_params* out) {

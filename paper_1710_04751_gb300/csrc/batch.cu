@@ -745,6 +745,7 @@ extern "C" int lbm_batch_create(int count, const lbm_grid* grids, int lattice,
 }
 
 extern "C" int lbm_batch_step_with(lbm_batch* b, int64_t n, int mode) {
+    NvtxRange nvtx("lbm_batch_step");
     if (!b || n < 0 || mode < LBM_BATCH_GRAPH || mode > LBM_BATCH_SEQUENTIAL)
         return bfail(b, LBM_EINVAL, "invalid batch, step count or mode%s");
     DeviceGuard g(b->device);

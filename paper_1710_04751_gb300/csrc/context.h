@@ -11,6 +11,24 @@
 #include "internal.h"
 #include "lbm.h"
 
+// NVTX ranges around the C ABI's calls (header-only NVTX 3: no cost without a tool attached;
+// build with -DLBM_NO_NVTX to leave them out).
+#ifndef LBM_NO_NVTX
+#include <nvtx3/nvToolsExt.h>
+#endif
+namespace lbm {
+struct NvtxRange {
+#ifndef LBM_NO_NVTX
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+#else
+    explicit NvtxRange(const char*) {}
+#endif
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace lbm
+
 struct lbm_batch;
 
 struct lbm_ctx {

@@ -25,7 +25,7 @@ EXPORTS = (
     "lbm_create_params", "lbm_step", "lbm_fields", "lbm_nusselt", "lbm_residual",
     "lbm_get_populations", "lbm_set_populations", "lbm_get_params", "lbm_steps_done",
     "lbm_last_error", "lbm_synchronize", "lbm_destroy", "lbm_nusselt_noalloc", "lbm_set_fields",
-    "lbm_init_fields",
+    "lbm_init_fields", "lbm_save", "lbm_checkpoint_info", "lbm_restore",
 )
 
 
@@ -119,6 +119,10 @@ def load(build_if_missing=True):
     L.lbm_synchronize.argtypes = [ctypes.c_void_p]
     L.lbm_destroy.argtypes = [ctypes.c_void_p]
     L.lbm_destroy.restype = None
+    L.lbm_save.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+    L.lbm_checkpoint_info.argtypes = [ctypes.c_char_p, P(Grid), P(ctypes.c_int), P(ctypes.c_int),
+                                      P(Params), P(ctypes.c_int64)]
+    L.lbm_restore.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
     L.lbm_nusselt_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                       ctypes.c_int, P(Grid), ctypes.c_int, P(Params),
                                       ctypes.c_void_p, P(Nu)]
@@ -145,6 +149,19 @@ def derive_params(grid, lattice, Ra, Pr, Ma, **opts):
     if rc != LBM_OK:
         raise LBMError(rc, L.lbm_last_error(None).decode())
     return p
+
+
+def checkpoint_info(path):
+    """The header of a checkpoint file written by LBM.save: grid, lattice, precision,
+    parameters (a dict, as LBM.params()) and step count."""
+    L = load()
+    g, lat, prec, p, steps = Grid(), ctypes.c_int(), ctypes.c_int(), Params(), ctypes.c_int64()
+    rc = L.lbm_checkpoint_info(os.fsencode(path), ctypes.byref(g), ctypes.byref(lat), ctypes.byref(prec),
+                               ctypes.byref(p), ctypes.byref(steps))
+    if rc != LBM_OK:
+        raise LBMError(rc, L.lbm_last_error(None).decode())
+    return dict(grid=(g.nx, g.ny, g.nz), lattice=lat.value, precision=prec.value,
+                params=p.as_dict(), steps=steps.value)
 
 
 def arena_bytes(grid, lattice, precision):
@@ -290,6 +307,24 @@ class LBM:
                 raise ValueError("fields must be contiguous CUDA float64 tensors of ncell values")
         ptr = [ctypes.c_void_p(a.data_ptr()) if a is not None else None for a in arrs]
         self._check(self._L.lbm_init_fields(self._ctx, *ptr, int(iterations)))
+
+    def save(self, path):
+        """Write the state, parameters and step count to a checkpoint file (lbm_save)."""
+        self._check(self._L.lbm_save(self._ctx, os.fsencode(path)))
+
+    def restore(self, path):
+        """Load the populations and step count of a checkpoint file of the same grid,
+        lattice and precision (lbm_restore)."""
+        self._check(self._L.lbm_restore(self._ctx, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path, **kw):
+        """A context created from a checkpoint file: its grid, lattice, precision and
+        parameters, then its populations and step count.  kw: further LBM options."""
+        info = checkpoint_info(path)
+        sim = cls(info["grid"], info["lattice"], params=info["params"], precision=info["precision"], **kw)
+        sim.restore(path)
+        return sim
 
     def params(self):
         return self.params_struct().as_dict()

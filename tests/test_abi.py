@@ -145,3 +145,25 @@ def test_precision_study_error_measures():
     e = precision.plane_errors(a, b)
     assert e["T_max"] == 0.3 and abs(e["T_rms"] - 0.3 / np.sqrt(20)) < 1e-15
     assert e["u_max"] == 5.0 and abs(e["u_rms"] - 5.0 / np.sqrt(20)) < 1e-15
+
+
+def test_checkpoint_header_layout(tmp_path):
+    # lbm_checkpoint_info reads the header layout include/lbm.h documents: magic, version 1,
+    # lattice, precision, grid, step count, lbm_params; anything else is rejected
+    import struct
+    p = binding.derive_params((12, 10, 8), 7, 1e4, 0.71, 0.05 * math.sqrt(3.0))
+    head = b"LBMCKPT1" + struct.pack("<Iii3iq", 1, 7, binding.FP32, 12, 10, 8, 12345) + bytes(p)
+    path = tmp_path / "c.ckpt"
+    path.write_bytes(head + b"\0" * 64)
+    info = binding.checkpoint_info(str(path))
+    assert info["grid"] == (12, 10, 8) and info["lattice"] == 7 and info["precision"] == binding.FP32
+    assert info["steps"] == 12345
+    assert info["params"] == p.as_dict()
+    bad = tmp_path / "bad.ckpt"
+    for data in (b"LBMCKPT2" + head[8:], head[:20], b""):
+        bad.write_bytes(data)
+        with pytest.raises(lbm.LBMError) as e:
+            binding.checkpoint_info(str(bad))
+        assert e.value.code == binding.LBM_EINVAL
+    with pytest.raises(lbm.LBMError):
+        binding.checkpoint_info(str(tmp_path / "missing.ckpt"))

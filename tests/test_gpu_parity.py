@@ -332,3 +332,32 @@ def test_library_owned_arena_and_default_stream():
     fa, ga = a.get_populations()
     fb, gb = b.get_populations()
     assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+@pytest.mark.parametrize("precision", ["FP32", "FP64", "FP16_DEV"])
+def test_checkpoint_file_restart(precision, tmp_path):
+    # 200 steps straight against 100 steps, lbm_save, LBM.load (lbm_checkpoint_info +
+    # lbm_create_params + lbm_restore) and 100 more: bitwise in FP32 and FP64; the 16-bit
+    # form re-encodes each deviation once on restore, so it is compared through Nu
+    lbm = lbm_mod()
+    prec = getattr(lbm, precision)
+    a = lbm.LBM((16, 12, 10), 15, Ra=1e4, precision=prec)
+    a.step(200)
+    b = lbm.LBM((16, 12, 10), 15, Ra=1e4, precision=prec)
+    b.step(100)
+    path = str(tmp_path / "state.ckpt")
+    b.save(path)
+    c = lbm.LBM.load(path)
+    assert c.steps_done == 100 and c.precision == prec and c.params() == b.params()
+    c.step(100)
+    assert c.steps_done == 200
+    fa, ga = a.get_populations()
+    fc, gc = c.get_populations()
+    if prec in (lbm.FP32, lbm.FP64):
+        assert np.array_equal(fa, fc) and np.array_equal(ga, gc)
+    else:
+        assert c.nusselt()["hot_wall_mean"] == pytest.approx(a.nusselt()["hot_wall_mean"], rel=1e-3)
+    other = lbm.LBM((16, 12, 12), 15, Ra=1e4, precision=prec)
+    with pytest.raises(lbm.LBMError) as e:
+        other.restore(path)
+    assert e.value.code == lbm.lbm.LBM_EINVAL
