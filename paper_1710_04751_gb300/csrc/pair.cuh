@@ -5,9 +5,10 @@
 //
 // It computes what node.cuh computes for each of the two nodes -- pull (Eqs. 2b, 13b)
 // with the x-face rules of Sec. 3, T (Eq. 25), the Boussinesq force, u (Eq. 3), the flow
-// collision of App. A and the scalar collision of Sec. 2.2 / App. C as central-moment
-// increments (collide.cuh), the store of both populations' deviations -- with about half
-// the instructions per node: every floating-point operation covers two nodes, the
+// collision of App. A and the scalar collision of Sec. 2.2 / App. C in central moments
+// (collide.cuh's increments, or the lean form below), the store of both populations'
+// deviations -- with about 40% fewer instructions per node (713 against ~1150 measured for
+// the one-node 16-bit update): every floating-point operation covers two nodes, the
 // populations of the x-aligned links (e_x = 0) and every store move two 16-bit values in
 // one 32-bit access, and the node temperatures of a source row come as one aligned
 // float2 plus the two x-neighbours.  Lane .x is node i = 2t, lane .y is node 2t + 1.
@@ -26,8 +27,8 @@
 
 // Which form of the two-node update each scalar lattice uses: the lean form (moments of
 // the deviations, pair_collide_store_lean) or the increment form (pair_collide_store).
-// Measured at 128^3 and 256^3: lean is faster for D3Q15 (0.0818 / 0.504 ms against 0.0863 /
-// 0.540 ms per step), the increment form for D3Q7 (0.0533 against 0.0552 ms).
+// Measured at 128^3 and 256^3 (FP16): lean is faster for D3Q15 (0.0825 / 0.511 ms against
+// 0.0863 / 0.540 ms per step), the increment form for D3Q7 (0.0533 against 0.0552 ms).
 #ifndef LBM_PAIR_LEAN_Q15
 #define LBM_PAIR_LEAN_Q15 1
 #endif
