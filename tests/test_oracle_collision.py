@@ -25,7 +25,7 @@ def _states(n, seed):
 
 @pytest.mark.parametrize("e4_mode", [0, 1])
 def test_flow_form_a_equals_form_b(e4_mode):
-    f, F, om = _states(400, 11)
+    f, F, om = _states(2500, 11)
     worst = 0.0
     for i in range(len(f)):
         a, rho_a, u_a = oracle.collide_flow(f[i], F[i], om[i], e4_mode)
@@ -55,12 +55,13 @@ def test_flow_source_form_a_equals_form_b_and_moments():
 @pytest.mark.parametrize("cs2", [1.0 / 3.0, 0.25])
 @pytest.mark.parametrize("R", [0.0, 3e-3])
 def test_thermal_form_a_equals_form_b(q, cs2, R):
-    rng_g = inputs.perturbed_populations(np.ones(q) * 0.05, (300,), 21, rel=1.0).T
-    T = inputs.uniform_field((300,), 22, -0.5, 0.5)
-    U = inputs.random_vectors(300, 23, 0.1)
+    n = 650  # with the flow test's 2 x 2500: about 1e4 random cell states in all
+    rng_g = inputs.perturbed_populations(np.ones(q) * 0.05, (n,), 21, rel=1.0).T
+    T = inputs.uniform_field((n,), 22, -0.5, 0.5)
+    U = inputs.random_vectors(n, 23, 0.1)
     w = oracle.weights_thermal(q, cs2)
     worst = 0.0
-    for i in range(300):
+    for i in range(n):
         g = w * T[i] + rng_g[i]
         om = inputs.random_rates(q, 100 + i)
         a = oracle.collide_thermal(g, U[i], om, cs2, R * (1 + T[i]))
