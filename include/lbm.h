@@ -165,6 +165,15 @@ int lbm_residual(lbm_ctx* ctx, double* max_dT);
 int lbm_get_populations(lbm_ctx* ctx, double* f, double* g);
 int lbm_set_populations(lbm_ctx* ctx, const double* f, const double* g);
 
+/* The same in the context's own storage precision, for LBM_FP32 (float arrays) and
+ * LBM_FP64 (double arrays) contexts: each population plane goes straight between the
+ * caller's host array and the device state, with no conversion pass (half the bytes of the
+ * FP64 calls for an FP32 context).  Same layout, ownership and residual-snapshot restart as
+ * above; page-locked host arrays make the copies fastest.  LBM_EINVAL for the 16-bit forms,
+ * whose stored values are deviations that need their node temperatures. */
+int lbm_get_populations_native(lbm_ctx* ctx, void* f, void* g);
+int lbm_set_populations_native(lbm_ctx* ctx, const void* f, const void* g);
+
 /* Set the stored populations to the equilibria of given fields: f to the populations
  * whose central moments are the flow collision's equilibria at (rho, u) (App. A:
  * Maxwellian, c_s^2 = 1/3), g to those whose central moments are the equilibria of

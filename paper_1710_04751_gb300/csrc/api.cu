@@ -504,6 +504,55 @@ extern "C" int lbm_set_populations(lbm_ctx* c, const double* f, const double* g)
     });
 }
 
+// Native-precision transfers: one copy per population plane between the host array and
+// the state buffer (FP32 and FP64 contexts).
+static int transfer_native(lbm_ctx* c, void* f, void* g, const void* fin, const void* gin) {
+    if (c->precision != LBM_FP32 && c->precision != LBM_FP64)
+        return fail(c, LBM_EINVAL, "native transfers need an FP32 or FP64 context%s");
+    const bool upload = fin || gin;
+    const size_t es = c->precision == LBM_FP64 ? 8 : 4;
+    const size_t bytes = (size_t)c->ncell * es;
+    for (int side = 0; side < 2; ++side) {
+        const int q = side == 0 ? 15 : c->Q;
+        char* dev = static_cast<char*>(side == 0 ? c->dev.F[c->cur] : c->dev.G[c->cur]);
+        for (int a = 0; a < q; ++a) {
+            char* plane = dev + (size_t)a * c->plane * es;
+            if (upload) {
+                const char* src = static_cast<const char*>(side == 0 ? fin : gin) + (size_t)a * bytes;
+                CUDA_OR_FAIL(c, cudaMemcpyAsync(plane, src, bytes, cudaMemcpyHostToDevice, c->stream));
+            } else {
+                char* dst = static_cast<char*>(side == 0 ? f : g) + (size_t)a * bytes;
+                CUDA_OR_FAIL(c, cudaMemcpyAsync(dst, plane, bytes, cudaMemcpyDeviceToHost, c->stream));
+            }
+        }
+    }
+    if (upload) {
+        int rc = with_storage(c->precision, [&](auto tag) {
+            using S = decltype(tag);
+            CUDA_OR_FAIL(c, launch_residual<S>(c->dev, c->cur, dev_params<typename Storage<S>::real>(c), 0,
+                                               c->stream));
+            return LBM_OK;
+        });
+        if (rc != LBM_OK) return rc;
+        c->last_residual = -1.0;
+    }
+    return wait_stream(c);
+}
+
+extern "C" int lbm_get_populations_native(lbm_ctx* c, void* f, void* g) {
+    NvtxRange nvtx("lbm_get_populations_native");
+    if (!c || !f || !g) return fail(c, LBM_EINVAL, "NULL argument%s");
+    DeviceGuard gd(c->device);
+    return transfer_native(c, f, g, nullptr, nullptr);
+}
+
+extern "C" int lbm_set_populations_native(lbm_ctx* c, const void* f, const void* g) {
+    NvtxRange nvtx("lbm_set_populations_native");
+    if (!c || !f || !g) return fail(c, LBM_EINVAL, "NULL argument%s");
+    DeviceGuard gd(c->device);
+    return transfer_native(c, nullptr, nullptr, f, g);
+}
+
 extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* ux, const double* uy,
                               const double* uz, const double* T) {
     return lbm_init_fields(c, rho, ux, uy, uz, T, 0);

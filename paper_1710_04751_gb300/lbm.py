@@ -26,6 +26,7 @@ EXPORTS = (
     "lbm_get_populations", "lbm_set_populations", "lbm_get_params", "lbm_steps_done",
     "lbm_last_error", "lbm_synchronize", "lbm_destroy", "lbm_nusselt_noalloc", "lbm_set_fields",
     "lbm_init_fields", "lbm_save", "lbm_checkpoint_info", "lbm_restore",
+    "lbm_get_populations_native", "lbm_set_populations_native",
 )
 
 
@@ -119,6 +120,8 @@ def load(build_if_missing=True):
     L.lbm_synchronize.argtypes = [ctypes.c_void_p]
     L.lbm_destroy.argtypes = [ctypes.c_void_p]
     L.lbm_destroy.restype = None
+    L.lbm_get_populations_native.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.lbm_set_populations_native.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.lbm_save.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
     L.lbm_checkpoint_info.argtypes = [ctypes.c_char_p, P(Grid), P(ctypes.c_int), P(ctypes.c_int),
                                       P(Params), P(ctypes.c_int64)]
@@ -294,6 +297,32 @@ class LBM:
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(15, nz, ny, nx)
         g = np.ascontiguousarray(g, dtype=np.float64).reshape(self.lattice, nz, ny, nx)
         self._check(self._L.lbm_set_populations(self._ctx, _dp(f), _dp(g)))
+
+    def _native_dtype(self):
+        if self.precision not in (FP32, FP64):
+            raise LBMError(LBM_EINVAL, "native transfers need an FP32 or FP64 context")
+        return np.float32 if self.precision == FP32 else np.float64
+
+    def get_populations_native(self, f=None, g=None):
+        """The stored populations in the context's own precision (FP32 or FP64 contexts);
+        f, g: optional preallocated C-contiguous arrays (e.g. page-locked) to fill."""
+        nx, ny, nz = self.grid
+        dt = self._native_dtype()
+        f = np.empty((15, nz, ny, nx), dtype=dt) if f is None else f
+        g = np.empty((self.lattice, nz, ny, nx), dtype=dt) if g is None else g
+        for a, rows in ((f, 15), (g, self.lattice)):
+            if a.dtype != dt or not a.flags.c_contiguous or a.size != rows * nx * ny * nz:
+                raise ValueError("arrays must be C-contiguous, of the context's dtype and size")
+        self._check(self._L.lbm_get_populations_native(self._ctx, f.ctypes.data, g.ctypes.data))
+        return f, g
+
+    def set_populations_native(self, f, g):
+        """Upload populations in the context's own precision (no conversion pass)."""
+        nx, ny, nz = self.grid
+        dt = self._native_dtype()
+        f = np.ascontiguousarray(f, dtype=dt).reshape(15, nz, ny, nx)
+        g = np.ascontiguousarray(g, dtype=dt).reshape(self.lattice, nz, ny, nx)
+        self._check(self._L.lbm_set_populations_native(self._ctx, f.ctypes.data, g.ctypes.data))
 
     def set_fields(self, ux, uy, uz, T, rho=None, iterations=0):
         """Populations at the equilibria of the fields: torch CUDA float64 tensors of

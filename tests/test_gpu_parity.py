@@ -361,3 +361,32 @@ def test_checkpoint_file_restart(precision, tmp_path):
     with pytest.raises(lbm.LBMError) as e:
         other.restore(path)
     assert e.value.code == lbm.lbm.LBM_EINVAL
+
+
+@pytest.mark.parametrize("precision", ["FP32", "FP64"])
+def test_native_precision_transfers(precision):
+    # lbm_get/set_populations_native move the stored values themselves: round trips are
+    # exact, and a step after a native upload equals a step after the FP64 upload of the
+    # same values, bitwise; the 16-bit forms refuse them
+    lbm = lbm_mod()
+    prec = getattr(lbm, precision)
+    dt = np.float32 if prec == lbm.FP32 else np.float64
+    p = _case_problem((20, 9, 7, 15, oracle.BC_CAVITY, 1, 0), 77)
+    F, G = random_state(p, 78)
+    a = gpu_for(p, prec)
+    a.set_populations(F, G)
+    fn, gn = a.get_populations_native()
+    assert fn.dtype == dt and np.array_equal(fn, F.astype(dt)) and np.array_equal(gn, G.astype(dt))
+    b = gpu_for(p, prec)
+    b.set_populations_native(fn, gn)
+    fb, gb = b.get_populations()
+    fa, ga = a.get_populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    a.step(3)
+    b.step(3)
+    assert np.array_equal(a.get_populations()[0], b.get_populations()[0])
+    assert np.array_equal(a.get_populations()[1], b.get_populations()[1])
+    h = gpu_for(p, lbm.FP16_DEV)
+    with pytest.raises(lbm.LBMError) as e:
+        h.get_populations_native()
+    assert e.value.code == lbm.lbm.LBM_EINVAL
