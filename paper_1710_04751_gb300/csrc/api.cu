@@ -341,19 +341,71 @@ extern "C" int lbm_create(const lbm_grid* grid, int lattice, double Ra, double P
     return lbm_create_params(grid, lattice, &p, opt, out);
 }
 
+// One step (and, when the step count reaches a multiple of the residual interval, the
+// residual check) launched on stream `st` from buffer `cur`.
+template <typename S>
+static cudaError_t enqueue_step(lbm_ctx* c, const ParamsOf<S>& p, int cur, int64_t steps_after,
+                                cudaStream_t st) {
+    cudaError_t e = launch_step<S>(c->dev, cur, p, st);
+    const int R = c->opt.residual_interval;
+    if (e == cudaSuccess && R > 0 && steps_after % R == 0) {
+        e = cudaMemsetAsync(c->dev.resid_bits, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = launch_residual<S>(c->dev, cur ^ 1, p, 1, st);
+    }
+    return e;
+}
+
+// The graph of residual_interval steps starting from buffer `cur` (captured on first use;
+// NULL when capture is not possible, and then never tried again for this context).
+#ifndef LBM_STEP_GRAPHS
+#define LBM_STEP_GRAPHS 1
+#endif
+template <typename S>
+static cudaGraphExec_t step_graph(lbm_ctx* c, const ParamsOf<S>& p, int cur) {
+    if (!LBM_STEP_GRAPHS || c->graphs_failed) return nullptr;
+    if (c->step_graph[cur]) return c->step_graph[cur];
+    const int R = c->opt.residual_interval;
+    bool ok = c->capture || cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) == cudaSuccess;
+    cudaGraph_t g = nullptr;
+    if (ok) ok = cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        int b = cur;
+        cudaError_t e = cudaSuccess;
+        for (int i = 1; i <= R && e == cudaSuccess; ++i, b ^= 1) e = enqueue_step<S>(c, p, b, i, c->capture);
+        const cudaError_t e2 = cudaStreamEndCapture(c->capture, &g);
+        ok = e == cudaSuccess && e2 == cudaSuccess && g;
+    }
+    if (ok) ok = cudaGraphInstantiate(&c->step_graph[cur], g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        c->step_graph[cur] = nullptr;
+        c->graphs_failed = true;
+        cudaGetLastError();  // a failed capture leaves no error behind for the next launch
+    }
+    return c->step_graph[cur];
+}
+
 template <typename S>
 static int run_steps(lbm_ctx* c, int64_t n, bool* checked) {
     const ParamsOf<S> p = dev_params<typename Storage<S>::real>(c);
     const int R = c->opt.residual_interval;
-    for (int64_t s = 0; s < n; ++s) {
-        CUDA_OR_FAIL(c, launch_step<S>(c->dev, c->cur, p, c->stream));
+    for (int64_t s = 0; s < n;) {
+        // whole residual intervals, aligned with the step count, go as one graph launch
+        if (R > 0 && c->steps % R == 0 && n - s >= R) {
+            if (cudaGraphExec_t g = step_graph<S>(c, p, c->cur)) {
+                CUDA_OR_FAIL(c, cudaGraphLaunch(g, c->stream));
+                if (R & 1) c->cur ^= 1;
+                c->steps += R;
+                s += R;
+                *checked = true;
+                continue;
+            }
+        }
+        CUDA_OR_FAIL(c, enqueue_step<S>(c, p, c->cur, c->steps + 1, c->stream));
         c->cur ^= 1;
         c->steps += 1;
-        if (R > 0 && c->steps % R == 0) {
-            CUDA_OR_FAIL(c, cudaMemsetAsync(c->dev.resid_bits, 0, sizeof(unsigned long long), c->stream));
-            CUDA_OR_FAIL(c, launch_residual<S>(c->dev, c->cur, p, 1, c->stream));
-            *checked = true;
-        }
+        s += 1;
+        if (R > 0 && c->steps % R == 0) *checked = true;
     }
     return LBM_OK;
 }
@@ -714,6 +766,9 @@ void lbm::destroy_context(lbm_ctx* c) {
     {
         DeviceGuard g(c->device);
         wait_stream(c);
+        for (cudaGraphExec_t& g : c->step_graph)
+            if (g) cudaGraphExecDestroy(g);
+        if (c->capture) cudaStreamDestroy(c->capture);
         if (c->own_arena && c->arena) cudaFree(c->arena);
         if (c->host_bits) cudaFreeHost(c->host_bits);
     }

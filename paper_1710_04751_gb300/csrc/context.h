@@ -51,6 +51,11 @@ struct lbm_ctx {
     unsigned long long* host_bits;  // pinned: residual bits + flag
     lbm_batch* owner;     // non-NULL: a member of a batch, stepped by the batch only
     std::string err;
+    // lbm_step's graphs: residual_interval steps and the residual check that ends them,
+    // one per starting buffer, captured on a private stream when first needed
+    cudaStream_t capture = nullptr;
+    cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+    bool graphs_failed = false;  // capture not possible here: launch the steps one by one
 };
 
 namespace lbm {
