@@ -28,6 +28,7 @@ if ROOT not in sys.path:
 METRIC = "coupled MLUPS & % HBM roofline; time-to-steady Nu at Ra=1e5 vs plain FP32"
 N_GRID, RA, PR, U0 = 128, 1e5, 0.71, 0.05
 RESIDUAL_INTERVAL = 100
+KERNEL_STEPS = 1000  # steps per kernel-timing graph
 # algorithmic bytes per node update: every population read once and written once; the
 # 16-bit forms also read and write the FP32 node temperature their thermal deviations use
 def bytes_per_node(q, storage_bytes=4):
@@ -183,11 +184,12 @@ def run_variant(lbm, q, steps, warmup, dist, device, clocks=None, precision=None
     nu = sim.nusselt()
     residual = sim.residual()
 
-    # the step kernel alone (no residual launches) for the roofline
+    # the step kernel for the roofline, as lbm_step runs it: one CUDA graph of KSTEPS steps
+    # (its single residual check adds < 0.05%); the first call captures the graph
+    ksteps = KERNEL_STEPS
     kern = lbm.LBM((n,) * 3, q, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0), precision=precision,
-                   residual_interval=0)
-    kern.step(max(10, warmup // 4))
-    ksteps = max(50, min(steps, 2000))
+                   residual_interval=ksteps)
+    kern.step(ksteps)
     t_kernel = time_steps(kern, ksteps, stream) / ksteps
     kern.close()
     return dict(sim=sim, elapsed=elapsed_max, mlups=n3 * steps / elapsed_max / 1e6,
