@@ -355,6 +355,28 @@ def batch_variant(lbm, steps, warmup, peak, converge_steps=0):
     return out
 
 
+def slab_variant(lbm, steps, warmup, device, undivided_ms):
+    """The same 128^3 cavity decomposed into z-slabs with a halo exchange after every step
+    (one GPU: the decomposition's own cost, the extra halo planes and the exchange kernel)."""
+    import torch
+    from paper_1710_04751_gb300 import slabs
+    stream = torch.cuda.current_stream(device)
+    out = {}
+    for nslabs in (2, 4):
+        dec = slabs.Slabs((N_GRID,) * 3, nslabs, 15, Ra=RA, Pr=PR, Ma=U0 * math.sqrt(3.0),
+                          residual_interval=RESIDUAL_INTERVAL)
+        dec.step(warmup)
+        t = time_steps(dec, steps, stream)
+        ms = t / steps * 1e3
+        out[f"{nslabs} slabs"] = {
+            "value": round(N_GRID ** 3 * steps / t / 1e6, 1), "unit": "MLUPS", "steps": steps,
+            "ms_per_step": round(ms, 5), "undivided_ms_per_step": round(undivided_ms, 5),
+            "time_vs_undivided": round(ms / undivided_ms, 4),
+            "halo_bytes_per_step": dec.halo_bytes, "kernel_launches_per_step": nslabs + 1}
+        dec.close()
+    return out
+
+
 def time_steps_mode(b, steps, stream, mode):
     import torch
     start = torch.cuda.Event(enable_timing=True)
@@ -586,6 +608,10 @@ def gpu_arm(args):
     if not args.no_batch:
         line["batch"] = batch_variant(lbm, args.batch_steps, RESIDUAL_INTERVAL, peak,
                                       args.batch_converge_steps)
+    if not args.no_slabs:
+        line["slabs"] = slab_variant(lbm, max(RESIDUAL_INTERVAL, args.steps // 10 // RESIDUAL_INTERVAL
+                                          * RESIDUAL_INTERVAL), args.warmup, device,
+                                     main["elapsed"] / args.steps * 1e3)
     if not args.no_net:
         line["net"] = net_variant()
     if args.warmstart:
@@ -669,6 +695,7 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-cavity batched form")
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--no-net", action="store_true", help="skip the warm-start network timings")
+    ap.add_argument("--no-slabs", action="store_true", help="skip the z-slab decomposition timings")
     ap.add_argument("--warmstart", action="store_true",
                     help="also run the learned warm start end to end (about 15 minutes)")
     ap.add_argument("--ws-train", type=int, default=400)

@@ -235,13 +235,18 @@ static int check_params(const lbm_params* p, int q) {
 template <typename S>
 static int run_init(lbm_ctx* c) {
     const ParamsOf<S> p = dev_params<typename Storage<S>::real>(c);
-    CUDA_OR_FAIL(c, launch_init<S>(c->dev, p, c->opt.seed, c->opt.noise_amp, c->stream));
+    CUDA_OR_FAIL(c, launch_init<S>(c->dev, p, c->opt.seed, c->cell0, c->opt.noise_amp, c->stream));
     CUDA_OR_FAIL(c, launch_residual<S>(c->dev, 0, p, 0, c->stream));
     return LBM_OK;
 }
 
 extern "C" int lbm_create_params(const lbm_grid* grid, int lattice, const lbm_params* params,
                                  const lbm_options* opt, lbm_ctx** out) {
+    return lbm::create_context(grid, lattice, params, opt, 0, out);
+}
+
+int lbm::create_context(const lbm_grid* grid, int lattice, const lbm_params* params,
+                        const lbm_options* opt, int64_t cell0, lbm_ctx** out) {
     if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL%s");
     *out = nullptr;
     if (!valid_grid(grid)) return fail(nullptr, LBM_EINVAL, "invalid grid%s");
@@ -269,6 +274,7 @@ extern "C" int lbm_create_params(const lbm_grid* grid, int lattice, const lbm_pa
     c->cur = 0;
     c->steps = 0;
     c->last_residual = -1.0;
+    c->cell0 = cell0;
     int rc = LBM_OK;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) {

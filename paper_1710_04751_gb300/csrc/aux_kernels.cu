@@ -11,7 +11,9 @@ namespace lbm {
 // ---------------------------------------------------------------------------------
 // Initial state: fluid at rest (f = rest weights) and T = seeded uniform noise in
 // [-amp, amp], g = w^phi T.  The noise is splitmix64 (Steele, Lea & Flood 2014, with
-// S. Vigna's published constants) of (seed xor cell index), top 53 bits.
+// S. Vigna's published constants) of (seed xor cell index), top 53 bits.  The cell index
+// is global: a context holding planes of a larger grid (one slab of a decomposition)
+// passes the global index of its cell 0 as cell0 and so starts from the same state.
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     uint64_t z = x + 0x9e3779b97f4a7c15ULL;
@@ -22,12 +24,12 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 
 template <typename S, int Q>
 __global__ void init_kernel(S* __restrict__ F, S* __restrict__ G, float* __restrict__ Tn,
-                            ParamsOf<S> p, uint64_t seed, double amp, double w0, double w1,
+                            ParamsOf<S> p, uint64_t seed, int64_t cell0, double amp, double w0, double w1,
                             double w7, double v0, double v1, double v7) {
     using real = typename Storage<S>::real;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= p.ncell) return;
-    const uint64_t r = splitmix64(seed ^ (uint64_t)c);
+    const uint64_t r = splitmix64(seed ^ (uint64_t)(c + cell0));
     const double u01 = (double)(r >> 11) * (1.0 / 9007199254740992.0);
     const double T = amp * (2.0 * u01 - 1.0);
 #pragma unroll
@@ -45,8 +47,8 @@ __global__ void init_kernel(S* __restrict__ F, S* __restrict__ G, float* __restr
 }
 
 template <typename S>
-cudaError_t launch_init(const DevState& s, const ParamsOf<S>& p, uint64_t seed, double amp,
-                        cudaStream_t st) {
+cudaError_t launch_init(const DevState& s, const ParamsOf<S>& p, uint64_t seed, int64_t cell0,
+                        double amp, cudaStream_t st) {
     // rest weights: flow (c_s^2 = 1/3) and thermal (c_sphi^2), from the equilibria
     const double cs2 = 1.0 / 3.0, ct = (double)p.cs2_phi;
     const double w7 = cs2 * cs2 / 8.0, w1 = 0.5 * (cs2 - cs2 * cs2), w0 = 1.0 - 6.0 * w1 - 8.0 * w7;
@@ -66,9 +68,9 @@ cudaError_t launch_init(const DevState& s, const ParamsOf<S>& p, uint64_t seed, 
     S* G = static_cast<S*>(s.G[0]);
     float* Tn = static_cast<float*>(s.T[0]);
     if (s.Q == 15)
-        init_kernel<S, 15><<<blocks, threads, 0, st>>>(F, G, Tn, p, seed, amp, w0, w1, w7, v0, v1, v7);
+        init_kernel<S, 15><<<blocks, threads, 0, st>>>(F, G, Tn, p, seed, cell0, amp, w0, w1, w7, v0, v1, v7);
     else
-        init_kernel<S, 7><<<blocks, threads, 0, st>>>(F, G, Tn, p, seed, amp, w0, w1, w7, v0, v1, v7);
+        init_kernel<S, 7><<<blocks, threads, 0, st>>>(F, G, Tn, p, seed, cell0, amp, w0, w1, w7, v0, v1, v7);
     return cudaGetLastError();
 }
 
@@ -454,8 +456,8 @@ cudaError_t launch_nusselt_into(const S* F, const S* G, const ParamsOf<S>& p, do
 }
 
 #define LBM_INSTANTIATE(S)                                                                         \
-    template cudaError_t launch_init<S>(const DevState&, const ParamsOf<S>&, uint64_t, double,      \
-                                        cudaStream_t);                                             \
+    template cudaError_t launch_init<S>(const DevState&, const ParamsOf<S>&, uint64_t, int64_t,     \
+                                        double, cudaStream_t);                                     \
     template cudaError_t launch_to_storage<S>(S*, const double*, int64_t, double, const float*,     \
                                               cudaStream_t);                                       \
     template cudaError_t launch_to_double<S>(double*, const S*, int64_t, double, const float*,      \

@@ -56,6 +56,7 @@ struct lbm_ctx {
     cudaStream_t capture = nullptr;
     cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
     bool graphs_failed = false;  // capture not possible here: launch the steps one by one
+    int64_t cell0 = 0;  // global index of cell 0 (slabs of a larger grid), for the initial noise
 };
 
 namespace lbm {
@@ -81,6 +82,11 @@ DevParams<real> dev_params(const lbm_ctx* c);
 
 // Frees a context (lbm_destroy without the batch-member check).
 void destroy_context(lbm_ctx* c);
+
+// lbm_create_params with the initial noise drawn for global cell indices cell0 + c (a slab
+// of a larger grid starts from that grid's state); cell0 = 0 is lbm_create_params.
+int create_context(const lbm_grid* grid, int lattice, const lbm_params* params,
+                   const lbm_options* opt, int64_t cell0, lbm_ctx** out);
 
 // Bytes of the device arena of one context.
 size_t context_arena_bytes(const lbm_grid* g, int q, int precision);

@@ -50,9 +50,10 @@ using ParamsOf = DevParams<typename Storage<S>::real>;
 
 template <typename S>
 cudaError_t launch_step(const DevState& s, int cur, const ParamsOf<S>& p, cudaStream_t st);
+// (cell0: global index of the context's cell 0, for the seeded initial noise)
 template <typename S>
-cudaError_t launch_init(const DevState& s, const ParamsOf<S>& p, uint64_t seed, double amp,
-                        cudaStream_t st);
+cudaError_t launch_init(const DevState& s, const ParamsOf<S>& p, uint64_t seed, int64_t cell0,
+                        double amp, cudaStream_t st);
 // one population plane between FP64 host values and storage (offset: that plane's
 // stored-value offset, used by the 16-bit forms)
 // (thermal planes of the 16-bit forms: offset = w^phi_a and Tn the node temperatures)

@@ -13,6 +13,7 @@ import paper_1710_04751_gb300 as lbm
 from paper_1710_04751_gb300 import batch as batch_binding
 from paper_1710_04751_gb300 import lbm as binding
 from paper_1710_04751_gb300 import net as net_binding
+from paper_1710_04751_gb300 import slabs as slabs_binding
 
 INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
 
@@ -25,7 +26,8 @@ def declared_functions(header):
 
 @pytest.mark.parametrize("header,exports", [("lbm.h", binding.EXPORTS),
                                             ("lbm_batch.h", batch_binding.EXPORTS),
-                                            ("lbm_net.h", net_binding.EXPORTS)])
+                                            ("lbm_net.h", net_binding.EXPORTS),
+                                            ("lbm_slabs.h", slabs_binding.EXPORTS)])
 def test_library_exports_every_declared_entry_point(header, exports):
     L = binding.load()
     names = declared_functions(header)
@@ -36,7 +38,8 @@ def test_library_exports_every_declared_entry_point(header, exports):
 
 
 def test_every_header_is_checked():
-    assert sorted(f for f in os.listdir(INCLUDE) if f.endswith(".h")) == ["lbm.h", "lbm_batch.h", "lbm_net.h"]
+    assert sorted(f for f in os.listdir(INCLUDE) if f.endswith(".h")) == ["lbm.h", "lbm_batch.h", "lbm_net.h",
+                                                                                     "lbm_slabs.h"]
 
 
 def test_structure_sizes_match_header_layout():
@@ -167,3 +170,38 @@ def test_checkpoint_header_layout(tmp_path):
         assert e.value.code == binding.LBM_EINVAL
     with pytest.raises(lbm.LBMError):
         binding.checkpoint_info(str(tmp_path / "missing.ckpt"))
+
+
+def test_slab_plan():
+    # even split: the first nz % nslabs slabs take one plane more; halos at inner cuts only
+    pl = slabs_binding.plan(23, 4)
+    assert pl == {"z0": [0, 6, 12, 18], "nz_owned": [6, 6, 6, 5], "halo_lo": [0, 1, 1, 1],
+                  "halo_hi": [1, 1, 1, 0]}
+    pl = slabs_binding.plan(23, 3, owned=[1, 11, 11])
+    assert pl["z0"] == [0, 1, 12] and pl["nz_owned"] == [1, 11, 11]
+    # z periodic (boundary bit 2): every slab has both halos; one slab has none
+    assert slabs_binding.plan(11, 4, boundary=lbm.BC_XWALLS)["halo_lo"] == [1, 1, 1, 1]
+    assert slabs_binding.plan(11, 4, boundary=lbm.BC_PERIODIC)["halo_hi"] == [1, 1, 1, 1]
+    assert slabs_binding.plan(11, 1, boundary=lbm.BC_PERIODIC) == {
+        "z0": [0], "nz_owned": [11], "halo_lo": [0], "halo_hi": [0]}
+    assert slabs_binding.plan(5, 5)["nz_owned"] == [1] * 5
+    for nz, n, owned in ((5, 6, None), (5, 0, None), (0, 1, None), (6, 2, [3, 2]), (6, 2, [6, 0])):
+        with pytest.raises(lbm.LBMError) as e:
+            slabs_binding.plan(nz, n, owned=owned)
+        assert e.value.code == binding.LBM_EINVAL
+
+
+def test_slabs_create_rejects_without_touching_the_device():
+    L = slabs_binding._lib()
+    p = lbm.derive_params((8, 8, 8), 15, 1e3, 0.71, 0.0866)
+    h = ctypes.c_void_p()
+    g = binding.Grid(8, 8, 8)
+    for nslabs, owned in ((0, None), (9, None), (2, [4, 5])):
+        rc = L.lbm_slabs_create(ctypes.byref(g), 15, ctypes.byref(p), None, nslabs,
+                                slabs_binding._ints(owned), ctypes.byref(h))
+        assert rc == binding.LBM_EINVAL and not h.value
+    o = binding.default_options()
+    o.device_arena = 0x1000  # slabs allocate their own memory
+    rc = L.lbm_slabs_create(ctypes.byref(g), 15, ctypes.byref(p), ctypes.byref(o), 2, None,
+                            ctypes.byref(h))
+    assert rc == binding.LBM_EINVAL and b"own device memory" in L.lbm_slabs_last_error(None)
