@@ -47,6 +47,9 @@ extern "C" int lbm_nn_gemm_bf16(const void* A, int64_t lda, const void* B, int64
                                 void* cuda_stream) {
     if (!A || !B || !C || ldc < N)
         return record_error(nullptr, LBM_EINVAL, "NULL operand or ldc < N%s");
+    // the public modes only (the internal split-slice mode writes past C)
+    if (out_mode != LBM_GEMM_F32 && out_mode != LBM_GEMM_BF16 && out_mode != LBM_GEMM_F32_ADD)
+        return record_error(nullptr, LBM_EINVAL, "invalid GEMM mode%s");
     int* err = error_word();
     if (!err) return record_error(nullptr, LBM_ECUDA, "no CUDA device%s");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

@@ -5,13 +5,16 @@
 // warp 1 lane 0 issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a TMEM
 // accumulator and frees each stage with tcgen05.commit; then all four warps read the
 // accumulator back (warp w owns TMEM lanes 32w..32w+31 = rows 32w..32w+31) and store it.
-// grid.z splits K; the split results are added with FP32 atomics.  Rows, columns and K
+// grid.z splits K; the split results are added with FP32 atomics, or (GEMM_F32_SPLITS)
+// stored in slices of a workspace and added to C in split order by a second kernel, so
+// that the sum is the same on every run.  Rows, columns and K
 // beyond the operands' extents read as zeros (TMA out-of-bounds fill) and are not stored.
 // Every wait is bounded (2 s): on a timeout the kernel records an error code, lets its
 // copies and MMAs drain, frees its TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "nn.h"
@@ -34,7 +37,7 @@ struct GemmSmem {
 struct GemmArgs {
     int M, N, K;
     int kblocks_per_split;
-    int out_mode;  // GEMM_F32, GEMM_BF16, GEMM_F32_ATOMIC
+    int out_mode;  // GEMM_F32, GEMM_BF16, GEMM_F32_ATOMIC, GEMM_F32_SPLITS
     void* C;
     long long ldc;
     int* err;
@@ -147,8 +150,11 @@ __global__ void __launch_bounds__(128, 1)
                         for (int j = 0; j < 16; ++j)
                             if (col0 + j < args.N) C[col0 + j] = __float2bfloat16_rn(v[j]);
                     }
-                } else if (args.out_mode == GEMM_F32) {
-                    float* C = static_cast<float*>(args.C) + row * args.ldc;
+                } else if (args.out_mode == GEMM_F32 || args.out_mode == GEMM_F32_SPLITS) {
+                    // GEMM_F32_SPLITS: split z stores its partial tile in slice z
+                    const long long slice =
+                        args.out_mode == GEMM_F32_SPLITS ? (long long)blockIdx.z * args.M * args.ldc : 0;
+                    float* C = static_cast<float*>(args.C) + slice + row * args.ldc;
                     if (full) {
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
@@ -227,18 +233,26 @@ static cudaError_t launch(const CUtensorMap& ta, const CUtensorMap& tb, const Ge
     return cudaGetLastError();
 }
 
+// The K blocks of one split (*per) and the number of splits actually launched: every
+// split gets at least one K block.
+static int split_count(int K, int splits, int* per) {
+    const int kb_total = (K + BK - 1) / BK;
+    splits = splits > kb_total ? kb_total : splits;
+    *per = (kb_total + splits - 1) / splits;
+    return (kb_total + *per - 1) / *per;
+}
+
 cudaError_t gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B,
                       long long ldb, void* C, long long ldc, int M, int N, int K, int out_mode,
                       int splits, int* err, cudaStream_t st) {
     if (M <= 0 || N <= 0 || K <= 0 || (lda % 8) || (ldb % 8) || lda < K || ldb < K || splits < 1 ||
-        ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || out_mode < GEMM_F32 || out_mode > GEMM_F32_ATOMIC)
+        ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || out_mode < GEMM_F32 || out_mode > GEMM_F32_SPLITS)
         return cudaErrorInvalidValue;
     const int BN = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
-    const int kb_total = (K + BK - 1) / BK;
-    splits = splits > kb_total ? kb_total : splits;
-    const int per = (kb_total + splits - 1) / splits;
-    splits = (kb_total + per - 1) / per;  // every split gets at least one K block
-    if (splits > 1 && out_mode != GEMM_F32_ATOMIC) return cudaErrorInvalidValue;
+    int per;
+    splits = split_count(K, splits, &per);
+    if (splits > 1 && out_mode != GEMM_F32_ATOMIC && out_mode != GEMM_F32_SPLITS)
+        return cudaErrorInvalidValue;
     CUtensorMap ta, tb;
     if (!make_map(&ta, A, M, K, lda, BM) || !make_map(&tb, B, N, K, ldb, BN))
         return cudaErrorInvalidValue;
@@ -251,6 +265,40 @@ cudaError_t gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16
     case 128: return launch<128>(ta, tb, a, splits, st);
     default: return launch<256>(ta, tb, a, splits, st);
     }
+}
+
+// C[r][c] += ws[0][r][c] + ws[1][r][c] + ... in split order (slices of M * ldc floats).
+__global__ void add_splits_kernel(const float* __restrict__ ws, int splits, int M, int N, long long ldc,
+                                  float* __restrict__ C) {
+    const int64_t total = (int64_t)M * N;
+    const int64_t slice = (int64_t)M * ldc;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = (q / N) * ldc + q % N;
+        float s = C[o];
+        for (int z = 0; z < splits; ++z) s += ws[z * slice + o];
+        C[o] = s;
+    }
+}
+
+cudaError_t gemm_bf16_add_splitk(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B,
+                                 long long ldb, float* C, long long ldc, int M, int N, int K,
+                                 int splits, float* ws, size_t ws_floats, int* err, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0 || splits < 1 || ldc < N) return cudaErrorInvalidValue;
+    int per;
+    const int used = split_count(K, splits, &per);
+    if ((size_t)used * M * ldc > ws_floats) return cudaErrorInvalidValue;
+    cudaError_t e = gemm_bf16(A, lda, B, ldb, ws, ldc, M, N, K, GEMM_F32_SPLITS, used, err, st);
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)M * N;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+    add_splits_kernel<<<blocks, 256, 0, st>>>(ws, used, M, N, ldc, C);
+    return cudaGetLastError();
+}
+
+size_t gemm_splitk_floats(int M, long long ldc, int K, int splits) {
+    int per;
+    return (size_t)split_count(K, splits, &per) * M * ldc;
 }
 
 }  // namespace nn

@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "nn.h"
 
 namespace lbm {
@@ -127,34 +129,58 @@ cudaError_t bias_relu(const float* Y, const float* bias, int64_t M, int C, __nv_
     return cudaGetLastError();
 }
 
-// dZ = dA where A > 0 (BF16, the GEMM operand), db[c] += sum_m dZ (FP32 per block, then
-// one atomic per channel and block).  C <= 256, blockDim = 256.
-__global__ void relu_bwd_kernel(const float* __restrict__ dA, const __nv_bfloat16* __restrict__ A,
-                                int64_t ldA, int a_off, int64_t M, int C,
-                                __nv_bfloat16* __restrict__ dZ, float* __restrict__ db) {
-    __shared__ float acc[256];
-    for (int c = threadIdx.x; c < C; c += blockDim.x) acc[c] = 0.f;
-    __syncthreads();
-    const int64_t total = M * C;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = q / C;
-        const int c = (int)(q - m * C);
-        const float g = __bfloat162float(A[m * ldA + a_off + c]) > 0.f ? dA[q] : 0.f;
-        dZ[q] = __float2bfloat16_rn(g);
-        atomicAdd(&acc[c], g);
+// Gradient sums over rows are taken in a fixed order -- rows ascending within a thread,
+// then the threads of a block, then the blocks (sum_partials_kernel) -- so that training
+// gives the same result on every run.
+
+// out[i] += sum_b part[b * ld + first + i] for i < count, blocks b in ascending order.
+__global__ void sum_partials_kernel(const float* __restrict__ part, int nblocks, int ld, int first,
+                                    int count, float* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        float s = out[i];
+        for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * ld + first + i];
+        out[i] = s;
     }
+}
+
+static int64_t rows_per_block(int64_t M, int64_t at_least, int max_blocks) {
+    return std::max<int64_t>(at_least, (M + max_blocks - 1) / max_blocks);
+}
+
+// dZ = dA where A > 0 (BF16, the GEMM operand) and the per-block sums of dZ over channels:
+// thread t takes channel c = t % C and every R-th row (R = 256 / C lanes, lane t / C) of
+// the block's rows; the lanes are then added in order.  C <= 256, blockDim = 256.
+__global__ void relu_bwd_kernel(const float* __restrict__ dA, const __nv_bfloat16* __restrict__ A,
+                                int64_t ldA, int a_off, int64_t M, int C, int64_t rows,
+                                __nv_bfloat16* __restrict__ dZ, float* __restrict__ part) {
+    __shared__ float acc[256];
+    const int R = 256 / C;
+    const int c = threadIdx.x % C, r = threadIdx.x / C;
+    const int64_t m0 = (int64_t)blockIdx.x * rows, m1 = m0 + rows < M ? m0 + rows : M;
+    float s = 0.f;
+    if (r < R) {
+        for (int64_t m = m0 + r; m < m1; m += R) {
+            const float g = __bfloat162float(A[m * ldA + a_off + c]) > 0.f ? dA[m * C + c] : 0.f;
+            dZ[m * C + c] = __float2bfloat16_rn(g);
+            s += g;
+        }
+    }
+    acc[threadIdx.x] = s;
     __syncthreads();
-    for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(db + c, acc[c]);
+    if (threadIdx.x < C) {
+        float t = 0.f;
+        for (int l = 0; l < R; ++l) t += acc[l * C + threadIdx.x];
+        part[(int64_t)blockIdx.x * C + threadIdx.x] = t;
+    }
 }
 
 cudaError_t relu_bwd(const float* dA, const __nv_bfloat16* A, int64_t ldA, int a_off, int64_t M,
-                     int C, __nv_bfloat16* dZ, float* db, cudaStream_t st) {
-    if (C > 256) return cudaErrorInvalidValue;
-    const int64_t total = M * C;
-    unsigned blocks = blocks_for(total, 256);
-    if (blocks > 4096) blocks = 4096;
-    relu_bwd_kernel<<<blocks, 256, 0, st>>>(dA, A, ldA, a_off, M, C, dZ, db);
+                     int C, __nv_bfloat16* dZ, float* db, float* part, cudaStream_t st) {
+    if (C < 1 || C > 256 || M < 1) return cudaErrorInvalidValue;
+    const int64_t rows = rows_per_block(M, 256 / C, kMaxPartialBlocks);
+    const int nblocks = (int)((M + rows - 1) / rows);
+    relu_bwd_kernel<<<nblocks, 256, 0, st>>>(dA, A, ldA, a_off, M, C, rows, dZ, part);
+    sum_partials_kernel<<<1, 256, 0, st>>>(part, nblocks, C, 0, C, db);
     return cudaGetLastError();
 }
 
@@ -298,34 +324,35 @@ __global__ void head_kernel(const __nv_bfloat16* __restrict__ A, int64_t M, int 
     }
 }
 
-// dA[m][c] = sum_j dOut[m][j] W[j][c]; dW[j][c] += sum_m dOut[m][j] A[m][c]; db[j] += sum_m dOut
-// (block partial sums in shared memory, one atomic per entry and block).  C <= 64.
-__global__ void head_bwd_kernel(const float* __restrict__ dOut, const __nv_bfloat16* __restrict__ A,
-                                int64_t M, int C, const float* __restrict__ W, float* __restrict__ dA,
-                                float* __restrict__ dW, float* __restrict__ db) {
-    __shared__ float sW[4 * 64], sb[4];
-    for (int i = threadIdx.x; i < 4 * C; i += blockDim.x) sW[i] = 0.f;
-    if (threadIdx.x < 4) sb[threadIdx.x] = 0.f;
-    __syncthreads();
+// dA[m][c] = sum_j dOut[m][j] W[j][c] (one thread per row).
+__global__ void head_dA_kernel(const float* __restrict__ dOut, int64_t M, int C,
+                               const float* __restrict__ W, float* __restrict__ dA) {
     for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
          m += (int64_t)gridDim.x * blockDim.x) {
         const float g[4] = {dOut[m * 4], dOut[m * 4 + 1], dOut[m * 4 + 2], dOut[m * 4 + 3]};
         for (int c = 0; c < C; ++c) {
-            const float a = __bfloat162float(A[m * C + c]);
             float s = 0.f;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                s += g[j] * W[j * C + c];
-                atomicAdd(&sW[j * C + c], g[j] * a);
-            }
+            for (int j = 0; j < 4; ++j) s += g[j] * W[j * C + c];
             dA[m * C + c] = s;
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) atomicAdd(&sb[j], g[j]);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 4 * C; i += blockDim.x) atomicAdd(dW + i, sW[i]);
-    if (threadIdx.x < 4) atomicAdd(db + threadIdx.x, sb[threadIdx.x]);
+}
+
+// Per-block sums over the block's rows, in row order: entry i < 4C is dW[j][c] (i = j C + c)
+// += dOut[m][j] A[m][c], entries 4C .. 4C+3 are db[j] += dOut[m][j].  C <= 64.
+__global__ void head_dW_kernel(const float* __restrict__ dOut, const __nv_bfloat16* __restrict__ A,
+                               int64_t M, int C, int64_t rows, float* __restrict__ part) {
+    const int E = 4 * C + 4;
+    const int64_t m0 = (int64_t)blockIdx.x * rows, m1 = m0 + rows < M ? m0 + rows : M;
+    for (int i = threadIdx.x; i < E; i += blockDim.x) {
+        const int j = i < 4 * C ? i / C : i - 4 * C;
+        const int c = i < 4 * C ? i % C : -1;
+        float s = 0.f;
+        for (int64_t m = m0; m < m1; ++m)
+            s += c >= 0 ? dOut[m * 4 + j] * __bfloat162float(A[m * C + c]) : dOut[m * 4 + j];
+        part[(int64_t)blockIdx.x * E + i] = s;
+    }
 }
 
 cudaError_t head_fwd(const __nv_bfloat16* A, int64_t M, int C, const float* W, const float* b,
@@ -334,18 +361,25 @@ cudaError_t head_fwd(const __nv_bfloat16* A, int64_t M, int C, const float* W, c
     return cudaGetLastError();
 }
 cudaError_t head_bwd(const float* dOut, const __nv_bfloat16* A, int64_t M, int C, const float* W,
-                     float* dA, float* dW, float* db, cudaStream_t st) {
-    if (C > 64) return cudaErrorInvalidValue;
+                     float* dA, float* dW, float* db, float* part, cudaStream_t st) {
+    if (C < 1 || C > 64 || M < 1) return cudaErrorInvalidValue;
     unsigned blocks = blocks_for(M, 256);
     if (blocks > 2048) blocks = 2048;
-    head_bwd_kernel<<<blocks, 256, 0, st>>>(dOut, A, M, C, W, dA, dW, db);
+    head_dA_kernel<<<blocks, 256, 0, st>>>(dOut, M, C, W, dA);
+    const int64_t rows = rows_per_block(M, 64, kMaxPartialBlocks);
+    const int nblocks = (int)((M + rows - 1) / rows);
+    const int E = 4 * C + 4;
+    head_dW_kernel<<<nblocks, 256, 0, st>>>(dOut, A, M, C, rows, part);
+    sum_partials_kernel<<<1, 256, 0, st>>>(part, nblocks, E, 0, 4 * C, dW);
+    sum_partials_kernel<<<1, 32, 0, st>>>(part, nblocks, E, 4 * C, 4, db);
     return cudaGetLastError();
 }
 
 // ---- loss: mean squared error over all outputs ------------------------------------------------
-// dOut = 2 (out - target) / count; *loss += sum (out - target)^2 / count (FP64 atomics).
+// dOut = 2 (out - target) / count; the per-block sums of (out - target)^2 / count go to
+// part[block] and are added to *loss in block order.
 __global__ void mse_kernel(const float* __restrict__ out, const float* __restrict__ target,
-                           int64_t count, float* __restrict__ dOut, double* __restrict__ loss) {
+                           int64_t count, float* __restrict__ dOut, double* __restrict__ part) {
     __shared__ double red[8];
     double s = 0.0;
     const double inv = 1.0 / (double)count;
@@ -361,15 +395,22 @@ __global__ void mse_kernel(const float* __restrict__ out, const float* __restric
     if (threadIdx.x < 32) {
         double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (threadIdx.x == 0) atomicAdd(loss, v * inv);
+        if (threadIdx.x == 0) part[blockIdx.x] = v * inv;
     }
 }
 
+__global__ void sum_loss_kernel(const double* __restrict__ part, int nblocks, double* __restrict__ loss) {
+    double s = *loss;
+    for (int b = 0; b < nblocks; ++b) s += part[b];
+    *loss = s;
+}
+
 cudaError_t mse(const float* out, const float* target, int64_t count, float* dOut, double* loss,
-                cudaStream_t st) {
+                double* part, cudaStream_t st) {
     unsigned blocks = blocks_for(count, 256);
-    if (blocks > 2048) blocks = 2048;
-    mse_kernel<<<blocks, 256, 0, st>>>(out, target, count, dOut, loss);
+    if (blocks > (unsigned)kMaxPartialBlocks) blocks = kMaxPartialBlocks;
+    mse_kernel<<<blocks, 256, 0, st>>>(out, target, count, dOut, part);
+    sum_loss_kernel<<<1, 1, 0, st>>>(part, (int)blocks, loss);
     return cudaGetLastError();
 }
 

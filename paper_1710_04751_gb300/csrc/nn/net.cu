@@ -53,6 +53,10 @@ struct lbm_net {
     // scratch
     __nv_bfloat16 *xcol, *xcolT, *dZ, *dZT;
     float* y;
+    float* ws;          // split-K partial results of the weight-gradient GEMMs
+    size_t ws_floats;
+    float* part;        // per-block partial sums of the bias / head gradients
+    double* partd;      // per-block partial sums of the loss
     double* loss;
     int* err;
     void* arena;
@@ -118,17 +122,29 @@ struct Carver {
     }
 };
 
+// K splits of the weight-gradient GEMM of a layer (K = M voxels): about two CTAs per SM
+// over the output tiles, at least one K block per split.
+int wgrad_splits(const lbm_net* N, const Conv& k, int64_t M) {
+    const int tiles = (k.Kp + 127) / 128;
+    const int kb = (int)((M + 63) / 64);
+    return std::max(1, std::min(2 * N->sm_count / tiles, kb));
+}
+
 // Lays out (base == nullptr: only sizes) every buffer of the network.
 size_t carve(lbm_net* N, char* base) {
     Carver c{base};
     const int64_t B = N->B, V0 = N->V[0], V1 = N->V[1], V2 = N->V[2];
     const int c1 = N->cfg.c1, c2 = N->cfg.c2, c3 = N->cfg.c3;
-    int64_t max_xcol = 0, max_y = 0;
+    int64_t max_xcol = 0, max_y = 0, max_cout = 0;
+    size_t ws = 0;
     for (int l = 0; l < kLayers; ++l) {
         Conv& k = N->conv[l];
         const int64_t M = B * N->V[k.level];
         max_xcol = std::max(max_xcol, M * std::max(k.Kp, k.Kpf));
         max_y = std::max(max_y, M * k.cout);
+        max_cout = std::max<int64_t>(max_cout, k.cout);
+        // the largest batch asks for the most splits (wgrad_splits grows with M)
+        ws = std::max(ws, gemm_splitk_floats(k.Kp, k.cout, (int)M, wgrad_splits(N, k, M)));
         const int64_t w = (int64_t)k.cout * k.K27;
         k.W = c.take<float>(w);
         k.b = c.take<float>(k.cout);
@@ -190,6 +206,10 @@ size_t carve(lbm_net* N, char* base) {
     N->dZ = c.take<bf>(max_y);
     N->dZT = c.take<bf>(max_y);
     N->y = c.take<float>(max_y);
+    N->ws = c.take<float>((int64_t)ws);
+    N->ws_floats = ws;
+    N->part = c.take<float>((int64_t)kMaxPartialBlocks * std::max<int64_t>(max_cout, 4 * c1 + 4));
+    N->partd = c.take<double>(kMaxPartialBlocks);
     N->loss = c.take<double>(1);
     return c.off;
 }
@@ -214,16 +234,12 @@ int conv_bwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, const __nv_bfloat
     const int n = N->n >> k.level;
     const int64_t M = (int64_t)B * N->V[k.level];
     cudaStream_t st = N->stream;
-    NET_CUDA(N, relu_bwd(dA, A, k.cout, 0, M, k.cout, N->dZ, k.gb, st));
+    NET_CUDA(N, relu_bwd(dA, A, k.cout, 0, M, k.cout, N->dZ, k.gb, N->part, st));
     NET_CUDA(N, transpose(N->dZ, M, k.cout, k.cout, N->dZT, M, st));
     NET_CUDA(N, im2col(X, B, n, k.cin, k.Kp, N->xcol, st));
     NET_CUDA(N, transpose(N->xcol, M, k.Kp, k.Kp, N->xcolT, M, st));
-    const int tiles = (k.Kp + 127) / 128;
-    const int kb = (int)((M + 63) / 64);
-    int splits = 2 * N->sm_count / tiles;
-    splits = std::max(1, std::min(splits, kb));
-    NET_CUDA(N, gemm_bf16(N->xcolT, M, N->dZT, M, k.dWT, k.cout, k.Kp, k.cout, (int)M,
-                          GEMM_F32_ATOMIC, splits, N->err, st));
+    NET_CUDA(N, gemm_bf16_add_splitk(N->xcolT, M, N->dZT, M, k.dWT, k.cout, k.Kp, k.cout, (int)M,
+                                     wgrad_splits(N, k, M), N->ws, N->ws_floats, N->err, st));
     if (dX) {  // dX = im2col(dZ) Wf^T (the xcol scratch is free again)
         NET_CUDA(N, im2col(N->dZ, B, n, k.cout, k.Kpf, N->xcol, st));
         NET_CUDA(N, gemm_bf16(N->xcol, k.Kpf, k.Wf, k.Kpf, dX, k.cin, (int)M, k.cin, k.Kpf,
@@ -277,8 +293,8 @@ int backward(lbm_net* N, int B, const float* target) {
     NET_CUDA(N, cudaMemsetAsync(N->gWh, 0, (size_t)4 * c1 * 4, st));
     NET_CUDA(N, cudaMemsetAsync(N->gbh, 0, 16, st));
     NET_CUDA(N, cudaMemsetAsync(N->loss, 0, 8, st));
-    NET_CUDA(N, mse(N->out, target, M0 * 4, N->dOut, N->loss, st));
-    NET_CUDA(N, head_bwd(N->dOut, N->A10, M0, c1, N->Wh, N->dA10, N->gWh, N->gbh, st));
+    NET_CUDA(N, mse(N->out, target, M0 * 4, N->dOut, N->loss, N->partd, st));
+    NET_CUDA(N, head_bwd(N->dOut, N->A10, M0, c1, N->Wh, N->dA10, N->gWh, N->gbh, N->part, st));
     NET_RC(conv_bwd(N, 10, N->A9, B, N->A10, N->dA10, N->dA9, 0));
     NET_RC(conv_bwd(N, 9, N->C1, B, N->A9, N->dA9, N->dC1, 0));
     NET_CUDA(N, upsample_bwd(N->dC1, c2 + c1, 0, B, n, c2, N->dA8, st));

@@ -9,15 +9,23 @@
 namespace lbm {
 namespace nn {
 
-enum { GEMM_F32 = 0, GEMM_BF16 = 1, GEMM_F32_ATOMIC = 2 };
+enum { GEMM_F32 = 0, GEMM_BF16 = 1, GEMM_F32_ATOMIC = 2, GEMM_F32_SPLITS = 3 };
 
 // C[M][N] (row stride ldc) = (or +=, GEMM_F32_ATOMIC) sum_k A[m][k] B[n][k]; A and B BF16
 // row-major with row strides lda, ldb (elements, multiples of 8, 16-byte aligned bases);
-// FP32 accumulation on the tensor cores; `splits` > 1 splits K (atomic mode only).  A
-// timeout inside the kernel writes a non-zero code to *err (device memory).
+// FP32 accumulation on the tensor cores; `splits` > 1 splits K (GEMM_F32_ATOMIC, or
+// GEMM_F32_SPLITS: split z writes its partial result to C + z * M * ldc).  A timeout
+// inside the kernel writes a non-zero code to *err (device memory).
 cudaError_t gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B,
                       long long ldb, void* C, long long ldc, int M, int N, int K, int out_mode,
                       int splits, int* err, cudaStream_t st);
+
+// C += A B^T (FP32 C) with K split across CTAs and the partial results added in split
+// order from the workspace ws (gemm_splitk_floats floats): run-to-run identical sums.
+cudaError_t gemm_bf16_add_splitk(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B,
+                                 long long ldb, float* C, long long ldc, int M, int N, int K,
+                                 int splits, float* ws, size_t ws_floats, int* err, cudaStream_t st);
+size_t gemm_splitk_floats(int M, long long ldc, int K, int splits);
 
 }  // namespace nn
 }  // namespace lbm
@@ -32,8 +40,13 @@ cudaError_t transpose(const __nv_bfloat16* in, int64_t R, int64_t C, int64_t ld_
                       __nv_bfloat16* out, int64_t ld_out, cudaStream_t st);
 cudaError_t bias_relu(const float* Y, const float* bias, int64_t M, int C, __nv_bfloat16* A,
                       int64_t ldA, int c_off, cudaStream_t st);
+// Gradient reductions over rows (relu_bwd's db, head_bwd's dW and db, mse's loss) add
+// per-block partial sums in block order: `part` holds kMaxPartialBlocks * C floats
+// (relu_bwd), kMaxPartialBlocks * (4 C + 4) floats (head_bwd) or kMaxPartialBlocks
+// doubles (mse).
+constexpr int kMaxPartialBlocks = 1024;
 cudaError_t relu_bwd(const float* dA, const __nv_bfloat16* A, int64_t ldA, int a_off, int64_t M,
-                     int C, __nv_bfloat16* dZ, float* db, cudaStream_t st);
+                     int C, __nv_bfloat16* dZ, float* db, float* part, cudaStream_t st);
 cudaError_t avgpool(const __nv_bfloat16* X, int B, int n, int C, __nv_bfloat16* P, cudaStream_t st);
 cudaError_t avgpool_bwd(const float* dP, int B, int n, int C, float* dX, int accumulate,
                         cudaStream_t st);
@@ -48,9 +61,9 @@ cudaError_t slice_grad(const float* dD, int64_t ldD, int c_off, int64_t M, int C
 cudaError_t head_fwd(const __nv_bfloat16* A, int64_t M, int C, const float* W, const float* b,
                      float* out, cudaStream_t st);
 cudaError_t head_bwd(const float* dOut, const __nv_bfloat16* A, int64_t M, int C, const float* W,
-                     float* dA, float* dW, float* db, cudaStream_t st);
+                     float* dA, float* dW, float* db, float* part, cudaStream_t st);
 cudaError_t mse(const float* out, const float* target, int64_t count, float* dOut, double* loss,
-                cudaStream_t st);
+                double* part, cudaStream_t st);
 cudaError_t adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
                  float b2, float eps, int step, cudaStream_t st);
 cudaError_t pack_weights(const float* W, int cin, int cout, int Kp, int Kpf, __nv_bfloat16* Wb,

@@ -1,8 +1,17 @@
 """Python binding of include/lbm_slabs.h (argument marshalling only): one cavity split
 into z-slabs, each a context of its own with halo planes, exchanged after every step by
 a copy kernel in liblbm.so.  The owned nodes follow the undivided grid's trajectory bit
-for bit; the slabs share one GPU and one CUDA stream."""
+for bit; the slabs share one GPU and one CUDA stream.
+
+    python -m paper_1710_04751_gb300.slabs [--n 128] [--slabs 2] [--steps 1000] [--warmup 300]
+        [--skip-undivided]
+
+times the cavity (Ra = 1e5, Pr = 0.71, U0 = 0.05, D3Q15 + D3Q15, FP32) undivided and in
+slabs with CUDA events and prints one JSON object.
+"""
+import argparse
 import ctypes
+import json
 import math
 
 import numpy as np
@@ -182,3 +191,47 @@ class Slabs:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _time(sim, steps):
+    import torch
+    stream = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    sim.step(steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--slabs", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=300)
+    ap.add_argument("--skip-undivided", action="store_true", help="time the slabs only")
+    args = ap.parse_args(argv)
+    grid = (args.n,) * 3
+    kw = dict(Ra=1e5, Pr=0.71, Ma=0.05 * math.sqrt(3.0))
+    t1 = None
+    if not args.skip_undivided:
+        one = _b.LBM(grid, D3Q15, **kw)
+        one.step(args.warmup)
+        t1 = _time(one, args.steps)
+        one.close()
+    dec = Slabs(grid, args.slabs, D3Q15, **kw)
+    dec.step(args.warmup)
+    t2 = _time(dec, args.steps)
+    out = {"grid": list(grid), "slabs": args.slabs, "plan": dec.plan, "steps": args.steps,
+           "undivided_ms_per_step": round(t1 / args.steps * 1e3, 5) if t1 else None,
+           "slabs_ms_per_step": round(t2 / args.steps * 1e3, 5),
+           "time_vs_undivided": round(t2 / t1, 4) if t1 else None,
+           "halo_bytes_per_step": dec.halo_bytes}
+    dec.close()
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -86,6 +86,8 @@ def test_gemm_rejects_bad_arguments():
     with pytest.raises(LBMError):  # row stride not a multiple of 8
         At = torch.zeros((128, 70), dtype=torch.bfloat16, device="cuda")
         net.gemm_bf16(At, B.cuda(), C, net.GEMM_F32, K=64)
+    with pytest.raises(LBMError):  # the library's internal split-slice mode is not public
+        net.gemm_bf16(A.cuda(), B.cuda(), C, 3, splits=2)
 
 
 # ------------------------------------------------------------------------------------
@@ -191,6 +193,25 @@ def test_loss_falls_when_fitting_one_sample():
     losses = [netw.train_step([[0.1, 0.1]], t) for _ in range(300)]
     assert losses[-1] < 0.1 * losses[0]
     netw.close()
+
+
+def test_training_is_bitwise_reproducible():
+    # every gradient sum over voxels (split-K weight gradients, bias and head gradients, the
+    # loss) is added in a fixed order, so two trainings from the same seed on the same data
+    # end with identical parameters and losses
+    torch = torch_mod()
+    n = SMALL["n"]
+    rng = np.random.default_rng(5)
+    tgt = torch.as_tensor(rng.standard_normal((2, n ** 3, 4)) * 0.3, dtype=torch.float32).cuda()
+    runs = []
+    for _ in range(2):
+        netw = _small_net(seed=4, batch=2)
+        losses = [netw.train_step([[0.1, -0.2], [0.4, 0.3]], tgt) for _ in range(40)]
+        runs.append((losses, netw.get_params()))
+        netw.close()
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][0][-1] < runs[0][0][0]
 
 
 # ------------------------------------------------------------------------------------
