@@ -441,12 +441,12 @@ extern "C" int lbm_step(lbm_ctx* c, int64_t n) {
 }
 
 template <typename S>
-static int run_fields(lbm_ctx* c, double* const* outs) {
+static int run_fields(lbm_ctx* c, double* const* outs, int64_t first, int64_t count) {
     const ParamsOf<S> p = dev_params<typename Storage<S>::real>(c);
     for (int w = 0; w < 5; ++w) {
         if (!outs[w]) continue;
         CUDA_OR_FAIL(c, launch_field<S>(c->dev, c->cur, p, w, c->stream));
-        CUDA_OR_FAIL(c, cudaMemcpyAsync(outs[w], c->dev.staging, c->ncell * sizeof(double),
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(outs[w], c->dev.staging + first, count * sizeof(double),
                                         cudaMemcpyDeviceToHost, c->stream));
         int rc = wait_stream(c);
         if (rc != LBM_OK) return rc;
@@ -454,12 +454,19 @@ static int run_fields(lbm_ctx* c, double* const* outs) {
     return LBM_OK;
 }
 
+int lbm::fields_cells(lbm_ctx* c, double* const outs[5], int64_t first, int64_t count) {
+    if (!c || first < 0 || count < 0 || first + count > c->ncell)
+        return fail(c, LBM_EINVAL, "invalid cell range%s");
+    DeviceGuard g(c->device);
+    return with_storage(c->precision,
+                        [&](auto tag) { return run_fields<decltype(tag)>(c, outs, first, count); });
+}
+
 extern "C" int lbm_fields(lbm_ctx* c, double* rho, double* ux, double* uy, double* uz, double* T) {
     NvtxRange nvtx("lbm_fields");
     if (!c) return fail(c, LBM_EINVAL, "NULL context%s");
-    DeviceGuard g(c->device);
     double* outs[5] = {rho, ux, uy, uz, T};
-    return with_storage(c->precision, [&](auto tag) { return run_fields<decltype(tag)>(c, outs); });
+    return fields_cells(c, outs, 0, c->ncell);
 }
 
 extern "C" int lbm_nusselt(lbm_ctx* c, lbm_nu* out) {
@@ -499,17 +506,20 @@ extern "C" int lbm_residual(lbm_ctx* c, double* max_dT) {
     return LBM_OK;
 }
 
+// Cells [first, first + n) of every population between the current state and FP64 host
+// arrays whose population a starts at a * hs (queued on the context's stream).
 template <typename S>
-static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const double* gin) {
+static int transfer_cells_(lbm_ctx* c, double* f, double* g, const double* fin, const double* gin,
+                           int64_t first, int64_t n, int64_t hs) {
     using real = typename Storage<S>::real;
     const ParamsOf<S> p = dev_params<real>(c);
-    const int64_t n = c->ncell;
     const bool upload = fin || gin;
-    float* Tn = static_cast<float*>(c->dev.T[c->cur]);  // 16-bit forms only, else NULL
+    // 16-bit forms only, else NULL
+    float* Tn = c->dev.T[c->cur] ? static_cast<float*>(c->dev.T[c->cur]) + first : nullptr;
     if (upload && Storage<S>::deviation) {
         // the node temperatures the thermal deviations will refer to: T = sum_a g_a
         for (int a = 0; a < c->Q; ++a) {
-            CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dev.staging, gin + (int64_t)a * n, n * sizeof(double),
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dev.staging, gin + (int64_t)a * hs, n * sizeof(double),
                                             cudaMemcpyHostToDevice, c->stream));
             CUDA_OR_FAIL(c, launch_accumulate_T(Tn, c->dev.staging, n, a == 0, c->stream));
         }
@@ -520,15 +530,15 @@ static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const d
         // stored-value offset: flow w_a; thermal w^phi_a times the node temperature
         const float* Tplane = side == 1 ? Tn : nullptr;
         for (int a = 0; a < q; ++a) {
-            S* plane = dev + (int64_t)a * c->plane;
+            S* plane = dev + (int64_t)a * c->plane + first;
             const double offset = (double)(side == 0 ? p.wf[a] : p.wg[a]);
             if (upload) {  // host -> device
-                const double* src = (side == 0 ? fin : gin) + (int64_t)a * n;
+                const double* src = (side == 0 ? fin : gin) + (int64_t)a * hs;
                 CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dev.staging, src, n * sizeof(double),
                                                 cudaMemcpyHostToDevice, c->stream));
                 CUDA_OR_FAIL(c, launch_to_storage<S>(plane, c->dev.staging, n, offset, Tplane, c->stream));
             } else {  // device -> host
-                double* dst = (side == 0 ? f : g) + (int64_t)a * n;
+                double* dst = (side == 0 ? f : g) + (int64_t)a * hs;
                 CUDA_OR_FAIL(c, launch_to_double<S>(c->dev.staging, plane, n, offset, Tplane, c->stream));
                 CUDA_OR_FAIL(c, cudaMemcpyAsync(dst, c->dev.staging, n * sizeof(double),
                                                 cudaMemcpyDeviceToHost, c->stream));
@@ -537,11 +547,38 @@ static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const d
             // behind the conversion that last used it, so no host wait is needed here
         }
     }
-    if (upload) {
-        CUDA_OR_FAIL(c, launch_residual<S>(c->dev, c->cur, p, 0, c->stream));
+    return LBM_OK;
+}
+
+int lbm::transfer_cells(lbm_ctx* c, double* f, double* g, const double* fin, const double* gin,
+                        int64_t first, int64_t count, int64_t hstride) {
+    if (!c || first < 0 || count < 0 || first + count > c->ncell || hstride < count)
+        return fail(c, LBM_EINVAL, "invalid cell range%s");
+    DeviceGuard gd(c->device);
+    return with_storage(c->precision, [&](auto tag) {
+        return transfer_cells_<decltype(tag)>(c, f, g, fin, gin, first, count, hstride);
+    });
+}
+
+int lbm::transfer_done(lbm_ctx* c, bool uploaded) {
+    DeviceGuard gd(c->device);
+    if (uploaded) {  // the residual's snapshot of the new state
+        const int rc = with_storage(c->precision, [&](auto tag) {
+            using S = decltype(tag);
+            CUDA_OR_FAIL(c, launch_residual<S>(c->dev, c->cur, dev_params<typename Storage<S>::real>(c), 0,
+                                               c->stream));
+            return LBM_OK;
+        });
+        if (rc != LBM_OK) return rc;
         c->last_residual = -1.0;
     }
     return wait_stream(c);  // the host arrays (download) or sources (upload) are done with
+}
+
+template <typename S>
+static int transfer(lbm_ctx* c, double* f, double* g, const double* fin, const double* gin) {
+    const int rc = transfer_cells_<S>(c, f, g, fin, gin, 0, c->ncell, c->ncell);
+    return rc != LBM_OK ? rc : transfer_done(c, fin || gin);
 }
 
 extern "C" int lbm_get_populations(lbm_ctx* c, double* f, double* g) {

@@ -88,6 +88,18 @@ void destroy_context(lbm_ctx* c);
 int create_context(const lbm_grid* grid, int lattice, const lbm_params* params,
                    const lbm_options* opt, int64_t cell0, lbm_ctx** out);
 
+// FP64 host populations <-> cells [first, first + count) of the current state, population
+// a of the host side starting at a * hstride (download: f, g; upload: fin, gin).  Queued
+// on the context's stream; transfer_done ends a series of them (an upload with the
+// residual's snapshot) with a bounded wait.  lbm_get/set_populations are the whole range.
+int transfer_cells(lbm_ctx* c, double* f, double* g, const double* fin, const double* gin,
+                   int64_t first, int64_t count, int64_t hstride);
+int transfer_done(lbm_ctx* c, bool uploaded);
+
+// lbm_fields for cells [first, first + count): outs[w] (rho, ux, uy, uz, T; NULL = skip)
+// receive count values each.
+int fields_cells(lbm_ctx* c, double* const outs[5], int64_t first, int64_t count);
+
 // Bytes of the device arena of one context.
 size_t context_arena_bytes(const lbm_grid* g, int q, int precision);
 

@@ -398,41 +398,32 @@ extern "C" int lbm_slabs_residual(lbm_slabs* s, double* max_dT) {
     return LBM_OK;
 }
 
-// Populations: through each member's own FP64 transfer, then its owned planes copied to
-// (or all of its planes filled from) the whole-grid arrays.
+// Populations: each member's owned planes straight to (or, halo planes included, from)
+// the whole-grid arrays through its FP64 transfer of a cell range.  An upload takes the
+// slab's planes in runs of consecutive global planes (a halo across a periodic z face
+// starts a new run).
 static int slab_transfer(lbm_slabs* s, double* f, double* g, const double* fin, const double* gin) {
     const int64_t nxy = (int64_t)s->grid.nx * s->grid.ny;
     const int64_t N = nxy * s->grid.nz;
     for (int k = 0; k < s->nslabs; ++k) {
         lbm_ctx* c = s->m[k];
-        const int64_t n = c->ncell;
-        std::vector<double> fs, gs;
-        try {
-            fs.resize(15 * n);
-            gs.resize((size_t)s->Q * n);
-        } catch (...) {
-            return sfail(s, LBM_ENOMEM, "host allocation failed%s");
-        }
-        const int nzb = c->grid.nz;
+        int rc = LBM_OK;
         if (fin) {
-            for (int a = 0; a < 15 + s->Q; ++a) {
-                const double* src = a < 15 ? fin + a * N : gin + (a - 15) * N;
-                double* dst = a < 15 ? fs.data() + a * n : gs.data() + (a - 15) * n;
-                for (int z = 0; z < nzb; ++z)
-                    memcpy(dst + z * nxy, src + global_plane(s, k, z) * nxy, nxy * sizeof(double));
+            const int nzb = c->grid.nz;
+            for (int z = 0; z < nzb && rc == LBM_OK;) {
+                const int zg = global_plane(s, k, z);
+                int len = 1;
+                while (z + len < nzb && global_plane(s, k, z + len) == zg + len) ++len;
+                rc = transfer_cells(c, nullptr, nullptr, fin + zg * nxy, gin + zg * nxy, z * nxy,
+                                    len * nxy, N);
+                z += len;
             }
-            const int rc = lbm_set_populations(c, fs.data(), gs.data());
-            if (rc != LBM_OK) return sfail(s, rc, "slab upload failed: %s", c->err.c_str());
         } else {
-            const int rc = lbm_get_populations(c, fs.data(), gs.data());
-            if (rc != LBM_OK) return sfail(s, rc, "slab download failed: %s", c->err.c_str());
-            for (int a = 0; a < 15 + s->Q; ++a) {
-                const double* src = a < 15 ? fs.data() + a * n : gs.data() + (a - 15) * n;
-                double* dst = a < 15 ? f + a * N : g + (a - 15) * N;
-                memcpy(dst + (int64_t)s->z0[k] * nxy, src + (int64_t)s->hlo[k] * nxy,
-                       (int64_t)s->own[k] * nxy * sizeof(double));
-            }
+            rc = transfer_cells(c, f + (int64_t)s->z0[k] * nxy, g + (int64_t)s->z0[k] * nxy, nullptr,
+                                nullptr, (int64_t)s->hlo[k] * nxy, (int64_t)s->own[k] * nxy, N);
         }
+        if (rc == LBM_OK) rc = transfer_done(c, fin != nullptr);
+        if (rc != LBM_OK) return sfail(s, rc, "slab transfer failed: %s", c->err.c_str());
     }
     if (fin) s->last_residual = -1.0;
     return LBM_OK;
@@ -461,24 +452,10 @@ extern "C" int lbm_slabs_fields(lbm_slabs* s, double* rho, double* ux, double* u
     double* outs[5] = {rho, ux, uy, uz, T};
     for (int k = 0; k < s->nslabs; ++k) {
         lbm_ctx* c = s->m[k];
-        std::vector<double> tmp[5];
-        double* p[5];
-        for (int i = 0; i < 5; ++i) {
-            if (outs[i]) {
-                try {
-                    tmp[i].resize(c->ncell);
-                } catch (...) {
-                    return sfail(s, LBM_ENOMEM, "host allocation failed%s");
-                }
-            }
-            p[i] = outs[i] ? tmp[i].data() : nullptr;
-        }
-        const int rc = lbm_fields(c, p[0], p[1], p[2], p[3], p[4]);
+        double* mine[5];
+        for (int i = 0; i < 5; ++i) mine[i] = outs[i] ? outs[i] + (int64_t)s->z0[k] * nxy : nullptr;
+        const int rc = fields_cells(c, mine, (int64_t)s->hlo[k] * nxy, (int64_t)s->own[k] * nxy);
         if (rc != LBM_OK) return sfail(s, rc, "slab fields failed: %s", c->err.c_str());
-        for (int i = 0; i < 5; ++i)
-            if (outs[i])
-                memcpy(outs[i] + (int64_t)s->z0[k] * nxy, p[i] + (int64_t)s->hlo[k] * nxy,
-                       (int64_t)s->own[k] * nxy * sizeof(double));
     }
     return LBM_OK;
 }
