@@ -82,7 +82,9 @@ int lbm_net_gradients(lbm_net* net, int batch, const float* scalars, const float
                       double* loss);
 /* The Adam learning rate of the following updates (> 0). */
 int lbm_net_set_lr(lbm_net* net, float lr);
-/* lbm_net_gradients followed by one Adam update of every parameter. */
+/* lbm_net_gradients followed by one Adam update of every parameter.  Gradients and the
+ * loss are summed in a fixed order (no floating-point atomics), so the same seed, data and
+ * sequence of calls give bitwise identical parameters and losses on every run. */
 int lbm_net_train_step(lbm_net* net, int batch, const float* scalars, const float* targets,
                        double* loss);
 const char* lbm_net_last_error(const lbm_net* net);
