@@ -491,19 +491,55 @@ def net_variant():
     return out
 
 
-def cpu_baseline(sample_steps=3, q=15):
-    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the same
-    workload (the 128^3 Ra = 1e5 cavity, a few steps from its initial state)."""
-    import oracle
-    p = oracle.Problem.cavity(N_GRID, RA, Pr=PR, Ma=U0 * math.sqrt(3.0), q_g=q)
+def cpu_model():
+    """The host CPU's model name (lscpu; /proc/cpuinfo as a fallback)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_leg(oracle, n, Ra, steps, threads, q=15):
+    """One timed oracle run of the cavity at n^3 from its seeded initial state."""
+    p = oracle.Problem.cavity(n, Ra, Pr=PR, Ma=U0 * math.sqrt(3.0), q_g=q)
     F, G = p.init(seed=1, noise_amp=1e-6)
-    F, G = p.step(F, G)  # first-touch / page-in outside the timing
+    oracle.set_num_threads(threads)
+    F, G = p.step(F, G)  # first touch / page-in outside the timing
     t0 = time.perf_counter()
-    F, G = p.run(F, G, sample_steps)
+    p.run(F, G, steps)
     dt = time.perf_counter() - t0
-    return {"value": N_GRID ** 3 * sample_steps / dt / 1e6, "unit": "MLUPS",
-            "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{N_GRID}^3 cavity Ra=1e5, D3Q15+D3Q{q}, {sample_steps} FP64 steps"}
+    return {"grid": n, "Ra": Ra, "steps": steps, "threads": threads,
+            "seconds": round(dt, 3), "mlups": round(n ** 3 * steps / dt / 1e6, 3)}
+
+
+def cpu_baseline():
+    """The FP64 oracle, as it stands, on the host cores: the 32^3 Ra = 1e3 cavity for
+    300 steps and the 64^3 one for 50 steps, each single-threaded and on every core, and
+    the bench's own workload (128^3, Ra = 1e5) for 3 steps on every core.  The line's
+    value is the 128^3 figure (the same workload as the GPU line)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    legs = []
+    for n, Ra, steps in ((32, 1e3, 300), (64, 1e3, 50)):
+        for threads in (1, cores):
+            legs.append(_oracle_leg(oracle, n, Ra, steps, threads))
+    main = _oracle_leg(oracle, N_GRID, RA, 3, cores)
+    oracle.set_num_threads(cores)
+    return {"value": main["mlups"], "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": cores,
+            "sample": f"{N_GRID}^3 cavity Ra=1e5, D3Q15+D3Q15, 3 FP64 steps on {cores} threads",
+            "legs": legs}
 
 
 def gpu_arm(args):
@@ -707,8 +743,7 @@ def main(argv=None):
     ap.add_argument("--ref-budget", type=float, default=90.0,
                     help="seconds the reference arm spends on warm-up + timed steps")
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of step_cavity_kernel<float,15>
-    # at 128^3 (ncu, profiles/step_cavity_kernel_q15_128cubed.md); to be retaken whenever
-    # that kernel changes
+    # at 128^3, from one ncu capture; to be retaken whenever that kernel changes
     ap.add_argument("--traffic-q15", type=float, default=456.4e6,
                     help="ncu DRAM bytes per launch of the FP32 D3Q15 step kernel at 128^3")
     ap.add_argument("--traffic-q7", type=float, default=None)

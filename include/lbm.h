@@ -213,6 +213,14 @@ int lbm_checkpoint_info(const char* path, lbm_grid* grid, int* lattice, int* pre
                         lbm_params* params, int64_t* steps);
 int lbm_restore(lbm_ctx* ctx, const char* path);
 
+/* Bound, in seconds (> 0), of every later host wait of this context for the GPU (the
+ * lbm_options.timeout_s given at creation until changed).  A wait that runs out returns
+ * LBM_ETIMEOUT and leaves the queued work running: the context stays usable, and a later
+ * call (lbm_synchronize, or any call that reads results) waits again.  Every call that
+ * returns data in caller memory first waits for the stream's earlier work under this
+ * bound, then copies.  LBM_EINVAL for a NULL context or timeout_s <= 0. */
+int lbm_set_timeout(lbm_ctx* ctx, double timeout_s);
+
 /* Parameters in use, step counter, last error message, stream wait, destruction. */
 int lbm_get_params(const lbm_ctx* ctx, lbm_params* out);
 int64_t lbm_steps_done(const lbm_ctx* ctx);
@@ -237,7 +245,9 @@ void lbm_destroy(lbm_ctx* ctx);
  * loading the library holds until the process exits; it bounds the face count:
  * ny*nz <= 262144 (1024 blocks of 256 face cells), larger grids give LBM_EINVAL.  The
  * first call on each device, with that device current, looks up the array's device
- * address (a one-time set-up); make that first call before any stream capture.  Every
+ * address (a one-time set-up); make that first call before any stream capture.  That
+ * address is cached for the life of the process: do not call this entry point after a
+ * cudaDeviceReset of the device in the same process.  Every
  * call overwrites the array's partial sums before reading them, so nothing carries over
  * from the previous call; calls that overlap on the GPU (other streams, other threads)
  * share the array and race.  Errors: LBM_EINVAL (NULL pointer, sizes, lattice,

@@ -35,6 +35,16 @@ int lbm_nn_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, voi
                      int64_t ldc, int M, int N, int K, int out_mode, int splits,
                      void* cuda_stream);
 
+/* Diagnostic of the bounded waits inside the tensor-core kernels (the paper has no
+ * counterpart).  Launches the GEMM kernel on one 128 x 32 tile with its operand loads
+ * withheld, so that the MMA thread's wait for its first operand stage can only run out
+ * (after 10 ms, instead of the 2 s every real launch allows).  The kernel then records
+ * the timeout in the device's error word, issues no MMA, frees its tensor memory and
+ * returns; the call reads and clears the word.  Returns LBM_ETIMEOUT when that path
+ * worked (later GEMMs run normally), LBM_ECUDA otherwise.  Nothing faults or hangs:
+ * this is how the timeout path is tested on a shared GPU. */
+int lbm_nn_gemm_timeout_probe(void* cuda_stream);
+
 /* ---- the network ------------------------------------------------------------------- */
 
 typedef struct lbm_net lbm_net;
@@ -82,12 +92,33 @@ int lbm_net_gradients(lbm_net* net, int batch, const float* scalars, const float
                       double* loss);
 /* The Adam learning rate of the following updates (> 0). */
 int lbm_net_set_lr(lbm_net* net, float lr);
-/* lbm_net_gradients followed by one Adam update of every parameter.  Gradients and the
- * loss are summed in a fixed order (no floating-point atomics), so the same seed, data and
+/* lbm_net_gradients followed by one Adam update of every parameter.  Every gradient and
+ * the loss is summed in a fixed order and every gradient element is written by plain
+ * stores (no floating-point atomics anywhere in the network), so the same seed, data and
  * sequence of calls give bitwise identical parameters and losses on every run. */
 int lbm_net_train_step(lbm_net* net, int batch, const float* scalars, const float* targets,
                        double* loss);
 const char* lbm_net_last_error(const lbm_net* net);
+
+/* Stored tensors of the last lbm_net_forward / lbm_net_gradients / lbm_net_train_step call,
+ * for inspection (the per-element checks of the kernels use them).  Activations, voxel-major
+ * [sample][voxel][channel] at their level's grid (n, n/2 or n/4): the input features X0,
+ * the ReLU outputs A0 S1 | A2 S2 | A4 A5 A6 | A7 A8 | A9 A10 of the eleven convolutions,
+ * the pooled P1, P2 and the concatenations C2 = [up(A6), S2], C1 = [up(A8), S1]: BF16
+ * (2 bytes each, as stored).  The outputs OUT [sample][n^3][4] and, after a gradient call,
+ * the gradients of the loss with respect to OUT and each activation (the D_* ids): FP32.
+ * Copies the first `batch` samples (count = batch * voxels * channels elements) into
+ * caller-owned host memory, after a bounded wait.  LBM_EINVAL for an unknown id, a batch
+ * outside 1..max_batch or a wrong count. */
+enum {
+    LBM_NET_X0 = 0, LBM_NET_A0, LBM_NET_S1, LBM_NET_P1, LBM_NET_A2, LBM_NET_S2, LBM_NET_P2,
+    LBM_NET_A4, LBM_NET_A5, LBM_NET_A6, LBM_NET_C2, LBM_NET_A7, LBM_NET_A8, LBM_NET_C1,
+    LBM_NET_A9, LBM_NET_A10, LBM_NET_OUT,
+    LBM_NET_D_A10, LBM_NET_D_A9, LBM_NET_D_C1, LBM_NET_D_S1, LBM_NET_D_A8, LBM_NET_D_A7,
+    LBM_NET_D_C2, LBM_NET_D_S2, LBM_NET_D_A6, LBM_NET_D_A5, LBM_NET_D_A4, LBM_NET_D_P2,
+    LBM_NET_D_A2, LBM_NET_D_P1, LBM_NET_D_A0, LBM_NET_D_OUT, LBM_NET_TENSORS
+};
+int lbm_net_tensor(lbm_net* net, int which, int batch, void* host, int64_t count);
 
 /* ---- the bridge to the solver ------------------------------------------------------- */
 

@@ -71,6 +71,8 @@ def lib():
         L.orc_weights_thermal.argtypes = [ctypes.c_int, ctypes.c_double, _D]
         L.orc_velocities.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
         L.orc_opposite.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
+        L.orc_set_num_threads.restype = None
     return _lib
 
 
@@ -289,3 +291,8 @@ class Problem:
 
 def num_threads():
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n):
+    """Threads of the oracle's OpenMP loop (results do not depend on it)."""
+    lib().orc_set_num_threads(int(n))

@@ -729,3 +729,13 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads of the OpenMP loop over z-planes in orc_step (1 = serial).  The result does not
+ * depend on the count: every node is computed independently. */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

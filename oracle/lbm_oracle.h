@@ -83,6 +83,7 @@ void orc_fields(const orc_problem* p, const double* F, const double* G,
 int  orc_nusselt(const orc_problem* p, const double* F, const double* G, orc_nu* out);
 uint64_t orc_splitmix64(uint64_t x);
 int  orc_num_threads(void);
+void orc_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

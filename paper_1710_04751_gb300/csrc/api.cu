@@ -446,9 +446,13 @@ static int run_fields(lbm_ctx* c, double* const* outs, int64_t first, int64_t co
     for (int w = 0; w < 5; ++w) {
         if (!outs[w]) continue;
         CUDA_OR_FAIL(c, launch_field<S>(c->dev, c->cur, p, w, c->stream));
+        // the bounded wait comes first: a copy into pageable caller memory would block the
+        // host until every earlier kernel on the stream has finished, with no time limit
+        int rc = wait_stream(c);
+        if (rc != LBM_OK) return rc;
         CUDA_OR_FAIL(c, cudaMemcpyAsync(outs[w], c->dev.staging + first, count * sizeof(double),
                                         cudaMemcpyDeviceToHost, c->stream));
-        int rc = wait_stream(c);
+        rc = wait_stream(c);
         if (rc != LBM_OK) return rc;
     }
     return LBM_OK;
@@ -481,10 +485,13 @@ extern "C" int lbm_nusselt(lbm_ctx* c, lbm_nu* out) {
         return LBM_OK;
     });
     if (lrc != LBM_OK) return lrc;
+    // bounded wait before the copy into host stack memory (see run_fields)
+    int rc = wait_stream(c);
+    if (rc != LBM_OK) return rc;
     double r[kResultDoubles];
     CUDA_OR_FAIL(c, cudaMemcpyAsync(r, c->dev.result, 11 * sizeof(double), cudaMemcpyDeviceToHost,
                                     c->stream));
-    int rc = wait_stream(c);
+    rc = wait_stream(c);
     if (rc != LBM_OK) return rc;
     out->hot_wall_mean = r[0];
     out->cold_wall_mean = r[1];
@@ -523,6 +530,13 @@ static int transfer_cells_(lbm_ctx* c, double* f, double* g, const double* fin, 
                                             cudaMemcpyHostToDevice, c->stream));
             CUDA_OR_FAIL(c, launch_accumulate_T(Tn, c->dev.staging, n, a == 0, c->stream));
         }
+    }
+    if (!upload) {
+        // every earlier kernel (the steps) finishes under the bounded wait before the first
+        // copy into caller memory, which would otherwise block the host without a limit;
+        // what follows is one short conversion kernel per plane
+        const int rc = wait_stream(c);
+        if (rc != LBM_OK) return rc;
     }
     for (int side = 0; side < 2; ++side) {
         const int q = side == 0 ? 15 : c->Q;
@@ -607,6 +621,10 @@ static int transfer_native(lbm_ctx* c, void* f, void* g, const void* fin, const 
     const bool upload = fin || gin;
     const size_t es = c->precision == LBM_FP64 ? 8 : 4;
     const size_t bytes = (size_t)c->ncell * es;
+    if (!upload) {  // bounded wait before copies into caller memory (see transfer_cells_)
+        const int rc = wait_stream(c);
+        if (rc != LBM_OK) return rc;
+    }
     for (int side = 0; side < 2; ++side) {
         const int q = side == 0 ? 15 : c->Q;
         char* dev = static_cast<char*>(side == 0 ? c->dev.F[c->cur] : c->dev.G[c->cur]);
@@ -792,6 +810,12 @@ extern "C" int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; 
 
 extern "C" const char* lbm_last_error(const lbm_ctx* c) {
     return c ? c->err.c_str() : g_err.c_str();
+}
+
+extern "C" int lbm_set_timeout(lbm_ctx* c, double timeout_s) {
+    if (!c || !(timeout_s > 0)) return fail(c, LBM_EINVAL, "NULL context or timeout <= 0%s");
+    c->opt.timeout_s = timeout_s;
+    return LBM_OK;
 }
 
 extern "C" int lbm_synchronize(lbm_ctx* c) {

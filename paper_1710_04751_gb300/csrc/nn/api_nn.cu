@@ -12,6 +12,11 @@ namespace {
 // Per-device error word the network kernels write on a timeout.
 __device__ int nn_error_word;
 
+// Operand and output of the timeout diagnostic (nothing reads the operand; nothing is
+// stored to the output).
+__device__ __align__(128) __nv_bfloat16 nn_probe_operand[128 * 64];
+__device__ __align__(128) float nn_probe_out[128 * 32];
+
 int* error_word() {
     static int* ptr[64] = {};
     static std::mutex mu;
@@ -60,4 +65,23 @@ extern "C" int lbm_nn_gemm_bf16(const void* A, int64_t lda, const void* B, int64
         return record_error(nullptr, LBM_EINVAL, "invalid GEMM shape, stride, alignment or mode%s");
     if (e != cudaSuccess) return record_error(nullptr, LBM_ECUDA, "GEMM launch failed: %s", cudaGetErrorString(e));
     return finish(st, err);
+}
+
+extern "C" int lbm_nn_gemm_timeout_probe(void* cuda_stream) {
+    int* err = error_word();
+    if (!err) return record_error(nullptr, LBM_ECUDA, "no CUDA device%s");
+    void* op = nullptr;
+    void* out = nullptr;
+    if (cudaGetSymbolAddress(&op, nn_probe_operand) != cudaSuccess ||
+        cudaGetSymbolAddress(&out, nn_probe_out) != cudaSuccess)
+        return record_error(nullptr, LBM_ECUDA, "cannot address the diagnostic buffers%s");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // earlier work on the stream must not be mistaken for the probe's own timeout
+    int rc = finish(st, err);
+    if (rc != LBM_OK) return rc;
+    const cudaError_t e = nn::gemm_timeout_probe(static_cast<const __nv_bfloat16*>(op),
+                                                 static_cast<float*>(out), err, st);
+    if (e != cudaSuccess)
+        return record_error(nullptr, LBM_ECUDA, "probe launch failed: %s", cudaGetErrorString(e));
+    return finish(st, err);  // LBM_ETIMEOUT when the bounded wait ran out as intended
 }

@@ -42,6 +42,8 @@ struct GemmArgs {
     long long ldc;
     int* err;
     int vec;       // C and its rows are 16-byte aligned: whole 16-column chunks use vector stores
+    unsigned long long wait_ns;  // bound of the operand-ring waits (2 s)
+    int withhold_loads;  // diagnostic only: issue no operand loads, so the ring wait runs out
 };
 
 template <int BN>
@@ -82,11 +84,11 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t tmem = *tmem_slot;
 
     int issued = 0;  // producer: stages loaded
-    if (nkb > 0 && warp == 0 && lane == 0) {
+    if (nkb > 0 && warp == 0 && lane == 0 && !args.withhold_loads) {
         for (int i = 0; i < nkb; ++i) {
             const int s = i % STAGES;
             const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (i >= STAGES && !mbar_wait(empty + s, ph ^ 1u, args.err, 1, &failed)) {
+            if (i >= STAGES && !mbar_wait(empty + s, ph ^ 1u, args.err, 1, &failed, args.wait_ns)) {
                 failed = 1;
                 break;
             }
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(128, 1)
         for (int i = 0; i < nkb; ++i) {
             const int s = i % STAGES;
             const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (failed || !mbar_wait(full + s, ph, args.err, 2, &failed)) {
+            if (failed || !mbar_wait(full + s, ph, args.err, 2, &failed, args.wait_ns)) {
                 failed = 1;
                 break;
             }
@@ -258,13 +260,26 @@ cudaError_t gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16
         return cudaErrorInvalidValue;
     const long long esz = out_mode == GEMM_BF16 ? 2 : 4;
     const int vec = ((uintptr_t)C % 16 == 0) && ((ldc * esz) % 16 == 0);
-    GemmArgs a{M, N, K, per, out_mode, C, ldc, err, vec};
+    GemmArgs a{M, N, K, per, out_mode, C, ldc, err, vec, 2000000000ull, 0};
     switch (BN) {
     case 32: return launch<32>(ta, tb, a, splits, st);
     case 64: return launch<64>(ta, tb, a, splits, st);
     case 128: return launch<128>(ta, tb, a, splits, st);
     default: return launch<256>(ta, tb, a, splits, st);
     }
+}
+
+// Diagnostic of the bounded waits: one 128 x 32 tile over one K block whose operand loads
+// are withheld, so the MMA thread's wait for the first stage can only run out (after
+// 10 ms).  The kernel then records code 2 in *err, issues no MMA, lets nothing drain
+// (nothing was loaded), frees its TMEM and returns.  `operand` is any 16-byte aligned
+// device buffer of 128 x 64 BF16 values; the tensor maps point at it, nothing reads it.
+cudaError_t gemm_timeout_probe(const __nv_bfloat16* operand, float* C, int* err, cudaStream_t st) {
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, operand, 128, 64, 64, BM) || !make_map(&tb, operand, 32, 64, 64, 32))
+        return cudaErrorInvalidValue;
+    GemmArgs a{128, 32, 64, 1, GEMM_F32, C, 32, err, 0, 10000000ull, 1};
+    return launch<32>(ta, tb, a, 1, st);
 }
 
 // C[r][c] += ws[0][r][c] + ws[1][r][c] + ... in split order (slices of M * ldc floats).

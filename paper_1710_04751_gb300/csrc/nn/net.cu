@@ -227,9 +227,9 @@ int conv_fwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, __nv_bfloat16* A)
 }
 
 // Gradients of layer l given dA (FP32, gradient of its ReLU output A): dW^T and db are
-// accumulated; dX (input gradient) written or added when non-NULL.
+// accumulated; dX (input gradient) is written (plain stores, no atomics) when non-NULL.
 int conv_bwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, const __nv_bfloat16* A,
-             const float* dA, float* dX, int accumulate) {
+             const float* dA, float* dX) {
     Conv& k = N->conv[l];
     const int n = N->n >> k.level;
     const int64_t M = (int64_t)B * N->V[k.level];
@@ -243,7 +243,7 @@ int conv_bwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, const __nv_bfloat
     if (dX) {  // dX = im2col(dZ) Wf^T (the xcol scratch is free again)
         NET_CUDA(N, im2col(N->dZ, B, n, k.cout, k.Kpf, N->xcol, st));
         NET_CUDA(N, gemm_bf16(N->xcol, k.Kpf, k.Wf, k.Kpf, dX, k.cin, (int)M, k.cin, k.Kpf,
-                              accumulate ? GEMM_F32_ATOMIC : GEMM_F32, 1, N->err, st));
+                              GEMM_F32, 1, N->err, st));
     }
     return LBM_OK;
 }
@@ -295,23 +295,23 @@ int backward(lbm_net* N, int B, const float* target) {
     NET_CUDA(N, cudaMemsetAsync(N->loss, 0, 8, st));
     NET_CUDA(N, mse(N->out, target, M0 * 4, N->dOut, N->loss, N->partd, st));
     NET_CUDA(N, head_bwd(N->dOut, N->A10, M0, c1, N->Wh, N->dA10, N->gWh, N->gbh, N->part, st));
-    NET_RC(conv_bwd(N, 10, N->A9, B, N->A10, N->dA10, N->dA9, 0));
-    NET_RC(conv_bwd(N, 9, N->C1, B, N->A9, N->dA9, N->dC1, 0));
+    NET_RC(conv_bwd(N, 10, N->A9, B, N->A10, N->dA10, N->dA9));
+    NET_RC(conv_bwd(N, 9, N->C1, B, N->A9, N->dA9, N->dC1));
     NET_CUDA(N, upsample_bwd(N->dC1, c2 + c1, 0, B, n, c2, N->dA8, st));
     NET_CUDA(N, slice_grad(N->dC1, c2 + c1, c2, M0, c1, N->dS1, 0, st));
-    NET_RC(conv_bwd(N, 8, N->A7, B, N->A8, N->dA8, N->dA7, 0));
-    NET_RC(conv_bwd(N, 7, N->C2, B, N->A7, N->dA7, N->dC2, 0));
+    NET_RC(conv_bwd(N, 8, N->A7, B, N->A8, N->dA8, N->dA7));
+    NET_RC(conv_bwd(N, 7, N->C2, B, N->A7, N->dA7, N->dC2));
     NET_CUDA(N, upsample_bwd(N->dC2, c3 + c2, 0, B, n / 2, c3, N->dA6, st));
     NET_CUDA(N, slice_grad(N->dC2, c3 + c2, c3, M1, c2, N->dS2, 0, st));
-    NET_RC(conv_bwd(N, 6, N->A5, B, N->A6, N->dA6, N->dA5, 0));
-    NET_RC(conv_bwd(N, 5, N->A4, B, N->A5, N->dA5, N->dA4, 0));
-    NET_RC(conv_bwd(N, 4, N->P2, B, N->A4, N->dA4, N->dP2, 0));
+    NET_RC(conv_bwd(N, 6, N->A5, B, N->A6, N->dA6, N->dA5));
+    NET_RC(conv_bwd(N, 5, N->A4, B, N->A5, N->dA5, N->dA4));
+    NET_RC(conv_bwd(N, 4, N->P2, B, N->A4, N->dA4, N->dP2));
     NET_CUDA(N, avgpool_bwd(N->dP2, B, n / 2, c2, N->dS2, 1, st));
-    NET_RC(conv_bwd(N, 3, N->A2, B, N->S2, N->dS2, N->dA2, 0));
-    NET_RC(conv_bwd(N, 2, N->P1, B, N->A2, N->dA2, N->dP1, 0));
+    NET_RC(conv_bwd(N, 3, N->A2, B, N->S2, N->dS2, N->dA2));
+    NET_RC(conv_bwd(N, 2, N->P1, B, N->A2, N->dA2, N->dP1));
     NET_CUDA(N, avgpool_bwd(N->dP1, B, n, c1, N->dS1, 1, st));
-    NET_RC(conv_bwd(N, 1, N->A0, B, N->S1, N->dS1, N->dA0, 0));
-    NET_RC(conv_bwd(N, 0, N->X0, B, N->A0, N->dA0, nullptr, 0));
+    NET_RC(conv_bwd(N, 1, N->A0, B, N->S1, N->dS1, N->dA0));
+    NET_RC(conv_bwd(N, 0, N->X0, B, N->A0, N->dA0, nullptr));
     for (int l = 0; l < kLayers; ++l) {
         Conv& k = N->conv[l];
         NET_CUDA(N, unpack_grad(k.dWT, k.cout, k.K27, k.gW, st));
@@ -344,6 +344,15 @@ int wait_net(lbm_net* N) {
         cudaMemset(N->err, 0, sizeof(int));
         return nfail(N, LBM_ETIMEOUT, "a wait inside a tensor-core kernel timed out%s");
     }
+    return LBM_OK;
+}
+
+// The bounded wait (and the kernels' error word) first, then the loss into caller memory:
+// a copy into pageable memory issued before the wait would block without a time limit.
+int finish_with_loss(lbm_net* N, double* loss) {
+    int rc = wait_net(N);
+    if (rc != LBM_OK || !loss) return rc;
+    NET_CUDA(N, cudaMemcpy(loss, N->loss, 8, cudaMemcpyDeviceToHost));
     return LBM_OK;
 }
 
@@ -531,8 +540,7 @@ extern "C" int lbm_net_gradients(lbm_net* N, int batch, const float* scalars, co
     NET_RC(upload_scalars(N, batch, scalars));
     NET_RC(forward(N, batch));
     NET_RC(backward(N, batch, targets));
-    if (loss) NET_CUDA(N, cudaMemcpyAsync(loss, N->loss, 8, cudaMemcpyDeviceToHost, N->stream));
-    return wait_net(N);
+    return finish_with_loss(N, loss);
 }
 
 extern "C" int lbm_net_train_step(lbm_net* N, int batch, const float* scalars, const float* targets,
@@ -542,8 +550,7 @@ extern "C" int lbm_net_train_step(lbm_net* N, int batch, const float* scalars, c
     NET_RC(forward(N, batch));
     NET_RC(backward(N, batch, targets));
     NET_RC(update(N));
-    if (loss) NET_CUDA(N, cudaMemcpyAsync(loss, N->loss, 8, cudaMemcpyDeviceToHost, N->stream));
-    return wait_net(N);
+    return finish_with_loss(N, loss);
 }
 
 extern "C" int lbm_net_set_lr(lbm_net* N, float lr) {
@@ -560,4 +567,29 @@ extern "C" void lbm_net_encode(double Ra, double Pr, float* out2) {
 
 extern "C" const char* lbm_net_last_error(const lbm_net* N) {
     return N ? N->msg.c_str() : lbm_last_error(nullptr);
+}
+
+extern "C" int lbm_net_tensor(lbm_net* N, int which, int batch, void* host, int64_t count) {
+    if (!N || !host || batch < 1 || batch > N->B) return nfail(N, LBM_EINVAL, "NULL argument or batch outside 1..max_batch%s");
+    const int c1 = N->cfg.c1, c2 = N->cfg.c2, c3 = N->cfg.c3;
+    struct T { const void* p; int level, channels, bytes; };
+    const T t[LBM_NET_TENSORS] = {
+        {N->X0, 0, 4, 2}, {N->A0, 0, c1, 2}, {N->S1, 0, c1, 2}, {N->P1, 1, c1, 2},
+        {N->A2, 1, c2, 2}, {N->S2, 1, c2, 2}, {N->P2, 2, c2, 2}, {N->A4, 2, c3, 2},
+        {N->A5, 2, c3, 2}, {N->A6, 2, c3, 2}, {N->C2, 1, c3 + c2, 2}, {N->A7, 1, c2, 2},
+        {N->A8, 1, c2, 2}, {N->C1, 0, c2 + c1, 2}, {N->A9, 0, c1, 2}, {N->A10, 0, c1, 2},
+        {N->out, 0, 4, 4},
+        {N->dA10, 0, c1, 4}, {N->dA9, 0, c1, 4}, {N->dC1, 0, c2 + c1, 4}, {N->dS1, 0, c1, 4},
+        {N->dA8, 1, c2, 4}, {N->dA7, 1, c2, 4}, {N->dC2, 1, c3 + c2, 4}, {N->dS2, 1, c2, 4},
+        {N->dA6, 2, c3, 4}, {N->dA5, 2, c3, 4}, {N->dA4, 2, c3, 4}, {N->dP2, 2, c2, 4},
+        {N->dA2, 1, c2, 4}, {N->dP1, 1, c1, 4}, {N->dA0, 0, c1, 4}, {N->dOut, 0, 4, 4},
+    };
+    if (which < 0 || which >= LBM_NET_TENSORS) return nfail(N, LBM_EINVAL, "unknown tensor id%s");
+    const T& d = t[which];
+    const int64_t elems = (int64_t)batch * N->V[d.level] * d.channels;
+    if (count != elems) return nfail(N, LBM_EINVAL, "count differs from batch * voxels * channels%s");
+    int rc = wait_net(N);  // bounded, before the copy into caller memory
+    if (rc != LBM_OK) return rc;
+    NET_CUDA(N, cudaMemcpy(host, d.p, (size_t)elems * d.bytes, cudaMemcpyDeviceToHost));
+    return LBM_OK;
 }

@@ -27,6 +27,10 @@ cudaError_t gemm_bf16_add_splitk(const __nv_bfloat16* A, long long lda, const __
                                  int splits, float* ws, size_t ws_floats, int* err, cudaStream_t st);
 size_t gemm_splitk_floats(int M, long long ldc, int K, int splits);
 
+// Diagnostic: the GEMM kernel on one tile with its operand loads withheld, so that its
+// bounded wait runs out (10 ms) and it records a timeout in *err (see gemm.cu).
+cudaError_t gemm_timeout_probe(const __nv_bfloat16* operand, float* C, int* err, cudaStream_t st);
+
 }  // namespace nn
 }  // namespace lbm
 

@@ -14,6 +14,9 @@
 // the array's name to a kernel (in host code that name is only a host-side stand-in):
 // its device address is looked up once per device with cudaGetSymbolAddress, on the
 // first call made with that device current, and that pointer is what the kernels get.
+// The cached address belongs to the device's primary context: a caller that resets the
+// device (cudaDeviceReset) must not use this entry point in the same process afterwards,
+// since the module, and with it the array, is loaded again at another address.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -149,13 +152,17 @@ extern "C" int lbm_nusselt_noalloc(const void* f_dev, const void* g_dev, int64_t
                                        blocks, partials, result, st);
     }
     if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
-    double r[11];
-    e = cudaMemcpyAsync(r, result, sizeof r, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
+    // The bounded wait comes before the copy: a device-to-host copy into pageable memory
+    // (the stack array below) returns only once every earlier kernel on the stream has
+    // finished, so issued first it would wait without any time limit.
     bool timed_out = false;
     e = wait_polling(st, 600.0, &timed_out);
     if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
     if (timed_out) return fail(LBM_ETIMEOUT, "timed out waiting for the GPU");
+    double r[11];  // the stream is idle now: this copy is all that is left to wait for
+    e = cudaMemcpyAsync(r, result, sizeof r, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
     out->hot_wall_mean = r[0];
     out->cold_wall_mean = r[1];
     out->mid_mean = r[2];

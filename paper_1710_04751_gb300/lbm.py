@@ -26,7 +26,7 @@ EXPORTS = (
     "lbm_get_populations", "lbm_set_populations", "lbm_get_params", "lbm_steps_done",
     "lbm_last_error", "lbm_synchronize", "lbm_destroy", "lbm_nusselt_noalloc", "lbm_set_fields",
     "lbm_init_fields", "lbm_save", "lbm_checkpoint_info", "lbm_restore",
-    "lbm_get_populations_native", "lbm_set_populations_native",
+    "lbm_get_populations_native", "lbm_set_populations_native", "lbm_set_timeout",
 )
 
 
@@ -118,6 +118,7 @@ def load(build_if_missing=True):
     L.lbm_last_error.argtypes = [ctypes.c_void_p]
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_synchronize.argtypes = [ctypes.c_void_p]
+    L.lbm_set_timeout.argtypes = [ctypes.c_void_p, ctypes.c_double]
     L.lbm_destroy.argtypes = [ctypes.c_void_p]
     L.lbm_destroy.restype = None
     L.lbm_get_populations_native.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -369,6 +370,10 @@ class LBM:
 
     def synchronize(self):
         self._check(self._L.lbm_synchronize(self._ctx))
+
+    def set_timeout(self, seconds):
+        """Bound of every later host wait for the GPU (lbm_set_timeout)."""
+        self._check(self._L.lbm_set_timeout(self._ctx, float(seconds)))
 
     @classmethod
     def _view(cls, handle, owner):

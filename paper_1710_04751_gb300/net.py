@@ -12,8 +12,14 @@ EXPORTS = (
     "lbm_nn_gemm_bf16", "lbm_net_default_config", "lbm_net_create", "lbm_net_destroy",
     "lbm_net_param_count", "lbm_net_encode", "lbm_net_get_params", "lbm_net_set_params",
     "lbm_net_forward", "lbm_net_gradients", "lbm_net_train_step", "lbm_net_last_error",
-    "lbm_net_targets", "lbm_net_warm_start", "lbm_net_set_lr",
+    "lbm_net_targets", "lbm_net_warm_start", "lbm_net_set_lr", "lbm_nn_gemm_timeout_probe",
+    "lbm_net_tensor",
 )
+
+# Stored tensors (lbm_net_tensor ids): BF16 activations, then FP32 outputs and gradients.
+TENSORS = ("X0", "A0", "S1", "P1", "A2", "S2", "P2", "A4", "A5", "A6", "C2", "A7", "A8", "C1",
+           "A9", "A10", "OUT", "D_A10", "D_A9", "D_C1", "D_S1", "D_A8", "D_A7", "D_C2", "D_S2",
+           "D_A6", "D_A5", "D_A4", "D_P2", "D_A2", "D_P1", "D_A0", "D_OUT")
 
 
 class NetConfig(ctypes.Structure):
@@ -52,6 +58,8 @@ def _lib():
     L.lbm_net_targets.argtypes = [vp, vp]
     L.lbm_net_warm_start.argtypes = [vp, vp, i32, i32]
     L.lbm_net_set_lr.argtypes = [vp, ctypes.c_float]
+    L.lbm_nn_gemm_timeout_probe.argtypes = [vp]
+    L.lbm_net_tensor.argtypes = [vp, i32, i32, vp, i64]
     _bound = True
     return L
 
@@ -74,6 +82,15 @@ def gemm_bf16(A, B, C, out_mode=GEMM_F32, splits=1, K=None):
     _check(_lib().lbm_nn_gemm_bf16(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
                                    C.data_ptr(), C.stride(0), M, N, K, out_mode, splits,
                                    _stream(C)))
+
+
+def gemm_timeout_probe(stream=None):
+    """Run the GEMM kernel with its operand loads withheld so that its bounded wait runs
+    out (lbm_nn_gemm_timeout_probe); returns the C status (LBM_ETIMEOUT when the timeout
+    path works)."""
+    import torch
+    st = torch.cuda.current_stream() if stream is None else stream
+    return int(_lib().lbm_nn_gemm_timeout_probe(ctypes.c_void_p(st.cuda_stream)))
 
 
 def encode(Ra, Pr):
@@ -176,6 +193,32 @@ class Net:
         self._check(self._L.lbm_net_train_step(self._net, arr.shape[0], ptr, t.data_ptr(),
                                                ctypes.byref(loss)))
         return loss.value
+
+    def tensor(self, name, batch):
+        """A stored tensor of the last call (lbm_net_tensor) as a float64 numpy array of
+        shape (batch, voxels, channels); BF16 activations are widened exactly."""
+        import numpy as np
+        which = TENSORS.index(name)
+        n, (c1, c2, c3) = self.n, self.channels
+        level = {"P1": 1, "A2": 1, "S2": 1, "C2": 1, "A7": 1, "A8": 1, "D_A8": 1, "D_A7": 1,
+                 "D_C2": 1, "D_S2": 1, "D_A2": 1, "D_P1": 1, "P2": 2, "A4": 2, "A5": 2, "A6": 2,
+                 "D_A6": 2, "D_A5": 2, "D_A4": 2, "D_P2": 2}.get(name, 0)
+        ch = {"X0": 4, "OUT": 4, "D_OUT": 4, "C2": c3 + c2, "D_C2": c3 + c2, "C1": c2 + c1,
+              "D_C1": c2 + c1}
+        base = name[2:] if name.startswith("D_") else name
+        chans = ch.get(name) or {"A0": c1, "S1": c1, "P1": c1, "A2": c2, "S2": c2, "P2": c2,
+                                 "A4": c3, "A5": c3, "A6": c3, "A7": c2, "A8": c2, "A9": c1,
+                                 "A10": c1}[base]
+        vox = (n >> level) ** 3
+        count = batch * vox * chans
+        if which <= TENSORS.index("A10"):
+            raw = np.empty(count, dtype=np.uint16)
+            self._check(self._L.lbm_net_tensor(self._net, which, int(batch), raw.ctypes.data, count))
+            vals = (raw.astype(np.uint32) << 16).view(np.float32)  # BF16 -> FP32, exact
+        else:
+            vals = np.empty(count, dtype=np.float32)
+            self._check(self._L.lbm_net_tensor(self._net, which, int(batch), vals.ctypes.data, count))
+        return vals.astype(np.float64).reshape(batch, vox, chans)
 
     def close(self):
         if getattr(self, "_net", None) is not None and self._net.value:

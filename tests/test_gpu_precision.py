@@ -147,45 +147,6 @@ def test_pair_kernel_one_step_against_oracle(prec_name, case):
         assert (np.abs(g - G1) <= bg).all(), np.max(np.abs(g - G1) / bg)
 
 
-def _sampled_nodes_check(n, q, prec_name, Ra, count=600):
-    import paper_1710_04751_gb300 as lbm
-    from tests.test_gpu_fullsize import sample_nodes
-    p = oracle.Problem.cavity(n, Ra, q_g=q)
-    sim = lbm.LBM((n, n, n), q, Ra=Ra, Pr=0.71, Ma=0.05 * math.sqrt(3.0), precision=getattr(lbm, prec_name))
-    sim.step(300)
-    f0, g0 = sim.get_populations()
-    sim.step(1)
-    f1, g1 = sim.get_populations()
-    sim.close()
-    wf = oracle.weights_flow()
-    wt = oracle.weights_thermal(q, p.cs2_phi)
-    floor_g = thermal_floor(q, p.cs2_phi, p.T_hot - p.T_cold)
-    e, sub = EPS.get(prec_name, 0.0), SUBNORMAL_HALF.get(prec_name, 0.0)
-    for (i, j, k) in sample_nodes(n, 11 + q, count):
-        fr, gr = p.cell_update(f0, g0, i, j, k)
-        bf = e * np.abs(fr - wf) + FP32_REL * np.maximum(np.abs(fr), wf) + sub
-        bg = e * np.abs(gr - wt * gr.sum()) + FP32_REL * np.maximum(np.abs(gr), floor_g) + sub
-        assert (np.abs(f1[:, k, j, i] - fr) <= bf).all(), (i, j, k)
-        assert (np.abs(g1[:, k, j, i] - gr) <= bg).all(), (i, j, k)
-    assert abs(f1.sum() - f0.sum()) <= 1e-5 * f0.sum()
-
-
-@pytest.mark.parametrize("prec_name", ["FP16_DEV", "BF16_DEV"])
-@pytest.mark.parametrize("q", [15, 7])
-def test_pair_kernel_sampled_nodes_at_128(q, prec_name):
-    # the benchmark's 16-bit workload: 128^3, Ra = 1e5, in the launch configuration the
-    # bench times; every corner, edge and face class plus random interior nodes
-    _sampled_nodes_check(128, q, prec_name, 1e5)
-
-
-@pytest.mark.timeout(600)
-@pytest.mark.parametrize("prec_name", ["FP16_DEV", "FP32"])
-def test_sampled_nodes_at_256(prec_name):
-    # the precision study's cavity (256^3, Ra = 1e6) and the bench's 256^3 line, in the
-    # launch configuration they time; the FP32 bound alone for FP32
-    _sampled_nodes_check(256, 15, prec_name, 1e6, count=300)
-
-
 # ------------------------------------------------------------------------------------
 # The pair kernel on long rows (nx up to 512: several 64-thread blocks per row) and on
 # grids of many short rows (thousands of blocks, most of them interior rows).
