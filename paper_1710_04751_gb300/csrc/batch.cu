@@ -56,7 +56,7 @@ __device__ __forceinline__ const BatchMember<S>& member_of(BatchMember<S>* cache
     return cache[0];
 }
 
-template <typename S, int Q>
+template <typename S, int Q, bool UNIT>
 __device__ __forceinline__ void batch_node(const BatchMember<S>& m, const ParamsOf<S>& p, int c,
                                            int parity) {
     const int nx = p.nx, ny = p.ny;
@@ -69,9 +69,9 @@ __device__ __forceinline__ void batch_node(const BatchMember<S>& m, const Params
     S* Fout = m.F[parity ^ 1];
     S* Gout = m.G[parity ^ 1];
     if (m.fast && j >= 1 && j + 1 < ny && k >= 1 && k + 1 < p.nz)
-        cavity_node<S, Q, true>(Fin, Gin, nullptr, Fout, Gout, nullptr, p, i, j, k);
+        cavity_node<S, Q, true, UNIT>(Fin, Gin, nullptr, Fout, Gout, nullptr, p, i, j, k);
     else
-        cavity_node<S, Q, false>(Fin, Gin, nullptr, Fout, Gout, nullptr, p, i, j, k);
+        cavity_node<S, Q, false, UNIT>(Fin, Gin, nullptr, Fout, Gout, nullptr, p, i, j, k);
 }
 
 // Parameters of a member of a sweep: every field of `base` (a kernel parameter, so it
@@ -101,8 +101,9 @@ __device__ __forceinline__ ParamsOf<S> sweep_params(const ParamsOf<S>& base, con
 // L2 -- and an SM that runs ahead takes more tiles.  Each block claims its next tile
 // while it works on the current one.  The launch for parity p uses queue[p] and zeroes
 // queue[p ^ 1] for the launch that follows it in the stream.
-// SWEEP: the members differ only in the fields sweep_params takes from them.
-template <typename S, int Q, int THREADS, int MINB, bool SWEEP>
+// MODE: 0 general members; 1 a sweep (the members differ only in the fields sweep_params
+// takes from them); 2 a sweep at the paper's unit higher-order rates (collide_unit.cuh).
+template <typename S, int Q, int THREADS, int MINB, int MODE>
 __global__ void __launch_bounds__(THREADS, MINB)
     batch_step_kernel(const BatchMember<S>* __restrict__ members, int count,
                       const BatchTile* __restrict__ tiles, const int* __restrict__ n_tiles,
@@ -125,8 +126,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
         if (threadIdx.x == 0) claim = atomicAdd(queue + parity, 1);
         const BatchMember<S>& m = member_of<S>(cache, members, tile.member, cache_all, loaded);
         for (int c = threadIdx.x; c < tile.count; c += THREADS) {
-            if constexpr (SWEEP) batch_node<S, Q>(m, sweep_params<S>(base, m.p), tile.c0 + c, parity);
-            else batch_node<S, Q>(m, m.p, tile.c0 + c, parity);
+            if constexpr (MODE > 0)
+                batch_node<S, Q, MODE == 2>(m, sweep_params<S>(base, m.p), tile.c0 + c, parity);
+            else
+                batch_node<S, Q, false>(m, m.p, tile.c0 + c, parity);
         }
         __syncthreads();  // every thread has read next_tile for this iteration
         if (threadIdx.x == 0) next_tile = claim;
@@ -211,25 +214,33 @@ struct Variant {
     const void* fn;
 };
 
-template <typename S, int Q, bool SWEEP>
+template <typename S, int Q, int MODE>
 static int step_variants(Variant* out) {
     if constexpr (sizeof(typename Storage<S>::real) == 8) {
-        out[0] = {128, 1, (const void*)batch_step_kernel<S, Q, 128, 1, SWEEP>};
-        out[1] = {256, 1, (const void*)batch_step_kernel<S, Q, 256, 1, SWEEP>};
+        out[0] = {128, 1, (const void*)batch_step_kernel<S, Q, 128, 1, MODE>};
+        out[1] = {256, 1, (const void*)batch_step_kernel<S, Q, 256, 1, MODE>};
         return 2;
-    } else if constexpr (Q == 15 && !SWEEP) {
+    } else if constexpr (Q == 15 && MODE == 0) {
         // general members: D3Q15 needs 96 registers without spills (every parameter comes
         // from shared memory, none from the constant bank); 80 spills 60 bytes
-        out[0] = {128, 5, (const void*)batch_step_kernel<S, Q, 128, 5, SWEEP>};
-        out[1] = {128, 6, (const void*)batch_step_kernel<S, Q, 128, 6, SWEEP>};
-        out[2] = {256, 2, (const void*)batch_step_kernel<S, Q, 256, 2, SWEEP>};
-        out[3] = {256, 3, (const void*)batch_step_kernel<S, Q, 256, 3, SWEEP>};
+        out[0] = {128, 5, (const void*)batch_step_kernel<S, Q, 128, 5, MODE>};
+        out[1] = {128, 6, (const void*)batch_step_kernel<S, Q, 128, 6, MODE>};
+        out[2] = {256, 2, (const void*)batch_step_kernel<S, Q, 256, 2, MODE>};
+        out[3] = {256, 3, (const void*)batch_step_kernel<S, Q, 256, 3, MODE>};
+        return 4;
+    } else if constexpr (MODE == 2) {
+        // unit higher-order rates: fewer live moments (D3Q15: 80 registers without spills
+        // at 6 blocks of 128 or 3 of 256; 72 spill 8 bytes)
+        out[0] = {128, 6, (const void*)batch_step_kernel<S, Q, 128, 6, MODE>};
+        out[1] = {128, 7, (const void*)batch_step_kernel<S, Q, 128, 7, MODE>};
+        out[2] = {256, 2, (const void*)batch_step_kernel<S, Q, 256, 2, MODE>};
+        out[3] = {256, 3, (const void*)batch_step_kernel<S, Q, 256, 3, MODE>};
         return 4;
     } else {
-        out[0] = {128, 6, (const void*)batch_step_kernel<S, Q, 128, 6, SWEEP>};
-        out[1] = {128, 7, (const void*)batch_step_kernel<S, Q, 128, 7, SWEEP>};
-        out[2] = {256, 2, (const void*)batch_step_kernel<S, Q, 256, 2, SWEEP>};
-        out[3] = {256, 3, (const void*)batch_step_kernel<S, Q, 256, 3, SWEEP>};
+        out[0] = {128, 6, (const void*)batch_step_kernel<S, Q, 128, 6, MODE>};
+        out[1] = {128, 7, (const void*)batch_step_kernel<S, Q, 128, 7, MODE>};
+        out[2] = {256, 2, (const void*)batch_step_kernel<S, Q, 256, 2, MODE>};
+        out[3] = {256, 3, (const void*)batch_step_kernel<S, Q, 256, 3, MODE>};
         return 4;
     }
 }
@@ -270,6 +281,7 @@ struct lbm_batch {
     Variant variant{};
     int grid = 0, cache_all = 0;
     bool sweep = false;  // members differ only in omega_nu, omega_phi, g beta and the grid
+    bool unit = false;   // ... and all relax their higher orders at the paper's unit rates
     size_t smem = 0;
     cudaGraphExec_t graph = nullptr;
     int64_t steps = 0;
@@ -363,11 +375,15 @@ static BatchLayout batch_layout(int count, const lbm_grid* grids, int lattice, i
 // Kernel builds of the batch's precision and lattice.
 static int batch_variants(const lbm_batch* b, Variant* out) {
     if (b->precision == LBM_FP64) {
-        if (b->sweep) return b->Q == 15 ? step_variants<double, 15, true>(out) : step_variants<double, 7, true>(out);
-        return b->Q == 15 ? step_variants<double, 15, false>(out) : step_variants<double, 7, false>(out);
+        if (b->sweep && b->unit)
+            return b->Q == 15 ? step_variants<double, 15, 2>(out) : step_variants<double, 7, 2>(out);
+        if (b->sweep) return b->Q == 15 ? step_variants<double, 15, 1>(out) : step_variants<double, 7, 1>(out);
+        return b->Q == 15 ? step_variants<double, 15, 0>(out) : step_variants<double, 7, 0>(out);
     }
-    if (b->sweep) return b->Q == 15 ? step_variants<float, 15, true>(out) : step_variants<float, 7, true>(out);
-    return b->Q == 15 ? step_variants<float, 15, false>(out) : step_variants<float, 7, false>(out);
+    if (b->sweep && b->unit)
+        return b->Q == 15 ? step_variants<float, 15, 2>(out) : step_variants<float, 7, 2>(out);
+    if (b->sweep) return b->Q == 15 ? step_variants<float, 15, 1>(out) : step_variants<float, 7, 1>(out);
+    return b->Q == 15 ? step_variants<float, 15, 0>(out) : step_variants<float, 7, 0>(out);
 }
 
 // Shared memory of a launch: the whole member table for a persistent grid when it fits
@@ -651,6 +667,9 @@ extern "C" int lbm_batch_create(int count, const lbm_grid* grids, int lattice,
     b->state.assign(count, LBM_MEMBER_ACTIVE);
     b->member_bytes = member_table_bytes(o.precision);
     b->sweep = is_sweep(count, params);
+    b->unit = true;  // a sweep's higher-order rates are those of member 0
+    for (int bb = 9; bb < 15; ++bb) b->unit = b->unit && params[0].omega_f[bb] == 1.0;
+    for (int bb = 4; bb < lattice; ++bb) b->unit = b->unit && params[0].omega_g[bb] == 1.0;
     auto bail = [&](int rc) {
         std::string msg = b->err;
         lbm_batch_destroy(b);

@@ -20,6 +20,7 @@
 #pragma once
 
 #include "collide.cuh"
+#include "collide_unit.cuh"
 #include "internal.h"
 #include "lattice.cuh"
 
@@ -97,8 +98,10 @@ __device__ __forceinline__ void pull(const S* __restrict__ Fin, const S* __restr
     }
 }
 
-// Macroscopic variables, both collisions and the store of one node.
-template <typename S, int Q>
+// Macroscopic variables, both collisions and the store of one node.  UNIT: the paper's
+// unit higher-order rates (collide_unit.cuh), for which the post-collision state needs
+// only the low-order moments of the pulled populations.
+template <typename S, int Q, bool UNIT = false>
 __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15],
                                               typename Storage<S>::real (&g)[Q],
                                               S* __restrict__ Fout, S* __restrict__ Gout,
@@ -107,6 +110,37 @@ __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15]
     using real = typename Storage<S>::real;
     using St = Storage<S>;
     const int64_t P = p.plane;
+    if constexpr (UNIT) {
+        const UnitRates<real> r = unit_rates<real>(p);
+        real m0, mx, my, mz;
+        raw_first<real, Q>(g, m0, mx, my, mz);  // all the scalar collision needs of g
+        const real T = m0 + r.halfR;             // Eq. (25)
+        const real Fx = p.ext_fx, Fy = p.ext_fy, Fz = p.ext_fz + p.gbeta * (T - p.T0);
+        Low10<real> dm = raw_low15<real>(f);     // moments of f - w_a: the rest state's are
+        dm.m0 -= real(1);                        // 1 (zeroth) and 1/3 (xx, yy, zz)
+        dm.xx -= real(1.0 / 3.0);
+        dm.yy -= real(1.0 / 3.0);
+        dm.zz -= real(1.0 / 3.0);
+        const real inv_rho = real(1) / (real(1) + dm.m0);
+        UPow<real> u;
+        Raw15<real> D;
+        flow_unit<real>(dm, Fx, Fy, Fz, r, inv_rho, u, D);
+        populations15<real>(D, f);  // f~ - w_a: the 16-bit forms store it as it is
+#pragma unroll
+        for (int a = 0; a < 15; ++a)
+            Fout[a * P + c] = St::store(St::deviation ? f[a] : f[a] + p.wf[a], real(0));
+        if constexpr (Q == 15) {
+            thermal15_unit<real>(T, m0, mx, my, mz, u, r, D);
+            populations15<real>(D, g);
+        } else {
+            thermal7_unit<real>(T, m0, mx, my, mz, u, r, g);
+        }
+        if constexpr (St::deviation) Tout[c] = T;  // the reference of the stored deviations
+#pragma unroll
+        for (int a = 0; a < Q; ++a)  // g~ - w^phi_a T: the 16-bit forms' stored value
+            Gout[a * P + c] = St::store(St::deviation ? g[a] : fmad(p.wg[a], T, g[a]), real(0));
+        return;
+    }
     real T = real(0);
 #pragma unroll
     for (int a = 0; a < Q; ++a) T += g[a];
@@ -135,7 +169,7 @@ __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15]
 // every thread.  Nodes touching a y or z wall run the generic pull.  The interior body
 // needs boundary == 0 (the cavity) and 15 * plane < 2^31 (32-bit node indices).
 // ---------------------------------------------------------------------------------
-template <typename S, int Q, bool INTERIOR>
+template <typename S, int Q, bool INTERIOR, bool UNIT = false>
 __device__ __forceinline__ void cavity_node(const S* __restrict__ Fin, const S* __restrict__ Gin,
                                             const float* __restrict__ Tin, S* __restrict__ Fout,
                                             S* __restrict__ Gout, float* __restrict__ Tout,
@@ -179,7 +213,7 @@ __device__ __forceinline__ void cavity_node(const S* __restrict__ Fin, const S* 
     } else {
         pull<S, Q>(Fin, Gin, Tin, p, i, j, k, c, f, g);
     }
-    collide_store<S, Q>(f, g, Fout, Gout, Tout, p, c);
+    collide_store<S, Q, UNIT>(f, g, Fout, Gout, Tout, p, c);
 }
 
 // Blocks per SM the single-precision kernels are built for: 7 for D3Q15 (at most 72

@@ -22,6 +22,7 @@
 #include <cuda_fp16.h>
 
 #include "collide.cuh"
+#include "collide_unit.cuh"
 #include "internal.h"
 #include "lattice.cuh"
 
@@ -73,6 +74,22 @@ struct Pack<__nv_bfloat16> {
     __device__ __forceinline__ static float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
 };
 
+// Two lanes of FP32 as one arithmetic value (the unit-rate collisions of
+// collide_unit.cuh are templates over it): every operator is one packed instruction.
+struct Pair {
+    float2 v;
+};
+__device__ __forceinline__ Pair operator+(Pair a, Pair b) { return {add2(a.v, b.v)}; }
+__device__ __forceinline__ Pair operator-(Pair a, Pair b) { return {sub2(a.v, b.v)}; }
+__device__ __forceinline__ Pair operator*(Pair a, Pair b) { return {mul2(a.v, b.v)}; }
+__device__ __forceinline__ Pair& operator+=(Pair& a, Pair b) { a = a + b; return a; }
+__device__ __forceinline__ Pair& operator-=(Pair& a, Pair b) { a = a - b; return a; }
+__device__ __forceinline__ Pair fmad(Pair a, Pair b, Pair c) { return {fma2(a.v, b.v, c.v)}; }
+template <>
+__device__ __forceinline__ Pair cst<Pair>(double v) {
+    return {make_float2((float)v, (float)v)};
+}
+
 // Parameters of the pair update, each broadcast to both lanes (host: make_pair_params).
 struct PairParams {
     float2 wf[15];     // flow rest values w_a: the offsets of the stored flow deviations
@@ -93,6 +110,7 @@ struct PairParams {
     float2 fx, fy, fz; // uniform body force
     float2 halffx, halffy;
     int e4_mode;
+    UnitRates<Pair> ur; // the rates of the unit-rate update (pair_node_unit)
 };
 
 // Powers of one velocity (lane-wise) that the binomial shifts need.
@@ -617,6 +635,94 @@ __device__ __forceinline__ void pair_node(const S* __restrict__ Fin, const S* __
         }
     }
     pair_finish<S, Q>(f, g, Fout, Gout, Tout, q, P, c0);
+}
+
+// ---------------------------------------------------------------------------------
+// The pair update at the paper's unit higher-order rates (collide_unit.cuh): the scalar
+// collision needs only phi and the first moments of the pulled g, so the thermal pull is
+// reduced to those four pairs at once and the flow update runs with no scalar population
+// held in registers.  Pull addressing and wall rules as pair_node.
+// ---------------------------------------------------------------------------------
+template <typename S, int Q>
+__device__ __forceinline__ void pair_node_unit(const S* __restrict__ Fin, const S* __restrict__ Gin,
+                                               const float* __restrict__ Tin, S* __restrict__ Fout,
+                                               S* __restrict__ Gout, float* __restrict__ Tout,
+                                               const PairParams& q, int nx, int nxy, int P, int c0,
+                                               bool lo, bool hi) {
+    using Pk = Pack<S>;
+    using two = typename Pk::two;
+    Pair m0, mx, my, mz;
+    {
+        Pair g[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int r = ey(a) * nx + ez(a) * nxy;
+            const S* Ga = Gin + a * P;
+            const float2 Tp = *reinterpret_cast<const float2*>(Tin + c0 - r);
+            if (ex(a) == 0) {
+                const float2 v = Pk::to_float2(*reinterpret_cast<const two*>(Ga + c0 - r));
+                g[a].v = fma2(q.wg[a], Tp, v);
+            } else if (ex(a) > 0) {
+                const S* Gs = Ga - r - 1;
+                const int i0 = lo ? c0 + r + 1 + (opp(a) - a) * P : c0;
+                const float* Ts = Tin - r - 1;
+                const float T0 = Ts[lo ? c0 + r + 1 : c0];
+                float2 v = make_float2(Pk::to_float(Gs[i0]), Pk::to_float(Gs[c0 + 1]));
+                v = fma2(q.wg[a], make_float2(T0, Tp.x), v);
+                v.x = lo ? q.wTc2[a] - v.x : v.x;
+                g[a].v = v;
+            } else {
+                const S* Gs = Ga - r + 1;
+                const int i1 = hi ? c0 + r + (opp(a) - a) * P : c0 + 1;
+                const float* Ts = Tin - r + 1;
+                const float T1 = Ts[hi ? c0 + r : c0 + 1];
+                float2 v = make_float2(Pk::to_float(Gs[c0]), Pk::to_float(Gs[i1]));
+                v = fma2(q.wg[a], make_float2(Tp.y, T1), v);
+                v.y = hi ? q.wTh2[a] - v.y : v.y;
+                g[a].v = v;
+            }
+        }
+        raw_first<Pair, Q>(g, m0, mx, my, mz);
+    }
+    Pair f[15];  // the stored flow deviations f - w_a
+#pragma unroll
+    for (int a = 0; a < 15; ++a) {
+        const int r = ey(a) * nx + ez(a) * nxy;
+        const S* Fa = Fin + a * P;
+        if (ex(a) == 0) {
+            f[a].v = Pk::to_float2(*reinterpret_cast<const two*>(Fa + c0 - r));
+        } else if (ex(a) > 0) {
+            const S* Fs = Fa - r - 1;
+            const int i0 = lo ? c0 + r + 1 + (opp(a) - a) * P : c0;
+            f[a].v = make_float2(Pk::to_float(Fs[i0]), Pk::to_float(Fs[c0 + 1]));
+        } else {
+            const S* Fs = Fa - r + 1;
+            const int i1 = hi ? c0 + r + (opp(a) - a) * P : c0 + 1;
+            f[a].v = make_float2(Pk::to_float(Fs[c0]), Pk::to_float(Fs[i1]));
+        }
+    }
+    const UnitRates<Pair>& ur = q.ur;
+    const Pair T = m0 + ur.halfR;  // Eq. (25)
+    const Pair Fz = {fma2(q.gbeta, sub2(T.v, q.T0), q.fz)};
+    const Pair Fx = {q.fx}, Fy = {q.fy};
+    const Low10<Pair> dm = raw_low15<Pair>(f);
+    const Pair inv_rho = {make_float2(1.0f / (1.0f + dm.m0.v.x), 1.0f / (1.0f + dm.m0.v.y))};
+    UPow<Pair> u;
+    Raw15<Pair> D;
+    flow_unit<Pair>(dm, Fx, Fy, Fz, ur, inv_rho, u, D);
+    populations15<Pair>(D, f);
+#pragma unroll
+    for (int a = 0; a < 15; ++a) *reinterpret_cast<two*>(Fout + a * P + c0) = Pk::from_float2(f[a].v);
+    *reinterpret_cast<float2*>(Tout + c0) = T.v;  // the reference of this node's stored deviations
+    Pair g[Q];
+    if constexpr (Q == 15) {
+        thermal15_unit<Pair>(T, m0, mx, my, mz, u, ur, D);
+        populations15<Pair>(D, g);
+    } else {
+        thermal7_unit<Pair>(T, m0, mx, my, mz, u, ur, g);
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) *reinterpret_cast<two*>(Gout + a * P + c0) = Pk::from_float2(g[a].v);
 }
 
 }  // namespace lbm

@@ -1,174 +1,16 @@
-// step.cu -- the single-cavity kernels of the fused stream-and-collide time step of
-// arXiv:1710.04751 (the node update itself is node.cuh) and their launcher.
-#include "node.cuh"
-#include "pair.cuh"
+// step.cu -- the single-cavity step launcher: the kernels of step_kernels.cuh at general
+// rates (instantiated here) or at the paper's unit higher-order rates (step_unit.cu).
+#include "step_kernels.cuh"
 
 namespace lbm {
 
-// Generic kernel: one thread per node of the flattened grid, any boundary mode.
-template <typename S, int Q>
-__global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ Fin,
-                                                   const S* __restrict__ Gin,
-                                                   const float* __restrict__ Tin,
-                                                   S* __restrict__ Fout, S* __restrict__ Gout,
-                                                   float* __restrict__ Tout, ParamsOf<S> p) {
-    using real = typename Storage<S>::real;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= p.ncell) return;
-    const int i = (int)(c % p.nx);
-    const int64_t t = c / p.nx;
-    const int j = (int)(t % p.ny);
-    const int k = (int)(t / p.ny);
-    real f[15], g[Q];
-    pull<S, Q>(Fin, Gin, Tin, p, i, j, k, c, f, g);
-    collide_store<S, Q>(f, g, Fout, Gout, Tout, p, c);
-}
-
-// ---------------------------------------------------------------------------------
-// Cavity kernel: one block per x-row segment (blockIdx.y = j, blockIdx.z = k), so the
-// y/z wall tests are block-uniform.
-// ---------------------------------------------------------------------------------
-template <typename S, int Q>
-__global__ void __launch_bounds__(128, (cavity_min_blocks<S, Q>()))
-    step_cavity_kernel(const S* __restrict__ Fin, const S* __restrict__ Gin,
-                       const float* __restrict__ Tin, S* __restrict__ Fout,
-                       S* __restrict__ Gout, float* __restrict__ Tout, ParamsOf<S> p) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
-    if (i >= p.nx) return;
-    const bool interior = j >= 1 && j + 1 < p.ny && k >= 1 && k + 1 < p.nz;
-    if (interior) cavity_node<S, Q, true>(Fin, Gin, Tin, Fout, Gout, Tout, p, i, j, k);
-    else cavity_node<S, Q, false>(Fin, Gin, Tin, Fout, Gout, Tout, p, i, j, k);
-}
-
-// ---------------------------------------------------------------------------------
-// Pair kernel of the 16-bit forms: one thread per pair of nodes (2t, 2t+1) of an x-row
-// (blockIdx.y = j, blockIdx.z = k), nx even.  Rows away from the y and z walls take the
-// packed pair update (pair.cuh); rows at a y or z wall update the two nodes one after
-// the other with the general pull.
-// ---------------------------------------------------------------------------------
-constexpr int kPairThreads = 64;
-
-// Resident blocks per SM the pair kernel is built for (sets its register budget: 128 for
-// 7 or 8 blocks of 64 threads).  Measured: 7-8 beat 5-6 (168-204 registers, fewer warps)
-// and 10 (96 registers, spills) at 128^3.
-#ifndef LBM_PAIR_MIN_BLOCKS_Q15
-#define LBM_PAIR_MIN_BLOCKS_Q15 7
-#endif
-#ifndef LBM_PAIR_MIN_BLOCKS_Q7
-#define LBM_PAIR_MIN_BLOCKS_Q7 8
-#endif
-template <int Q>
-constexpr int pair_min_blocks() { return Q == 15 ? LBM_PAIR_MIN_BLOCKS_Q15 : LBM_PAIR_MIN_BLOCKS_Q7; }
-
-template <typename S, int Q>
-__global__ void __launch_bounds__(kPairThreads, (pair_min_blocks<Q>()))
-    step_pair_kernel(const S* __restrict__ Fin, const S* __restrict__ Gin,
-                     const float* __restrict__ Tin, S* __restrict__ Fout,
-                     S* __restrict__ Gout, float* __restrict__ Tout, ParamsOf<S> p,
-                     PairParams q) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
-    const int npair = p.nx >> 1;
-    if (t >= npair) return;
-    if (j >= 1 && j + 1 < p.ny && k >= 1 && k + 1 < p.nz) {
-        const int nx = p.nx, nxy = nx * p.ny;
-        pair_node<S, Q>(Fin, Gin, Tin, Fout, Gout, Tout, q, nx, nxy, (int)p.plane,
-                        k * nxy + j * nx + 2 * t, t == 0, t == npair - 1);
-    } else {
-#pragma unroll 1
-        for (int e = 0; e < 2; ++e)
-            cavity_node<S, Q, false>(Fin, Gin, Tin, Fout, Gout, Tout, p, 2 * t + e, j, k);
-    }
-}
-
-// The pair parameters of a context's FP32 parameters, every value broadcast to both lanes.
-static PairParams make_pair_params(const DevParams<float>& p, int Q) {
-    auto b = [](float v) { return make_float2(v, v); };
-    PairParams q;
-    for (int a = 0; a < 15; ++a) {
-        q.wf[a] = b(p.wf[a]);
-        q.wg[a] = b(p.wg[a]);
-        q.nwg[a] = b(-p.wg[a]);
-        q.wTc2[a] = 2.0f * p.wg[a] * p.T_cold;
-        q.wTh2[a] = 2.0f * p.wg[a] * p.T_hot;
-        q.nomf[a] = b(-p.om_f[a]);
-        q.nomg[a] = b(-p.om_g[a]);
-    }
-    const float cs2 = 1.0f / 3.0f;
-    q.omf9 = b(p.om_f[9]);
-    q.omf14 = b(p.om_f[14]);
-    for (int i = 0; i < 3; ++i) q.cf3[i] = b((1.0f - p.om_f[10 + i]) * cs2);
-    const float cp = p.cs2_phi;
-    q.omg_tr = b(p.om_g[Q == 15 ? 9 : 6] * (3.0f * cp));
-    q.omg_4 = b(p.om_g[14] * (cp * cp));
-    q.cs2 = b(cp);
-    q.cs4 = b(cp * cp);
-    q.R = b(p.heat_source);
-    q.halfR = b(0.5f * p.heat_source);
-    q.gbeta = b(p.gbeta);
-    q.T0 = b(p.T0);
-    q.fx = b(p.ext_fx);
-    q.fy = b(p.ext_fy);
-    q.fz = b(p.ext_fz);
-    q.halffx = b(0.5f * p.ext_fx);
-    q.halffy = b(0.5f * p.ext_fy);
-    q.e4_mode = p.e4_mode;
-    return q;
-}
-
 template <typename S>
-static bool launch_pair(const DevState& s, int cur, const ParamsOf<S>& p, cudaStream_t st) {
-    if constexpr (!Storage<S>::deviation) {
-        return false;
-    } else {
-        if (p.boundary != 0 || (p.nx & 1) || p.ny > 65535 || p.nz > 65535 ||
-            15 * p.plane >= (int64_t(1) << 31))
-            return false;
-        const S* Fin = static_cast<const S*>(s.F[cur]);
-        const S* Gin = static_cast<const S*>(s.G[cur]);
-        S* Fout = static_cast<S*>(s.F[cur ^ 1]);
-        S* Gout = static_cast<S*>(s.G[cur ^ 1]);
-        const float* Tin = static_cast<const float*>(s.T[cur]);
-        float* Tout = static_cast<float*>(s.T[cur ^ 1]);
-        const PairParams q = make_pair_params(p, s.Q);
-        const int npair = p.nx / 2;
-        const int bx = npair <= 32 ? 32 : kPairThreads;
-        const dim3 grid((npair + bx - 1) / bx, p.ny, p.nz);
-        if (s.Q == 15)
-            step_pair_kernel<S, 15><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, q);
-        else
-            step_pair_kernel<S, 7><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, q);
-        return true;
-    }
-}
-
+cudaError_t launch_step_unit(const DevState& s, int cur, const ParamsOf<S>& p, cudaStream_t st);
 
 template <typename S>
 cudaError_t launch_step(const DevState& s, int cur, const ParamsOf<S>& p, cudaStream_t st) {
-    const S* Fin = static_cast<const S*>(s.F[cur]);
-    const S* Gin = static_cast<const S*>(s.G[cur]);
-    S* Fout = static_cast<S*>(s.F[cur ^ 1]);
-    S* Gout = static_cast<S*>(s.G[cur ^ 1]);
-    const float* Tin = static_cast<const float*>(s.T[cur]);
-    float* Tout = static_cast<float*>(s.T[cur ^ 1]);
-    if (launch_pair<S>(s, cur, p, st)) return cudaGetLastError();
-    if (p.boundary == 0 && p.ny <= 65535 && p.nz <= 65535 && 15 * p.plane < (int64_t(1) << 31)) {
-        const int bx = 128;
-        const dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
-        if (s.Q == 15)
-            step_cavity_kernel<S, 15><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
-        else
-            step_cavity_kernel<S, 7><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
-        return cudaGetLastError();
-    }
-    const int threads = 256;
-    const int64_t blocks = (p.ncell + threads - 1) / threads;
-    if (s.Q == 15)
-        step_kernel<S, 15><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
-    else
-        step_kernel<S, 7><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
-    return cudaGetLastError();
+    if (has_unit_rates(p, s.Q)) return launch_step_unit<S>(s, cur, p, st);
+    return launch_step_as<S, false>(s, cur, p, st);
 }
 
 template cudaError_t launch_step<double>(const DevState&, int, const ParamsOf<double>&, cudaStream_t);

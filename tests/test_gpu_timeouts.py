@@ -13,6 +13,8 @@ import time
 import numpy as np
 import pytest
 
+from paper_1710_04751_gb300.lbm import LBM_ETIMEOUT
+
 pytestmark = pytest.mark.gpu
 
 
@@ -27,17 +29,17 @@ def test_host_wait_times_out_and_the_context_recovers():
     a.set_timeout(1e-9)
     with pytest.raises(lbm.LBMError) as e:
         a.step(2000)  # ~0.16 s of kernels; the residual check's wait runs out at once
-    assert e.value.code == lbm.LBM_ETIMEOUT
+    assert e.value.code == LBM_ETIMEOUT
     with pytest.raises(lbm.LBMError) as e:
         a.nusselt()  # waits before copying: times out again, copies nothing
-    assert e.value.code == lbm.LBM_ETIMEOUT
+    assert e.value.code == LBM_ETIMEOUT
     t0 = time.time()
     while True:  # the queued work keeps running; poll until the stream is idle
         try:
             a.synchronize()
             break
         except lbm.LBMError as err:
-            assert err.code == lbm.LBM_ETIMEOUT
+            assert err.code == LBM_ETIMEOUT
             assert time.time() - t0 < 60
     a.set_timeout(600.0)
     assert a.steps_done == 2000
@@ -59,7 +61,7 @@ def test_gemm_bounded_wait_runs_out_and_the_next_gemm_is_exact():
     import paper_1710_04751_gb300 as lbm
     from paper_1710_04751_gb300 import net
     for _ in range(2):
-        assert net.gemm_timeout_probe() == lbm.LBM_ETIMEOUT
+        assert net.gemm_timeout_probe() == LBM_ETIMEOUT
     g = torch.Generator().manual_seed(3)
     A = torch.randn((256, 128), generator=g, dtype=torch.float64).to(torch.bfloat16)
     B = torch.randn((64, 128), generator=g, dtype=torch.float64).to(torch.bfloat16)
