@@ -86,6 +86,35 @@ int lbm_slabs_count(const lbm_slabs* s);
 int64_t lbm_slabs_steps_done(const lbm_slabs* s);
 int64_t lbm_slabs_halo_bytes(const lbm_slabs* s);
 
+/* ---- the message of one cut, for slabs held by different processes -------------------
+ *
+ * Pull streaming carries across a cut only the populations whose e_z points across it:
+ * upwards (dir = +1) the D3Q15 directions 5, 7, 8, 9, 10 of the flow and of a D3Q15 scalar
+ * (direction 5 alone for D3Q7), downwards (dir = -1) 6, 11, 12, 13, 14 (D3Q7: 6).  Every
+ * wall rule a node next to a cut applies reads, from the plane across the cut, only
+ * populations of that set (a specular reflection keeps e_z), so a slab held by another
+ * process needs, each step, only these: (5 + 5) or (5 + 1) values per node of one plane,
+ * a third or a quarter of the planes lbm_slabs_step copies.  Per step and cut, the slab
+ * below packs the upward set of its last owned plane and the slab above unpacks it into
+ * its halo plane below; the slab above packs the downward set of its first owned plane
+ * and the slab below unpacks it into its halo plane above (planes as lbm_slabs_plan
+ * gives them).  The other populations of a halo plane are then not those of the
+ * neighbour's plane: only the owned planes follow the undivided grid.
+ *
+ * These calls are host only (no GPU): they move values between FP64 host arrays of a
+ * slab's state, in the layout of include/lbm.h for the slab grid (nx, ny, planes of the
+ * slab), and a message of lbm_slabs_cut_values doubles (the flow set, then the scalar
+ * set, each population one nx * ny plane, x fastest).  The transport between processes
+ * (MPI, torch.distributed, NCCL) is the caller's.  LBM_EINVAL for an invalid grid,
+ * lattice, plane, direction or NULL array. */
+int lbm_slabs_cut_populations(int lattice, int dir, int* flow_ids, int* n_flow,
+                              int* scalar_ids, int* n_scalar);
+int64_t lbm_slabs_cut_values(int nx, int ny, int lattice);
+int lbm_slabs_pack_cut(const lbm_grid* slab_grid, int lattice, int plane, int dir,
+                       const double* f, const double* g, double* msg);
+int lbm_slabs_unpack_cut(const lbm_grid* slab_grid, int lattice, int plane, int dir,
+                         const double* msg, double* f, double* g);
+
 /* Wait (bounded) for the work queued on the decomposition's stream. */
 int lbm_slabs_synchronize(lbm_slabs* s);
 const char* lbm_slabs_last_error(const lbm_slabs* s);

@@ -26,7 +26,28 @@ struct BatchMember {
     typename Storage<S>::real* snap;
     int fast;  // the cavity interior body applies (boundary 0, 32-bit node indices)
     int pad;
+    // division of node / row indices by nx and ny as a multiplication: q = (n M) >> s
+    unsigned long long div_nx, div_ny;
+    int shift_nx, shift_ny;
 };
+
+// Division by an invariant integer d >= 1 as a multiplication (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994).  With l = ceil(log2 d),
+// M = ceil(2^(32+l) / d) and e = M d - 2^(32+l) in [0, d):
+//   n M / 2^(32+l) = n / d + n e / (d 2^(32+l)).
+// The fractional part of n / d is at most (d - 1) / d, and the added term stays below 1 / d
+// whenever n e < 2^(32+l), which holds for every n < 2^31 since e < d <= 2^l.  So
+// floor(n M / 2^(32+l)) = floor(n / d).  (M <= 2^33, so n M fits in 64 bits.)
+inline void invariant_divisor(int d, unsigned long long* M, int* shift) {
+    int l = 0;
+    while ((1ll << l) < d) ++l;
+    const unsigned long long p = 1ull << (32 + l);
+    *M = p / (unsigned long long)d + (p % (unsigned long long)d != 0);
+    *shift = 32 + l;
+}
+__device__ __forceinline__ int div_invariant(int n, unsigned long long M, int shift) {
+    return (int)(((unsigned long long)(unsigned)n * M) >> shift);
+}
 
 // A run of `count` nodes of one member starting at node c0 (count <= nodes per tile).
 struct BatchTile {
@@ -60,9 +81,9 @@ template <typename S, int Q, bool UNIT>
 __device__ __forceinline__ void batch_node(const BatchMember<S>& m, const ParamsOf<S>& p, int c,
                                            int parity) {
     const int nx = p.nx, ny = p.ny;
-    const int row = c / nx;
+    const int row = div_invariant(c, m.div_nx, m.shift_nx);
     const int i = c - row * nx;
-    const int k = row / ny;
+    const int k = div_invariant(row, m.div_ny, m.shift_ny);
     const int j = row - k * ny;
     const S* Fin = m.F[parity];
     const S* Gin = m.G[parity];
@@ -640,6 +661,8 @@ static void fill_member_table(lbm_batch* b, std::vector<unsigned char>& table) {
         }
         t[m].snap = static_cast<typename Storage<S>::real*>(c->dev.snap);
         t[m].fast = c->params.boundary == LBM_BC_CAVITY;
+        invariant_divisor(c->grid.nx, &t[m].div_nx, &t[m].shift_nx);
+        invariant_divisor(c->grid.ny, &t[m].div_ny, &t[m].shift_ny);
     }
 }
 

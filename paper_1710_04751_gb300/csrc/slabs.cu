@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "context.h"
+#include "lattice.cuh"
 #include "lbm_slabs.h"
 
 using namespace lbm;
@@ -475,3 +476,82 @@ extern "C" const char* lbm_slabs_last_error(const lbm_slabs* s) {
 }
 
 extern "C" void lbm_slabs_destroy(lbm_slabs* s) { free_slabs(s); }
+
+// ---------------------------------------------------------------------------------
+// The message of one cut for a decomposition over several processes (host only).
+// ---------------------------------------------------------------------------------
+namespace {
+// Populations whose e_z is `dir` (+1 or -1), in the paper's direction order.
+int cut_ids(int lattice, int dir, int* flow, int* scalar, int* nscalar) {
+    int nf = 0, ns = 0;
+    for (int a = 0; a < 15; ++a) {
+        if (ez(a) != dir) continue;
+        flow[nf++] = a;
+        if (a < lattice) scalar[ns++] = a;
+    }
+    *nscalar = ns;
+    return nf;
+}
+
+int check_cut(const lbm_grid* g, int lattice, int plane, int dir) {
+    if (!g || g->nx < 1 || g->ny < 1 || g->nz < 1) return sfail(nullptr, LBM_EINVAL, "invalid slab grid%s");
+    if (lattice != LBM_THERMAL_D3Q15 && lattice != LBM_THERMAL_D3Q7)
+        return sfail(nullptr, LBM_EINVAL, "lattice must be 15 or 7%s");
+    if (dir != 1 && dir != -1) return sfail(nullptr, LBM_EINVAL, "direction must be +1 or -1%s");
+    if (plane < 0 || plane >= g->nz) return sfail(nullptr, LBM_EINVAL, "plane outside the slab%s");
+    return LBM_OK;
+}
+
+template <bool PACK>
+int move_cut(const lbm_grid* g, int lattice, int plane, int dir, double* f, double* gp, double* msg) {
+    int rc = check_cut(g, lattice, plane, dir);
+    if (rc != LBM_OK) return rc;
+    if (!f || !gp || !msg) return sfail(nullptr, LBM_EINVAL, "NULL array%s");
+    int flow[15], scalar[15], ns = 0;
+    const int nf = cut_ids(lattice, dir, flow, scalar, &ns);
+    const int64_t nxy = (int64_t)g->nx * g->ny, ncell = nxy * g->nz, off = (int64_t)plane * nxy;
+    double* m = msg;
+    for (int side = 0; side < 2; ++side) {
+        double* p = side == 0 ? f : gp;
+        const int* ids = side == 0 ? flow : scalar;
+        for (int n = 0, cnt = side == 0 ? nf : ns; n < cnt; ++n, m += nxy) {
+            double* row = p + ids[n] * ncell + off;
+            for (int64_t c = 0; c < nxy; ++c) {
+                if (PACK) m[c] = row[c];
+                else row[c] = m[c];
+            }
+        }
+    }
+    return LBM_OK;
+}
+}  // namespace
+
+extern "C" int lbm_slabs_cut_populations(int lattice, int dir, int* flow_ids, int* n_flow,
+                                         int* scalar_ids, int* n_scalar) {
+    if ((lattice != LBM_THERMAL_D3Q15 && lattice != LBM_THERMAL_D3Q7) || (dir != 1 && dir != -1))
+        return sfail(nullptr, LBM_EINVAL, "lattice must be 15 or 7 and direction +1 or -1%s");
+    int flow[15], scalar[15], ns = 0;
+    const int nf = cut_ids(lattice, dir, flow, scalar, &ns);
+    for (int n = 0; n < nf && flow_ids; ++n) flow_ids[n] = flow[n];
+    for (int n = 0; n < ns && scalar_ids; ++n) scalar_ids[n] = scalar[n];
+    if (n_flow) *n_flow = nf;
+    if (n_scalar) *n_scalar = ns;
+    return LBM_OK;
+}
+
+extern "C" int64_t lbm_slabs_cut_values(int nx, int ny, int lattice) {
+    if (nx < 1 || ny < 1 || (lattice != LBM_THERMAL_D3Q15 && lattice != LBM_THERMAL_D3Q7)) return 0;
+    return (int64_t)(5 + (lattice == LBM_THERMAL_D3Q15 ? 5 : 1)) * nx * ny;
+}
+
+extern "C" int lbm_slabs_pack_cut(const lbm_grid* slab_grid, int lattice, int plane, int dir,
+                                  const double* f, const double* g, double* msg) {
+    return move_cut<true>(slab_grid, lattice, plane, dir, const_cast<double*>(f),
+                          const_cast<double*>(g), msg);
+}
+
+extern "C" int lbm_slabs_unpack_cut(const lbm_grid* slab_grid, int lattice, int plane, int dir,
+                                    const double* msg, double* f, double* g) {
+    return move_cut<false>(slab_grid, lattice, plane, dir, f, g, const_cast<double*>(msg));
+}
+

@@ -24,7 +24,8 @@ EXPORTS = (
     "lbm_slabs_plan", "lbm_slabs_create", "lbm_slabs_step", "lbm_slabs_residual",
     "lbm_slabs_get_populations", "lbm_slabs_set_populations", "lbm_slabs_fields",
     "lbm_slabs_count", "lbm_slabs_steps_done", "lbm_slabs_halo_bytes", "lbm_slabs_synchronize",
-    "lbm_slabs_last_error", "lbm_slabs_destroy",
+    "lbm_slabs_last_error", "lbm_slabs_destroy", "lbm_slabs_cut_populations",
+    "lbm_slabs_cut_values", "lbm_slabs_pack_cut", "lbm_slabs_unpack_cut",
 )
 
 _bound = False
@@ -57,12 +58,63 @@ def _lib():
     L.lbm_slabs_last_error.restype = ctypes.c_char_p
     L.lbm_slabs_destroy.argtypes = [vp]
     L.lbm_slabs_destroy.restype = None
+    L.lbm_slabs_cut_populations.argtypes = [ctypes.c_int, ctypes.c_int, _I, _I, _I, _I]
+    L.lbm_slabs_cut_values.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.lbm_slabs_cut_values.restype = ctypes.c_int64
+    L.lbm_slabs_pack_cut.argtypes = [P(Grid), ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D]
+    L.lbm_slabs_unpack_cut.argtypes = [P(Grid), ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D]
     _bound = True
     return L
 
 
 def _ints(values):
     return None if values is None else (ctypes.c_int * len(values))(*[int(v) for v in values])
+
+
+def cut_populations(lattice, direction):
+    """The flow and scalar directions that cross a cut upwards (+1) or downwards (-1)."""
+    L = _lib()
+    f, g = (ctypes.c_int * 15)(), (ctypes.c_int * 15)()
+    nf, ng = ctypes.c_int(), ctypes.c_int()
+    rc = L.lbm_slabs_cut_populations(int(lattice), int(direction), f, ctypes.byref(nf), g, ctypes.byref(ng))
+    if rc != LBM_OK:
+        raise LBMError(rc, L.lbm_slabs_last_error(None).decode())
+    return list(f)[:nf.value], list(g)[:ng.value]
+
+
+def _cut_args(f, g, lattice):
+    if f.dtype != np.float64 or g.dtype != np.float64 or not (f.flags.c_contiguous and g.flags.c_contiguous):
+        raise ValueError("populations must be C-contiguous float64 arrays")
+    if f.ndim != 4 or g.ndim != 4 or f.shape[0] != 15 or g.shape[0] != lattice or f.shape[1:] != g.shape[1:]:
+        raise ValueError("populations must be shaped (15, nz, ny, nx) and (lattice, nz, ny, nx)")
+    nz, ny, nx = f.shape[1:]
+    return Grid(nx, ny, nz)
+
+
+def pack_cut(f, g, lattice, plane, direction):
+    """The message of one cut (lbm_slabs_pack_cut): the populations of local plane `plane`
+    of a slab's host state (f, g) that cross the cut in `direction`."""
+    L = _lib()
+    grid = _cut_args(f, g, lattice)
+    msg = np.empty(L.lbm_slabs_cut_values(grid.nx, grid.ny, int(lattice)))
+    rc = L.lbm_slabs_pack_cut(ctypes.byref(grid), int(lattice), int(plane), int(direction),
+                              f.ctypes.data_as(_D), g.ctypes.data_as(_D), msg.ctypes.data_as(_D))
+    if rc != LBM_OK:
+        raise LBMError(rc, L.lbm_slabs_last_error(None).decode())
+    return msg
+
+
+def unpack_cut(msg, f, g, lattice, plane, direction):
+    """Write a message into local plane `plane` of a slab's host state (lbm_slabs_unpack_cut)."""
+    L = _lib()
+    grid = _cut_args(f, g, lattice)
+    msg = np.ascontiguousarray(msg, dtype=np.float64)
+    if msg.size != L.lbm_slabs_cut_values(grid.nx, grid.ny, int(lattice)):
+        raise ValueError("message of the wrong size")
+    rc = L.lbm_slabs_unpack_cut(ctypes.byref(grid), int(lattice), int(plane), int(direction),
+                                msg.ctypes.data_as(_D), f.ctypes.data_as(_D), g.ctypes.data_as(_D))
+    if rc != LBM_OK:
+        raise LBMError(rc, L.lbm_slabs_last_error(None).decode())
 
 
 def plan(nz, nslabs, boundary=_b.BC_CAVITY, owned=None):

@@ -35,11 +35,13 @@ KEY = {"u_max": "umax", "w_max": "wmax", "Nu_max": "mid_max", "Nu_min": "mid_min
 POS = {"u_max": "umax_z", "w_max": "wmax_x", "Nu_max": "mid_max_z", "Nu_min": "mid_min_z"}
 
 
-def run(n, Ra, precision="FP32", e4_mode=0, max_steps=None, chunk=2000):
+def run(n, Ra, precision="FP32", e4_mode=0, max_steps=None, chunk=2000, lattice=15,
+        adiabatic_mode=_lbm.ADIABATIC_SPECULAR):
     """One cavity from rest to its first steady plateau; returns the Table 1 quantities."""
     max_steps = max_steps or int(6000 * n)
-    sim = _lbm.LBM((n, n, n), 15, Ra=Ra, Pr=PR, Ma=U0 * math.sqrt(3.0),
-                   precision=getattr(_lbm, precision), e4_mode=e4_mode, residual_interval=100)
+    sim = _lbm.LBM((n, n, n), lattice, Ra=Ra, Pr=PR, Ma=U0 * math.sqrt(3.0),
+                   precision=getattr(_lbm, precision), e4_mode=e4_mode,
+                   adiabatic_mode=adiabatic_mode, residual_interval=100)
     t0 = time.perf_counter()
     res = -1.0
     while sim.steps_done < max_steps:
@@ -49,7 +51,8 @@ def run(n, Ra, precision="FP32", e4_mode=0, max_steps=None, chunk=2000):
             break
     dt = time.perf_counter() - t0
     nu = sim.nusselt()
-    out = {"n": n, "Ra": Ra, "precision": precision, "e4_mode": e4_mode,
+    out = {"n": n, "Ra": Ra, "precision": precision, "e4_mode": e4_mode, "lattice": lattice,
+           "adiabatic_mode": adiabatic_mode,
            "steps": sim.steps_done, "seconds": round(dt, 2), "residual_per_100": res,
            "steady": bool(0 <= res < STEADY)}
     for q, k in KEY.items():
@@ -70,6 +73,8 @@ def markdown(rows):
             ref = PAPER[q][r["Ra"]]
             cells.append(f"{r[q]:.4f} ({100 * (r[q] - ref) / ref:+.1f}%)")
         form = r["precision"] + ("" if r["e4_mode"] == 0 else " E=rho/9")
+        form += "" if r.get("lattice", 15) == 15 else " D3Q7"
+        form += "" if r.get("adiabatic_mode", 1) == 1 else " bounce-back"
         lines.append(f"| {r['n']} | {r['Ra']:g} | {form} | {r['steps']} | " + " | ".join(cells) + " |")
     return "\n".join(lines)
 
@@ -81,6 +86,8 @@ def main(argv=None):
     ap.add_argument("--e4-modes", type=int, nargs="*", default=[1])
     ap.add_argument("--fp64-grid", type=int, default=91)
     ap.add_argument("--fp64-Ra", type=float, nargs="*", default=[1e4, 1e5])
+    ap.add_argument("--variants", action="store_true",
+                    help="also the D3Q7 scalar lattice and the bounce-back adiabatic rule on every grid")
     ap.add_argument("--json", default=None)
     args = ap.parse_args(argv)
     rows = []
@@ -88,8 +95,12 @@ def main(argv=None):
     plan += [(args.grids[0], Ra, "FP32", m) for m in args.e4_modes if m != 0 for Ra in args.Ra]
     if args.fp64_grid:
         plan += [(args.fp64_grid, Ra, "FP64", 0) for Ra in args.fp64_Ra]
-    for n, Ra, prec, mode in plan:
-        r = run(n, Ra, prec, mode)
+    plan = [(n, Ra, prec, mode, 15, 1) for n, Ra, prec, mode in plan]
+    if args.variants:
+        plan += [(n, Ra, "FP32", 0, 7, 1) for n in args.grids for Ra in args.Ra]
+        plan += [(n, Ra, "FP32", 0, 15, 0) for n in args.grids for Ra in args.Ra]
+    for n, Ra, prec, mode, q, am in plan:
+        r = run(n, Ra, prec, mode, lattice=q, adiabatic_mode=am)
         rows.append(r)
         print(json.dumps(r), flush=True)
     print(markdown(rows), flush=True)

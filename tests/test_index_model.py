@@ -61,3 +61,19 @@ def test_pair_kernel_addressing(nx, ny, nz, q):
                             assert 0 <= got[e] < planes * P and 0 <= got_t[e] < P
                 pairs += 1
     assert pairs == (ny - 2) * (nz - 2) * (nx // 2)
+
+
+def test_division_by_invariant_integers():
+    # the batched kernel divides node and row indices by nx and ny as n M >> (32 + l) with
+    # l = ceil(log2 d), M = ceil(2^(32+l) / d) (batch.cu); that equals n // d for n < 2^31
+    import numpy as np
+    rng = np.random.default_rng(3)
+    for d in list(range(1, 300)) + [511, 512, 513, 1023, 1024, 4095, 65535, 2 ** 20 + 7]:
+        l = 0
+        while (1 << l) < d:
+            l += 1
+        M = -(-(1 << (32 + l)) // d)
+        ns = np.concatenate([np.arange(0, 4 * d + 3), rng.integers(0, 2 ** 31, 2000),
+                             [2 ** 31 - 1, 2 ** 31 - 2, (2 ** 31 - 1) // d * d, (2 ** 31 - 1) // d * d - 1]])
+        for n in ns.tolist():
+            assert (n * M) >> (32 + l) == n // d, (n, d)

@@ -160,3 +160,100 @@ def test_two_gloo_ranks_exchange_halo_planes(case):
         assert np.array_equal(f, F[:, zs]) and np.array_equal(g, G[:, zs])
         seen += list(zs)
     assert sorted(seen) == list(range(nz))
+
+
+def _rank_cut_messages(rank, world, port, case, steps, out):
+    """As _rank, but each cut carries only the library's message: the populations whose
+    e_z crosses it (lbm_slabs_pack_cut / lbm_slabs_unpack_cut)."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sl = _slabs()
+    nx, ny, nz, q, bc = case
+    p = _problem(nx, ny, nz, q, bc)
+    plan = sl.plan(nz, world, bc)
+    F, G = _random_state(p, 5)
+    zs = _slab_planes(plan, rank, nz)
+    f, g = F[:, zs].copy(), G[:, zs].copy()
+    prob = _with_nz(p, len(zs))
+    lo, hi, own = plan["halo_lo"][rank], plan["halo_hi"][rank], plan["nz_owned"][rank]
+    below, above = (rank - 1) % world, (rank + 1) % world
+    sizes = []
+    for _ in range(steps):
+        f, g = prob.step(f, g)
+        sends = []
+        if hi:  # upward set of my last owned plane, for the halo below of the slab above
+            m = sl.pack_cut(f, g, q, lo + own - 1, +1)
+            sizes.append(m.size)
+            sends.append(dist.isend(torch.from_numpy(m), above, tag=0))
+        if lo:  # downward set of my first owned plane, for the halo above of the slab below
+            m = sl.pack_cut(f, g, q, lo, -1)
+            sizes.append(m.size)
+            sends.append(dist.isend(torch.from_numpy(m), below, tag=1))
+        n = sl.pack_cut(f, g, q, 0, +1).size
+        if lo:
+            buf = torch.empty(n, dtype=torch.float64)
+            dist.recv(buf, below, tag=0)
+            sl.unpack_cut(buf.numpy(), f, g, q, 0, +1)
+        if hi:
+            buf = torch.empty(n, dtype=torch.float64)
+            dist.recv(buf, above, tag=1)
+            sl.unpack_cut(buf.numpy(), f, g, q, lo + own, -1)
+        for w in sends:
+            w.wait()
+    out[rank] = (zs[lo:lo + own], f[:, lo:lo + own], g[:, lo:lo + own], sizes[:1])
+    dist.destroy_process_group()
+
+
+@pytest.mark.timeout(180)
+@pytest.mark.parametrize("case", [(10, 8, 12, 15, oracle.BC_CAVITY), (9, 8, 10, 7, 6)],
+                         ids=["cavity", "periodic-z"])
+def test_two_gloo_ranks_exchange_the_library_cut_messages(case):
+    world, steps = 2, 5
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        procs = [ctx.Process(target=_rank_cut_messages, args=(r, world, port, case, steps, out))
+                 for r in range(world)]
+        for pr in procs:
+            pr.start()
+        for pr in procs:
+            pr.join(150)
+            assert pr.exitcode == 0
+        res = dict(out)
+    nx, ny, nz, q, bc = case
+    p = _problem(nx, ny, nz, q, bc)
+    F, G = p.run(*_random_state(p, 5), steps)
+    seen = []
+    for r in range(world):
+        zs, f, g, sizes = res[r]
+        assert np.array_equal(f, F[:, zs]) and np.array_equal(g, G[:, zs])
+        seen += list(zs)
+        assert sizes == [(5 + (5 if q == 15 else 1)) * nx * ny]  # a third / a quarter of the plane
+    assert sorted(seen) == list(range(nz))
+
+
+@pytest.mark.parametrize("q", [15, 7])
+def test_cut_message_sets_and_round_trip(q):
+    sl = _slabs()
+    up_f, up_g = sl.cut_populations(q, +1)
+    dn_f, dn_g = sl.cut_populations(q, -1)
+    ez = oracle.velocities(15)[:, 2]
+    assert up_f == [a for a in range(15) if ez[a] == 1] and dn_f == [a for a in range(15) if ez[a] == -1]
+    assert up_g == [a for a in up_f if a < q] and dn_g == [a for a in dn_f if a < q]
+    rng = np.random.default_rng(2)
+    f, g = rng.standard_normal((15, 4, 3, 5)), rng.standard_normal((q, 4, 3, 5))
+    msg = sl.pack_cut(f, g, q, 2, -1)
+    assert np.array_equal(msg[:15], f[dn_f[0], 2].ravel())
+    f2, g2 = np.zeros_like(f), np.zeros_like(g)
+    sl.unpack_cut(msg, f2, g2, q, 1, -1)
+    assert np.array_equal(f2[dn_f][:, 1], f[dn_f][:, 2]) and np.array_equal(g2[dn_g][:, 1], g[dn_g][:, 2])
+    others = [a for a in range(15) if a not in dn_f]
+    assert not f2[others].any() and not f2[:, [0, 2, 3]].any()
+    from paper_1710_04751_gb300.lbm import LBMError
+    with pytest.raises(LBMError):
+        sl.pack_cut(f, g, q, 4, +1)  # no plane 4 in a 4-plane slab
+
