@@ -744,7 +744,7 @@ def main(argv=None):
                     help="seconds the reference arm spends on warm-up + timed steps")
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of step_cavity_kernel<float,15>
     # at 128^3, from one ncu capture; to be retaken whenever that kernel changes
-    ap.add_argument("--traffic-q15", type=float, default=456.4e6,
+    ap.add_argument("--traffic-q15", type=float, default=455.9e6,
                     help="ncu DRAM bytes per launch of the FP32 D3Q15 step kernel at 128^3")
     ap.add_argument("--traffic-q7", type=float, default=None)
     args = ap.parse_args(argv)

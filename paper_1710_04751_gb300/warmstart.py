@@ -171,12 +171,36 @@ def fp64_reference(samples, n, steady_tol=1e-7, max_steps=300_000):
     return out
 
 
+def nu_error_vs_fp64(report, n, count, steady_tol=1e-6):
+    """The final hot-wall Nu of the warm-started (and the cold-started) FP32 runs of the
+    first `count` held-out cases where both converged, against the FP64 solver run to the
+    same convergence test from rest (the FP64 solver follows the FP64 oracle step for step
+    to 1e-12)."""
+    rows = [r for r in report["rows"] if r["cold_state"] == "converged" and r["warm_state"] == "converged"]
+    rows = rows[:count]
+    ref = fp64_reference([(r["Ra"], r["Pr"]) for r in rows], n, steady_tol=steady_tol)
+    out = []
+    for r, nu64 in zip(rows, ref):
+        if nu64 is None:
+            continue
+        out.append({"Ra": r["Ra"], "Pr": r["Pr"], "Nu_fp64": nu64,
+                    "warm_rel": (r["Nu_warm"] - nu64) / nu64, "cold_rel": (r["Nu_cold"] - nu64) / nu64})
+    summary = {"cases": len(out)}
+    if out:
+        w = np.array([abs(o["warm_rel"]) for o in out])
+        c = np.array([abs(o["cold_rel"]) for o in out])
+        summary.update({"warm_max_rel": float(w.max()), "warm_mean_rel": float(w.mean()),
+                        "cold_max_rel": float(c.max()), "cold_mean_rel": float(c.mean())})
+    return {"summary": summary, "rows": out}
+
+
 def experiment(n_train=64, count_train=400, count_test=50, n_big=128, count_big=8, epochs=40,
-               batch=4, rounds=50, seed=1, steady_tol=1e-6, log=print):
+               batch=4, rounds=50, seed=1, steady_tol=1e-6, count_fp64=12, log=print):
     """The learned warm start end to end: `count_train` steady states at n_train^3 with Ra
     log-uniform in [1e3, 1e6] and Pr log-uniform in [0.7, 7] (seed), the network trained on
     them, and cold against warm starts on `count_test` held-out samples at n_train^3 and
-    `count_big` of them at n_big^3 (the prediction resampled trilinearly)."""
+    `count_big` of them at n_big^3 (the prediction resampled trilinearly); the final Nu of
+    `count_fp64` of the n_train^3 cases against the FP64 solver."""
     import torch
     from .net import Net
     t0 = time.perf_counter()
@@ -197,11 +221,15 @@ def experiment(n_train=64, count_train=400, count_test=50, n_big=128, count_big=
     if count_big:
         big = evaluate(netw, test[:count_big], n_big, steady_tol=steady_tol, rounds=rounds)
         log(f"{n_big}^3: {big['summary']}")
+    fp64 = None
+    if count_fp64:
+        fp64 = nu_error_vs_fp64(rep, n_train, count_fp64, steady_tol=steady_tol)
+        log(f"Nu against the FP64 solver ({n_train}^3): {fp64['summary']}")
     out = {"train": {"samples": len(data["samples"]), "dropped": data["dropped"],
                      "generate_seconds": round(t_gen, 1), "epochs": epochs, "batch": batch,
                      "train_seconds": round(t_train, 1), "loss_first": hist[0],
                      "loss_last": hist[-1], "params": netw.param_count},
-           "test": rep, "big": big}
+           "test": rep, "big": big, "fp64": fp64}
     return out, netw
 
 
@@ -215,9 +243,11 @@ if __name__ == "__main__":
     ap.add_argument("--big", type=int, default=8)
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--rounds", type=int, default=50)
+    ap.add_argument("--fp64", type=int, default=12, help="held-out cases checked against the FP64 solver")
     ap.add_argument("--save", default=None, help="write the trained parameters (float32) here")
     a = ap.parse_args()
-    res, netw = experiment(a.n, a.train, a.test, 2 * a.n, a.big, a.epochs, rounds=a.rounds)
+    res, netw = experiment(a.n, a.train, a.test, 2 * a.n, a.big, a.epochs, rounds=a.rounds,
+                           count_fp64=a.fp64)
     if a.save:
         netw.get_params().tofile(a.save)
     print(json.dumps(res))
