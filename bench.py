@@ -461,12 +461,40 @@ def net_variant():
         return {"M": M, "N": N, "K": K, "ms": round(best * 1e3, 4), "tflops": round(tf, 1),
                 "frac": round(tf / peak, 4)}
 
+    def conv_rate(B, n, cin, cout, mode, reps=5):
+        """The implicit-GEMM convolution (no im2col matrix): time, TFLOP/s and the bytes it
+        must move at least (input and output once)."""
+        X = torch.randn((B, n ** 3, cin), device="cuda", generator=gen).to(torch.bfloat16)
+        ldw = (27 * cin + 63) // 64 * 64
+        W = (0.05 * torch.randn((cout, ldw), device="cuda", generator=gen)).to(torch.bfloat16)
+        bias = torch.zeros(cout, device="cuda")
+        out = torch.empty((B * n ** 3, cout), device="cuda",
+                          dtype=torch.bfloat16 if mode == net.CONV_BIAS_RELU_BF16 else torch.float32)
+        net.conv3d_bf16(X, n, W, out, mode=mode, bias=bias)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 1e30
+        for _ in range(reps):
+            e0.record(st)
+            net.conv3d_bf16(X, n, W, out, mode=mode, bias=bias)
+            e1.record(st)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        tf = 2.0 * B * n ** 3 * 27 * cin * cout / best / 1e12
+        nbytes = B * n ** 3 * (2 * cin + out.element_size() * cout) + cout * ldw * 2
+        return {"B": B, "n": n, "cin": cin, "cout": cout, "ms": round(best * 1e3, 4),
+                "tflops": round(tf, 1), "frac": round(tf / peak, 4),
+                "min_bytes": nbytes, "GB_per_s_of_min_bytes": round(nbytes / best / 1e9, 1)}
+
     M0 = 2 * 64 ** 3
     out = {
         "peak_tflops": peak, "peak_kind": kind,
         "gemm_large": gemm_rate(65536, 256, 8192, net.GEMM_F32),
-        "conv_fwd_L9": gemm_rate(M0, 32, 2624, net.GEMM_F32),      # 96 -> 32 channels at 64^3
-        "conv_dgrad_L9": gemm_rate(M0, 96, 896, net.GEMM_F32),     # input gradient
+        # the network's layer 9 at 64^3, batch 2 (96 -> 32 channels): the forward pass and
+        # the input gradient as implicit GEMMs, the weight gradient as a split-K GEMM over
+        # an im2col matrix
+        "conv_fwd_L9": conv_rate(2, 64, 96, 32, net.CONV_BIAS_RELU_BF16),
+        "conv_dgrad_L9": conv_rate(2, 64, 32, 96, net.CONV_F32),
         "conv_wgrad_L9": gemm_rate(2624, 32, M0, net.GEMM_F32_ADD, splits=64),
     }
     for B in (2, 4):

@@ -6,8 +6,10 @@
  * an accelerator around the method of arXiv:1710.04751, never a replacement: the
  * warm-started solver still runs until its own convergence criterion holds.
  *
- * Arithmetic: BF16 operands on the tcgen05 tensor cores with FP32 accumulation (every
- * convolution is a GEMM over an im2col matrix), FP32 master weights and Adam moments.
+ * Arithmetic: BF16 operands on the tcgen05 tensor cores with FP32 accumulation (the
+ * forward convolutions and the input gradients are implicit GEMMs that read their operand
+ * tiles straight from the activations; the weight gradients GEMMs over an im2col matrix),
+ * FP32 master weights and Adam moments.
  *
  * Errors follow include/lbm.h (LBM_OK or a negative LBM_E* code, the message in
  * lbm_last_error(NULL)).  Device pointers are caller-owned.
@@ -34,6 +36,20 @@ enum { LBM_GEMM_F32 = 0, LBM_GEMM_BF16 = 1, LBM_GEMM_F32_ADD = 2 };
 int lbm_nn_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, void* C,
                      int64_t ldc, int M, int N, int K, int out_mode, int splits,
                      void* cuda_stream);
+
+/* 3x3x3 convolution with zero padding as an implicit GEMM on the tensor cores (the
+ * network's convolutions, exposed for tests and reuse).  X: device BF16 activations
+ * [batch][n][n][n][cin], channels last (voxel ((b n + z) n + y) n + x); W: device BF16
+ * weights [cout][ldw] with K index tap * cin + ci, tap = (kz 3 + ky) 3 + kx reading the
+ * input at (z + kz - 1, y + ky - 1, x + kx - 1) (ldw >= 27 cin, a multiple of 8); out
+ * [batch n^3][cout]: LBM_CONV_BIAS_RELU_BF16 writes BF16 max(y + bias, 0) (bias: device
+ * FP32 [cout]), LBM_CONV_F32 writes the FP32 sums y.  Each K block's operand tile is one
+ * TMA box of X shifted by the tap, zero-filled outside the grid: no im2col matrix.  cin a
+ * multiple of 32, n a power of two in 2..256, cout <= 256, 16-byte aligned bases; else
+ * LBM_EINVAL.  Waits for `cuda_stream` (bounded); LBM_ETIMEOUT as lbm_nn_gemm_bf16. */
+enum { LBM_CONV_BIAS_RELU_BF16 = 0, LBM_CONV_F32 = 1 };
+int lbm_nn_conv3d_bf16(const void* X, int batch, int n, int cin, const void* W, int64_t ldw,
+                       int cout, const float* bias, void* out, int mode, void* cuda_stream);
 
 /* Diagnostic of the bounded waits inside the tensor-core kernels (the paper has no
  * counterpart).  Launches the GEMM kernel on one 128 x 32 tile with its operand loads

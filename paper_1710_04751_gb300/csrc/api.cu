@@ -183,6 +183,7 @@ DevParams<real> lbm::dev_params(const lbm_ctx* c) {
     p.nz = c->grid.nz;
     p.ncell = c->ncell;
     p.plane = c->plane;
+    p.cell0 = c->cell0;
     return p;
 }
 template DevParams<double> lbm::dev_params<double>(const lbm_ctx*);
@@ -320,6 +321,7 @@ int lbm::create_context(const lbm_grid* grid, int lattice, const lbm_params* par
     c->dev.result = reinterpret_cast<double*>(base + L.result);
     c->dev.resid_bits = reinterpret_cast<unsigned long long*>(base + L.bits);
     c->dev.nonfinite = reinterpret_cast<int*>(base + L.bits + 64);
+    c->dev.step_ctr = reinterpret_cast<unsigned*>(base + L.bits + 128);
 
     rc = LBM_OK;
     if (cudaMemsetAsync(base + L.bits, 0, 256, c->stream) != cudaSuccess)

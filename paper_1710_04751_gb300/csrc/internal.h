@@ -22,6 +22,7 @@ struct DevParams {
     int nx, ny, nz;
     int64_t ncell;      // nx * ny * nz
     int64_t plane;      // elements between population planes (ncell rounded up to 64)
+    int64_t cell0;      // global index of cell 0 (slabs of a larger grid; 0 otherwise)
 };
 
 // Host-side view of one context's device buffers for the launchers.
@@ -37,6 +38,7 @@ struct DevState {
     double* result;     // reduction results
     unsigned long long* resid_bits;
     int* nonfinite;
+    unsigned* step_ctr; // 16-bit forms: steps taken, per buffer parity (the rounding dither)
 };
 
 constexpr int kPartialBlocks = 1024;   // max blocks of the face reduction

@@ -85,3 +85,28 @@ extern "C" int lbm_nn_gemm_timeout_probe(void* cuda_stream) {
         return record_error(nullptr, LBM_ECUDA, "probe launch failed: %s", cudaGetErrorString(e));
     return finish(st, err);  // LBM_ETIMEOUT when the bounded wait ran out as intended
 }
+
+extern "C" int lbm_nn_conv3d_bf16(const void* X, int batch, int n, int cin, const void* W,
+                                  int64_t ldw, int cout, const float* bias, void* out, int mode,
+                                  void* cuda_stream) {
+    if (!X || !W || !out || (mode == LBM_CONV_BIAS_RELU_BF16 && !bias))
+        return record_error(nullptr, LBM_EINVAL, "NULL operand%s");
+    if (mode != LBM_CONV_BIAS_RELU_BF16 && mode != LBM_CONV_F32)
+        return record_error(nullptr, LBM_EINVAL, "invalid convolution mode%s");
+    if (!nn::conv_implicit_supported(n, cin, cout) || batch < 1)
+        return record_error(nullptr, LBM_EINVAL,
+                            "implicit convolution needs cin a multiple of 32, n a power of two in 2..256, "
+                            "1 <= cout <= 256 and batch >= 1%s");
+    int* err = error_word();
+    if (!err) return record_error(nullptr, LBM_ECUDA, "no CUDA device%s");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const cudaError_t e = nn::conv_implicit(
+        static_cast<const __nv_bfloat16*>(X), batch, n, cin, static_cast<const __nv_bfloat16*>(W), ldw,
+        cout, bias, out, mode == LBM_CONV_BIAS_RELU_BF16 ? nn::CONV_BIAS_RELU_BF16 : nn::CONV_F32, err, st);
+    if (e == cudaErrorInvalidValue)
+        return record_error(nullptr, LBM_EINVAL, "invalid convolution shape, stride or alignment%s");
+    if (e != cudaSuccess)
+        return record_error(nullptr, LBM_ECUDA, "convolution launch failed: %s", cudaGetErrorString(e));
+    return finish(st, err);
+}
+

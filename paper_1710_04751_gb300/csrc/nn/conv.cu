@@ -1,0 +1,299 @@
+// conv.cu -- 3x3x3 convolutions with zero padding as implicit GEMMs on the tcgen05 tensor
+// cores:
+//   Y[m][co] = sum_{tap, ci} X[m shifted by tap][ci] * W[co][tap * cin + ci]
+// for activations X [B][n][n][n][cin] (BF16, channels last, voxel m = ((b n + z) n + y) n + x)
+// and W [cout][Kp] (K index tap * cin + ci, tap = (kz 3 + ky) 3 + kx reading the input at
+// (z + kz - 1, y + ky - 1, x + kx - 1)).  No im2col matrix goes through HBM: the A operand of
+// the K block (tap, channel chunk) is loaded straight from X by one 5D TMA box
+//   {BKC channels, bx, by, bz, bb} at (c0, x0 + kx - 1, y0 + ky - 1, z0 + kz - 1, b0),
+// the 128 voxels of the M tile (bx by bz bb = 128, whole x-rows) seen through the tap's
+// shift; the box's out-of-range part -- the zero padding -- arrives as zeros (TMA fill).
+// The box lands in shared memory exactly as the 2D box of an im2col matrix would (rows of
+// BKC channels, 128-byte swizzle for 64 channels, 64-byte swizzle for 32), so the MMA side
+// is the GEMM's: one CTA of 128 threads per 128 x BN tile, warp 0 lane 0 producing into a
+// 4-stage mbarrier ring, warp 1 lane 0 issuing tcgen05.mma into TMEM, all four warps
+// draining the accumulator.  Epilogues: bias + ReLU + BF16 (the forward pass) or FP32 (the
+// input gradient, the convolution of the output gradient with the mirrored weights).
+// Every wait is bounded as in gemm.cu.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "nn.h"
+#include "tc.cuh"
+
+namespace lbm {
+namespace nn {
+
+namespace {
+
+constexpr int CBM = 128, CSTAGES = 4;
+
+template <int BN, int BKC>
+struct ConvSmem {
+    static constexpr int A_BYTES = CBM * BKC * 2;
+    static constexpr int B_BYTES = BN * BKC * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int BYTES = 1024 + CSTAGES * STAGE + 256;
+    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+struct ConvArgs {
+    int M, N;               // output rows (B n^3) and columns (cout)
+    int n;                  // grid edge
+    int chunks;             // channel chunks of BKC per tap (cin / BKC)
+    int bx, by, bz;         // the M tile as a box of the grid (with bb = 128 / (bx by bz))
+    int mode;               // CONV_BIAS_RELU_BF16 or CONV_F32
+    void* C;                // output [M][N]
+    const float* bias;      // bias[N] (CONV_BIAS_RELU_BF16)
+    int* err;
+};
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, int bkc) {
+    return bkc == 64 ? sdesc_k_sw128(saddr) : sdesc_k_sw64(saddr);
+}
+
+template <int BN, int BKC>
+__global__ void __launch_bounds__(128, 1)
+    conv_bf16_kernel(const __grid_constant__ CUtensorMap tmX,
+                     const __grid_constant__ CUtensorMap tmW, ConvArgs args) {
+    using L = ConvSmem<BN, BKC>;
+    extern __shared__ uint8_t conv_smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(conv_smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + CSTAGES * L::STAGE);
+    uint64_t* empty = full + CSTAGES;
+    uint64_t* done = empty + CSTAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ volatile int failed;
+
+    if (*static_cast<volatile int*>(args.err) != 0) return;  // another CTA timed out
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * BN;
+    const int nkb = 27 * args.chunks;
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int s = 0; s < CSTAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(done, 1);
+        mbar_fence_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, L::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0;
+    if (warp == 0 && lane == 0) {
+        // the tile's first voxel (its x0 is 0 unless a row holds several tiles)
+        const int n = args.n;
+        const int x0 = m0 % n, y0 = (m0 / n) % n, z0 = (m0 / (n * n)) % n, b0 = m0 / (n * n * n);
+        int tap = 0, chunk = 0;
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % CSTAGES;
+            const uint32_t ph = (uint32_t)(i / CSTAGES) & 1u;
+            if (i >= CSTAGES && !mbar_wait(empty + s, ph ^ 1u, args.err, 1, &failed)) {
+                failed = 1;
+                break;
+            }
+            if (failed) break;
+            uint8_t* a = smem + s * L::STAGE;
+            const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
+            mbar_expect_tx(full + s, L::STAGE);
+            tma_load_5d(a, &tmX, full + s, chunk * BKC, x0 + kx - 1, y0 + ky - 1, z0 + kz - 1, b0);
+            tma_load_2d(a + L::A_BYTES, &tmW, full + s, i * BKC, n0);
+            ++issued;
+            if (++chunk == args.chunks) {
+                chunk = 0;
+                ++tap;
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_bf16_f32(CBM, BN);
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % CSTAGES;
+            const uint32_t ph = (uint32_t)(i / CSTAGES) & 1u;
+            if (failed || !mbar_wait(full + s, ph, args.err, 2, &failed)) {
+                failed = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a = smem_u32(smem + s * L::STAGE), b = a + L::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BKC / 16; ++kk)
+                mma_bf16(tmem, sdesc(a + kk * 32, BKC), sdesc(b + kk * 32, BKC), idesc,
+                         (i > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(empty + s);
+        }
+        mma_commit(done);  // also when stopped early: every issued MMA drains before dealloc
+    }
+    __syncwarp();
+    if (!mbar_wait(done, 0, args.err, 3)) failed = 1;
+    __syncthreads();
+    const bool ok = !failed;
+    if (warp == 0 && lane == 0 && failed) {  // let every started copy land
+        for (int i = max(0, issued - CSTAGES); i < issued; ++i)
+            mbar_wait(full + (i % CSTAGES), (uint32_t)(i / CSTAGES) & 1u, args.err, 4);
+    }
+    tc_fence_after();
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            const int col0 = n0 + c;
+            if (row >= args.M || col0 >= args.N) continue;
+            const bool whole = col0 + 16 <= args.N && (args.N % 8) == 0;  // 16-byte stores
+            if (args.mode == CONV_BIAS_RELU_BF16) {
+                __nv_bfloat16* C = static_cast<__nv_bfloat16*>(args.C) + (int64_t)row * args.N;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    v[j] = fmaxf(v[j] + (col0 + j < args.N ? args.bias[col0 + j] : 0.f), 0.f);
+                if (whole) {
+                    uint4 pk[2];
+                    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(pk);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                    reinterpret_cast<uint4*>(C + col0)[0] = pk[0];
+                    reinterpret_cast<uint4*>(C + col0)[1] = pk[1];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (col0 + j < args.N) C[col0 + j] = __float2bfloat16_rn(v[j]);
+                }
+            } else {
+                float* C = static_cast<float*>(args.C) + (int64_t)row * args.N;
+                if (whole && (args.N % 4) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        reinterpret_cast<float4*>(C + col0)[j] =
+                            make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (col0 + j < args.N) C[col0 + j] = v[j];
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, L::TMEM_COLS);
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// X [B][n][n][n][cin] as a 5D tensor (innermost first) read in boxes of
+// {bkc, bx, by, bz, bb}; out-of-range elements read as zeros.
+bool make_x_map(CUtensorMap* map, const void* X, int B, int n, int cin, int bkc, int bx, int by,
+                int bz, int bb) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[5] = {(cuuint64_t)cin, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n,
+                                (cuuint64_t)B};
+    const cuuint64_t row = (cuuint64_t)cin * 2;
+    const cuuint64_t strides[4] = {row, row * n, row * n * n, row * n * n * n};
+    const cuuint32_t box[5] = {(cuuint32_t)bkc, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz,
+                               (cuuint32_t)bb};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(X), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              bkc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// W [N][Kp] (row stride ld) read in boxes of bkc x box_rows.
+bool make_w_map(CUtensorMap* map, const void* W, int N, int K, long long ld, int bkc, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)bkc, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(W), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              bkc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int BKC>
+cudaError_t launch_conv(const CUtensorMap& tx, const CUtensorMap& tw, const ConvArgs& a,
+                        cudaStream_t st) {
+    using L = ConvSmem<BN, BKC>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(conv_bf16_kernel<BN, BKC>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+    });
+    if (attr != cudaSuccess) return attr;
+    const dim3 grid((a.M + CBM - 1) / CBM, (a.N + BN - 1) / BN, 1);
+    conv_bf16_kernel<BN, BKC><<<grid, 128, L::BYTES, st>>>(tx, tw, a);
+    return cudaGetLastError();
+}
+
+template <int BKC>
+cudaError_t launch_conv_bkc(const CUtensorMap& tx, const CUtensorMap& tw, const ConvArgs& a,
+                            int BN, cudaStream_t st) {
+    switch (BN) {
+    case 32: return launch_conv<32, BKC>(tx, tw, a, st);
+    case 64: return launch_conv<64, BKC>(tx, tw, a, st);
+    case 128: return launch_conv<128, BKC>(tx, tw, a, st);
+    default: return launch_conv<256, BKC>(tx, tw, a, st);
+    }
+}
+
+}  // namespace
+
+bool conv_implicit_supported(int n, int cin, int cout) {
+    return cin % 32 == 0 && n >= 2 && n <= 256 && (n & (n - 1)) == 0 && cout >= 1 && cout <= 256;
+}
+
+cudaError_t conv_implicit(const __nv_bfloat16* X, int B, int n, int cin, const __nv_bfloat16* W,
+                          long long ldw, int cout, const float* bias, void* out, int mode, int* err,
+                          cudaStream_t st) {
+    if (!conv_implicit_supported(n, cin, cout) || B < 1 || ((uintptr_t)X & 15) || ((uintptr_t)W & 15) ||
+        (ldw % 8) || ldw < 27LL * cin || (mode == CONV_BIAS_RELU_BF16 && !bias) ||
+        (mode != CONV_BIAS_RELU_BF16 && mode != CONV_F32))
+        return cudaErrorInvalidValue;
+    const int bkc = cin % 64 == 0 ? 64 : 32;
+    // the 128-voxel M tile as a box: whole x-rows, then y, z and samples
+    const int bx = n < 128 ? n : 128;
+    const int by = 128 / bx < n ? 128 / bx : n;
+    const int bz = 128 / (bx * by) < n ? 128 / (bx * by) : n;
+    const int bb = 128 / (bx * by * bz);
+    if (bx * by * bz * bb != 128) return cudaErrorInvalidValue;
+    const int BN = cout <= 32 ? 32 : cout <= 64 ? 64 : cout <= 128 ? 128 : 256;
+    CUtensorMap tx, tw;
+    if (!make_x_map(&tx, X, B, n, cin, bkc, bx, by, bz, bb) ||
+        !make_w_map(&tw, W, cout, 27 * cin, ldw, bkc, BN))
+        return cudaErrorInvalidValue;
+    ConvArgs a{B * n * n * n, cout, n, cin / bkc, bx, by, bz, mode, out, bias, err};
+    return bkc == 64 ? launch_conv_bkc<64>(tx, tw, a, BN, st) : launch_conv_bkc<32>(tx, tw, a, BN, st);
+}
+
+}  // namespace nn
+}  // namespace lbm

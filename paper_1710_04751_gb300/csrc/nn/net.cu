@@ -62,6 +62,7 @@ struct lbm_net {
     void* arena;
     size_t arena_bytes;
     int step;
+    int implicit;       // convolutions as implicit GEMMs where conv_implicit_supported
     cudaStream_t stream;
     int device;
     int sm_count;
@@ -219,6 +220,11 @@ int conv_fwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, __nv_bfloat16* A)
     const int n = N->n >> k.level;
     const int64_t M = (int64_t)B * N->V[k.level];
     cudaStream_t st = N->stream;
+    if (N->implicit && conv_implicit_supported(n, k.cin, k.cout)) {  // no im2col matrix
+        NET_CUDA(N, conv_implicit(X, B, n, k.cin, k.Wb, k.Kp, k.cout, k.b, A, CONV_BIAS_RELU_BF16,
+                                  N->err, st));
+        return LBM_OK;
+    }
     NET_CUDA(N, im2col(X, B, n, k.cin, k.Kp, N->xcol, st));
     NET_CUDA(N, gemm_bf16(N->xcol, k.Kp, k.Wb, k.Kp, N->y, k.cout, (int)M, k.cout, k.Kp, GEMM_F32, 1,
                           N->err, st));
@@ -240,10 +246,15 @@ int conv_bwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, const __nv_bfloat
     NET_CUDA(N, transpose(N->xcol, M, k.Kp, k.Kp, N->xcolT, M, st));
     NET_CUDA(N, gemm_bf16_add_splitk(N->xcolT, M, N->dZT, M, k.dWT, k.cout, k.Kp, k.cout, (int)M,
                                      wgrad_splits(N, k, M), N->ws, N->ws_floats, N->err, st));
-    if (dX) {  // dX = im2col(dZ) Wf^T (the xcol scratch is free again)
-        NET_CUDA(N, im2col(N->dZ, B, n, k.cout, k.Kpf, N->xcol, st));
-        NET_CUDA(N, gemm_bf16(N->xcol, k.Kpf, k.Wf, k.Kpf, dX, k.cin, (int)M, k.cin, k.Kpf,
-                              GEMM_F32, 1, N->err, st));
+    if (dX) {  // dX = im2col(dZ) Wf^T: the convolution of dZ with the mirrored weights
+        if (N->implicit && conv_implicit_supported(n, k.cout, k.cin)) {
+            NET_CUDA(N, conv_implicit(N->dZ, B, n, k.cout, k.Wf, k.Kpf, k.cin, nullptr, dX, CONV_F32,
+                                      N->err, st));
+        } else {  // the xcol scratch is free again
+            NET_CUDA(N, im2col(N->dZ, B, n, k.cout, k.Kpf, N->xcol, st));
+            NET_CUDA(N, gemm_bf16(N->xcol, k.Kpf, k.Wf, k.Kpf, dX, k.cin, (int)M, k.cin, k.Kpf,
+                                  GEMM_F32, 1, N->err, st));
+        }
     }
     return LBM_OK;
 }
@@ -419,6 +430,7 @@ extern "C" int lbm_net_create(const lbm_net_config* cfg, lbm_net** out) {
     N->cfg = c;
     N->n = c.n;
     N->B = c.max_batch;
+    N->implicit = 1;
     N->stream = static_cast<cudaStream_t>(c.cuda_stream);
     for (int lv = 0; lv < 3; ++lv) {
         const int64_t m = c.n >> lv;

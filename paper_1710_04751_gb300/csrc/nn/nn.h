@@ -27,6 +27,16 @@ cudaError_t gemm_bf16_add_splitk(const __nv_bfloat16* A, long long lda, const __
                                  int splits, float* ws, size_t ws_floats, int* err, cudaStream_t st);
 size_t gemm_splitk_floats(int M, long long ldc, int K, int splits);
 
+// 3x3x3 convolution with zero padding as an implicit GEMM (conv.cu): X [B][n][n][n][cin]
+// BF16 channels last, W [cout][ldw] BF16 (K index tap * cin + ci), out [B n^3][cout]:
+// CONV_BIAS_RELU_BF16 writes bf16(max(y + bias, 0)), CONV_F32 writes y.  Needs
+// conv_implicit_supported (cin a multiple of 32, n a power of two); 16-byte aligned bases.
+enum { CONV_BIAS_RELU_BF16 = 0, CONV_F32 = 1 };
+bool conv_implicit_supported(int n, int cin, int cout);
+cudaError_t conv_implicit(const __nv_bfloat16* X, int B, int n, int cin, const __nv_bfloat16* W,
+                          long long ldw, int cout, const float* bias, void* out, int mode, int* err,
+                          cudaStream_t st);
+
 // Diagnostic: the GEMM kernel on one tile with its operand loads withheld, so that its
 // bounded wait runs out (10 ms) and it records a timeout in *err (see gemm.cu).
 cudaError_t gemm_timeout_probe(const __nv_bfloat16* operand, float* C, int* err, cudaStream_t st);

@@ -101,12 +101,14 @@ __device__ __forceinline__ void pull(const S* __restrict__ Fin, const S* __restr
 // Macroscopic variables, both collisions and the store of one node.  UNIT: the paper's
 // unit higher-order rates (collide_unit.cuh), for which the post-collision state needs
 // only the low-order moments of the pulled populations.
+// seed: the node's rounding dither (dither_seed of its global index and the step) for
+// the stochastically rounded flow stores of the 16-bit forms; unused otherwise.
 template <typename S, int Q, bool UNIT = false>
 __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15],
                                               typename Storage<S>::real (&g)[Q],
                                               S* __restrict__ Fout, S* __restrict__ Gout,
                                               float* __restrict__ Tout,
-                                              const ParamsOf<S>& p, int64_t c) {
+                                              const ParamsOf<S>& p, int64_t c, uint32_t seed = 0) {
     using real = typename Storage<S>::real;
     using St = Storage<S>;
     const int64_t P = p.plane;
@@ -127,8 +129,10 @@ __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15]
         flow_unit<real>(dm, Fx, Fy, Fz, r, inv_rho, u, D);
         populations15<real>(D, f);  // f~ - w_a: the 16-bit forms store it as it is
 #pragma unroll
-        for (int a = 0; a < 15; ++a)
-            Fout[a * P + c] = St::store(St::deviation ? f[a] : f[a] + p.wf[a], real(0));
+        for (int a = 0; a < 15; ++a) {
+            if constexpr (St::deviation) Fout[a * P + c] = store16<S, St::sr_flow>(f[a], dither_of(seed, a));
+            else Fout[a * P + c] = St::store(f[a] + p.wf[a], real(0));
+        }
         if constexpr (Q == 15) {
             thermal15_unit<real>(T, m0, mx, my, mz, u, r, D);
             populations15<real>(D, g);
@@ -137,8 +141,12 @@ __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15]
         }
         if constexpr (St::deviation) Tout[c] = T;  // the reference of the stored deviations
 #pragma unroll
-        for (int a = 0; a < Q; ++a)  // g~ - w^phi_a T: the 16-bit forms' stored value
-            Gout[a * P + c] = St::store(St::deviation ? g[a] : fmad(p.wg[a], T, g[a]), real(0));
+        for (int a = 0; a < Q; ++a) {  // g~ - w^phi_a T: the 16-bit forms' stored value
+            if constexpr (St::deviation)
+                Gout[a * P + c] = store16<S, St::sr_thermal>(g[a], dither_of(seed, 15 + a));
+            else
+                Gout[a * P + c] = St::store(fmad(p.wg[a], T, g[a]), real(0));
+        }
         return;
     }
     real T = real(0);
@@ -149,7 +157,12 @@ __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15]
     real ux, uy, uz;
     collide_flow<real>(f, p.ext_fx, p.ext_fy, Fz, p, ux, uy, uz);
 #pragma unroll
-    for (int a = 0; a < 15; ++a) Fout[a * P + c] = St::store(f[a], p.wf[a]);
+    for (int a = 0; a < 15; ++a) {
+        if constexpr (St::deviation)
+            Fout[a * P + c] = store16<S, St::sr_flow>(f[a] - p.wf[a], dither_of(seed, a));
+        else
+            Fout[a * P + c] = St::store(f[a], p.wf[a]);
+    }
     if constexpr (Q == 15) collide_thermal15<real>(g, ux, uy, uz, p);
     else collide_thermal7<real>(g, ux, uy, uz, p);
     if constexpr (St::deviation) Tout[c] = T;  // collision conserves T: the node's reference
@@ -173,7 +186,8 @@ template <typename S, int Q, bool INTERIOR, bool UNIT = false>
 __device__ __forceinline__ void cavity_node(const S* __restrict__ Fin, const S* __restrict__ Gin,
                                             const float* __restrict__ Tin, S* __restrict__ Fout,
                                             S* __restrict__ Gout, float* __restrict__ Tout,
-                                            const ParamsOf<S>& p, int i, int j, int k) {
+                                            const ParamsOf<S>& p, int i, int j, int k,
+                                            uint32_t step = 0) {
     using real = typename Storage<S>::real;
     using St = Storage<S>;
     const int nx = p.nx;
@@ -213,7 +227,9 @@ __device__ __forceinline__ void cavity_node(const S* __restrict__ Fin, const S* 
     } else {
         pull<S, Q>(Fin, Gin, Tin, p, i, j, k, c, f, g);
     }
-    collide_store<S, Q, UNIT>(f, g, Fout, Gout, Tout, p, c);
+    uint32_t seed = 0;
+    if constexpr (St::deviation) seed = dither_seed((uint32_t)(p.cell0 + c), step);
+    collide_store<S, Q, UNIT>(f, g, Fout, Gout, Tout, p, c, seed);
 }
 
 // Blocks per SM the single-precision kernels are built for: 7 for D3Q15 (at most 72

@@ -65,6 +65,15 @@ struct Pack<__half> {
     __device__ __forceinline__ static float2 to_float2(two v) { return __half22float2(v); }
     __device__ __forceinline__ static two from_float2(float2 v) { return __float22half2_rn(v); }
     __device__ __forceinline__ static float to_float(__half v) { return __half2float(v); }
+    // both lanes rounded stochastically (storage.cuh), lane .x with dither dx, .y with dy
+    __device__ __forceinline__ static two from_float2_sr(float2 v, uint32_t dx, uint32_t dy) {
+        return __halves2half2(Storage<__half>::store_sr(v.x, dx), Storage<__half>::store_sr(v.y, dy));
+    }
+    template <bool SR>
+    __device__ __forceinline__ static two store2(float2 v, uint32_t dx, uint32_t dy) {
+        if constexpr (SR) return from_float2_sr(v, dx, dy);
+        else return from_float2(v);
+    }
 };
 template <>
 struct Pack<__nv_bfloat16> {
@@ -72,7 +81,19 @@ struct Pack<__nv_bfloat16> {
     __device__ __forceinline__ static float2 to_float2(two v) { return __bfloat1622float2(v); }
     __device__ __forceinline__ static two from_float2(float2 v) { return __float22bfloat162_rn(v); }
     __device__ __forceinline__ static float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ __forceinline__ static two from_float2_sr(float2 v, uint32_t dx, uint32_t dy) {
+        return __halves2bfloat162(Storage<__nv_bfloat16>::store_sr(v.x, dx),
+                                  Storage<__nv_bfloat16>::store_sr(v.y, dy));
+    }
+    template <bool SR>
+    __device__ __forceinline__ static two store2(float2 v, uint32_t dx, uint32_t dy) {
+        if constexpr (SR) return from_float2_sr(v, dx, dy);
+        else return from_float2(v);
+    }
 };
+
+// The dither seed of node c0 + 1 from that of node c0 (dither_seed is linear in the node).
+__device__ __forceinline__ uint32_t next_node_seed(uint32_t seed) { return seed + 0x2C1B3C6Du; }
 
 // Two lanes of FP32 as one arithmetic value (the unit-rate collisions of
 // collide_unit.cuh are templates over it): every operator is one packed instruction.
@@ -367,7 +388,7 @@ template <typename S, int Q>
 __device__ __forceinline__ void pair_collide_store(float2 (&f)[15], float2 (&g)[Q],
                                                    S* __restrict__ Fout, S* __restrict__ Gout,
                                                    float* __restrict__ Tout, const PairParams& q,
-                                                   int P, int c0) {
+                                                   int P, int c0, uint32_t seed) {
     using Pk = Pack<S>;
     using two = typename Pk::two;
     float2 T = g[0];
@@ -377,9 +398,12 @@ __device__ __forceinline__ void pair_collide_store(float2 (&f)[15], float2 (&g)[
     const float2 Fz = fma2(q.gbeta, sub2(T, q.T0), q.fz);
     Vel2 vu;
     collide_flow2(f, Fz, q, vu);
+    const uint32_t seed1 = next_node_seed(seed);
 #pragma unroll
     for (int a = 0; a < 15; ++a)
-        *reinterpret_cast<two*>(Fout + a * P + c0) = Pk::from_float2(sub2(f[a], q.wf[a]));
+        *reinterpret_cast<two*>(Fout + a * P + c0) =
+            Pk::template store2<Storage<S>::sr_flow>(sub2(f[a], q.wf[a]), dither_of(seed, a),
+                                                     dither_of(seed1, a));
     if constexpr (Q == 15) collide_thermal15_2(g, vu, q);
     else collide_thermal7_2(g, vu, q);
     // the collision conserves T: it is the reference of this node's stored deviations
@@ -513,7 +537,8 @@ template <typename S, int Q>
 __device__ __forceinline__ void pair_collide_store_lean(float2 (&f)[15], float2 (&g)[Q],
                                                         S* __restrict__ Fout, S* __restrict__ Gout,
                                                         float* __restrict__ Tout,
-                                                        const PairParams& q, int P, int c0) {
+                                                        const PairParams& q, int P, int c0,
+                                                        uint32_t seed) {
     using Pk = Pack<S>;
     using two = typename Pk::two;
     float2 T = g[0];
@@ -544,9 +569,11 @@ __device__ __forceinline__ void pair_collide_store_lean(float2 (&f)[15], float2 
             *reinterpret_cast<two*>(Gout + a * P + c0) = Pk::from_float2(fma2(q.nwg[a], T, g[a]));
     }
     populations15_2(add15_2(df, flow_increment2(mf, inv_rho, Fz, q, vu)), f);
+    const uint32_t seed1 = next_node_seed(seed);
 #pragma unroll
     for (int a = 0; a < 15; ++a)
-        *reinterpret_cast<two*>(Fout + a * P + c0) = Pk::from_float2(f[a]);
+        *reinterpret_cast<two*>(Fout + a * P + c0) =
+            Pk::template store2<Storage<S>::sr_flow>(f[a], dither_of(seed, a), dither_of(seed1, a));
 }
 
 // The pair update after the pull: f holds the pulled flow deviations (f - w_a), g the pulled
@@ -554,13 +581,13 @@ __device__ __forceinline__ void pair_collide_store_lean(float2 (&f)[15], float2 
 template <typename S, int Q>
 __device__ __forceinline__ void pair_finish(float2 (&f)[15], float2 (&g)[Q], S* __restrict__ Fout,
                                             S* __restrict__ Gout, float* __restrict__ Tout,
-                                            const PairParams& q, int P, int c0) {
+                                            const PairParams& q, int P, int c0, uint32_t seed) {
     if constexpr (Q == 15 ? LBM_PAIR_LEAN_Q15 : LBM_PAIR_LEAN_Q7) {
-        pair_collide_store_lean<S, Q>(f, g, Fout, Gout, Tout, q, P, c0);
+        pair_collide_store_lean<S, Q>(f, g, Fout, Gout, Tout, q, P, c0, seed);
     } else {
 #pragma unroll
         for (int a = 0; a < 15; ++a) f[a] = add2(f[a], q.wf[a]);
-        pair_collide_store<S, Q>(f, g, Fout, Gout, Tout, q, P, c0);
+        pair_collide_store<S, Q>(f, g, Fout, Gout, Tout, q, P, c0, seed);
     }
 }
 
@@ -583,7 +610,7 @@ __device__ __forceinline__ void pair_node(const S* __restrict__ Fin, const S* __
                                           const float* __restrict__ Tin, S* __restrict__ Fout,
                                           S* __restrict__ Gout, float* __restrict__ Tout,
                                           const PairParams& q, int nx, int nxy, int P, int c0,
-                                          bool lo, bool hi) {
+                                          bool lo, bool hi, uint32_t seed) {
     using Pk = Pack<S>;
     using two = typename Pk::two;
     float2 g[Q], f[15];
@@ -634,7 +661,7 @@ __device__ __forceinline__ void pair_node(const S* __restrict__ Fin, const S* __
             f[a] = make_float2(Pk::to_float(Fs[c0]), Pk::to_float(Fs[i1]));
         }
     }
-    pair_finish<S, Q>(f, g, Fout, Gout, Tout, q, P, c0);
+    pair_finish<S, Q>(f, g, Fout, Gout, Tout, q, P, c0, seed);
 }
 
 // ---------------------------------------------------------------------------------
@@ -648,7 +675,7 @@ __device__ __forceinline__ void pair_node_unit(const S* __restrict__ Fin, const 
                                                const float* __restrict__ Tin, S* __restrict__ Fout,
                                                S* __restrict__ Gout, float* __restrict__ Tout,
                                                const PairParams& q, int nx, int nxy, int P, int c0,
-                                               bool lo, bool hi) {
+                                               bool lo, bool hi, uint32_t seed) {
     using Pk = Pack<S>;
     using two = typename Pk::two;
     Pair m0, mx, my, mz;
@@ -711,8 +738,11 @@ __device__ __forceinline__ void pair_node_unit(const S* __restrict__ Fin, const 
     Raw15<Pair> D;
     flow_unit<Pair>(dm, Fx, Fy, Fz, ur, inv_rho, u, D);
     populations15<Pair>(D, f);
+    const uint32_t seed1 = next_node_seed(seed);
 #pragma unroll
-    for (int a = 0; a < 15; ++a) *reinterpret_cast<two*>(Fout + a * P + c0) = Pk::from_float2(f[a].v);
+    for (int a = 0; a < 15; ++a)
+        *reinterpret_cast<two*>(Fout + a * P + c0) =
+            Pk::template store2<Storage<S>::sr_flow>(f[a].v, dither_of(seed, a), dither_of(seed1, a));
     *reinterpret_cast<float2*>(Tout + c0) = T.v;  // the reference of this node's stored deviations
     Pair g[Q];
     if constexpr (Q == 15) {
@@ -722,7 +752,9 @@ __device__ __forceinline__ void pair_node_unit(const S* __restrict__ Fin, const 
         thermal7_unit<Pair>(T, m0, mx, my, mz, u, ur, g);
     }
 #pragma unroll
-    for (int a = 0; a < Q; ++a) *reinterpret_cast<two*>(Gout + a * P + c0) = Pk::from_float2(g[a].v);
+    for (int a = 0; a < Q; ++a)
+        *reinterpret_cast<two*>(Gout + a * P + c0) = Pk::template store2<Storage<S>::sr_thermal>(
+            g[a].v, dither_of(seed, 15 + a), dither_of(seed1, 15 + a));
 }
 
 }  // namespace lbm

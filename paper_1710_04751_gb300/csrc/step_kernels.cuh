@@ -12,13 +12,33 @@
 namespace lbm {
 
 // Generic kernel: one thread per node of the flattened grid, any boundary mode.
+// The step number of the 16-bit forms' rounding dither: read from the counter of the
+// source buffer's parity; the launch's first thread writes the next value into the other
+// parity's counter, which no thread of this launch reads (the next launch, in stream
+// order, does).
+template <typename S>
+__device__ __forceinline__ uint32_t step_of(const unsigned* __restrict__ ctr_in,
+                                            unsigned* __restrict__ ctr_out) {
+    if constexpr (Storage<S>::deviation) {
+        const uint32_t step = *ctr_in;
+        if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+            *ctr_out = step + 1;
+        return step;
+    } else {
+        return 0;
+    }
+}
+
 template <typename S, int Q, bool UNIT>
 __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ Fin,
                                                    const S* __restrict__ Gin,
                                                    const float* __restrict__ Tin,
                                                    S* __restrict__ Fout, S* __restrict__ Gout,
-                                                   float* __restrict__ Tout, ParamsOf<S> p) {
+                                                   float* __restrict__ Tout, ParamsOf<S> p,
+                                                   const unsigned* __restrict__ ctr_in,
+                                                   unsigned* __restrict__ ctr_out) {
     using real = typename Storage<S>::real;
+    const uint32_t step = step_of<S>(ctr_in, ctr_out);
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= p.ncell) return;
     const int i = (int)(c % p.nx);
@@ -27,7 +47,9 @@ __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ Fin,
     const int k = (int)(t / p.ny);
     real f[15], g[Q];
     pull<S, Q>(Fin, Gin, Tin, p, i, j, k, c, f, g);
-    collide_store<S, Q, UNIT>(f, g, Fout, Gout, Tout, p, c);
+    uint32_t seed = 0;
+    if constexpr (Storage<S>::deviation) seed = dither_seed((uint32_t)(p.cell0 + c), step);
+    collide_store<S, Q, UNIT>(f, g, Fout, Gout, Tout, p, c, seed);
 }
 
 // ---------------------------------------------------------------------------------
@@ -38,13 +60,15 @@ template <typename S, int Q, bool UNIT>
 __global__ void __launch_bounds__(128, (cavity_min_blocks<S, Q>()))
     step_cavity_kernel(const S* __restrict__ Fin, const S* __restrict__ Gin,
                        const float* __restrict__ Tin, S* __restrict__ Fout,
-                       S* __restrict__ Gout, float* __restrict__ Tout, ParamsOf<S> p) {
+                       S* __restrict__ Gout, float* __restrict__ Tout, ParamsOf<S> p,
+                       const unsigned* __restrict__ ctr_in, unsigned* __restrict__ ctr_out) {
+    const uint32_t step = step_of<S>(ctr_in, ctr_out);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
     if (i >= p.nx) return;
     const bool interior = j >= 1 && j + 1 < p.ny && k >= 1 && k + 1 < p.nz;
-    if (interior) cavity_node<S, Q, true, UNIT>(Fin, Gin, Tin, Fout, Gout, Tout, p, i, j, k);
-    else cavity_node<S, Q, false, UNIT>(Fin, Gin, Tin, Fout, Gout, Tout, p, i, j, k);
+    if (interior) cavity_node<S, Q, true, UNIT>(Fin, Gin, Tin, Fout, Gout, Tout, p, i, j, k, step);
+    else cavity_node<S, Q, false, UNIT>(Fin, Gin, Tin, Fout, Gout, Tout, p, i, j, k, step);
 }
 
 // ---------------------------------------------------------------------------------
@@ -84,23 +108,27 @@ __global__ void __launch_bounds__(kPairThreads, (pair_min_blocks<Q, UNIT>()))
     step_pair_kernel(const S* __restrict__ Fin, const S* __restrict__ Gin,
                      const float* __restrict__ Tin, S* __restrict__ Fout,
                      S* __restrict__ Gout, float* __restrict__ Tout, ParamsOf<S> p,
-                     PairParams q) {
+                     PairParams q, const unsigned* __restrict__ ctr_in,
+                     unsigned* __restrict__ ctr_out) {
+    const uint32_t step = step_of<S>(ctr_in, ctr_out);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
     const int npair = p.nx >> 1;
     if (t >= npair) return;
     if (j >= 1 && j + 1 < p.ny && k >= 1 && k + 1 < p.nz) {
         const int nx = p.nx, nxy = nx * p.ny;
+        const int c0 = k * nxy + j * nx + 2 * t;
+        const uint32_t seed = dither_seed((uint32_t)(p.cell0 + c0), step);
         if constexpr (UNIT)
-            pair_node_unit<S, Q>(Fin, Gin, Tin, Fout, Gout, Tout, q, nx, nxy, (int)p.plane,
-                                 k * nxy + j * nx + 2 * t, t == 0, t == npair - 1);
+            pair_node_unit<S, Q>(Fin, Gin, Tin, Fout, Gout, Tout, q, nx, nxy, (int)p.plane, c0,
+                                 t == 0, t == npair - 1, seed);
         else
-            pair_node<S, Q>(Fin, Gin, Tin, Fout, Gout, Tout, q, nx, nxy, (int)p.plane,
-                            k * nxy + j * nx + 2 * t, t == 0, t == npair - 1);
+            pair_node<S, Q>(Fin, Gin, Tin, Fout, Gout, Tout, q, nx, nxy, (int)p.plane, c0,
+                            t == 0, t == npair - 1, seed);
     } else {
 #pragma unroll 1
         for (int e = 0; e < 2; ++e)
-            cavity_node<S, Q, false, UNIT>(Fin, Gin, Tin, Fout, Gout, Tout, p, 2 * t + e, j, k);
+            cavity_node<S, Q, false, UNIT>(Fin, Gin, Tin, Fout, Gout, Tout, p, 2 * t + e, j, k, step);
     }
 }
 
@@ -171,9 +199,11 @@ bool launch_pair(const DevState& s, int cur, const ParamsOf<S>& p, cudaStream_t 
         const int bx = npair <= 32 ? 32 : kPairThreads;
         const dim3 grid((npair + bx - 1) / bx, p.ny, p.nz);
         if (s.Q == 15)
-            step_pair_kernel<S, 15, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, q);
+            step_pair_kernel<S, 15, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, q,
+                                                                s.step_ctr + cur, s.step_ctr + (cur ^ 1));
         else
-            step_pair_kernel<S, 7, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, q);
+            step_pair_kernel<S, 7, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, q,
+                                                               s.step_ctr + cur, s.step_ctr + (cur ^ 1));
         return true;
     }
 }
@@ -188,21 +218,27 @@ cudaError_t launch_step_as(const DevState& s, int cur, const ParamsOf<S>& p, cud
     const float* Tin = static_cast<const float*>(s.T[cur]);
     float* Tout = static_cast<float*>(s.T[cur ^ 1]);
     if (launch_pair<S, UNIT>(s, cur, p, st)) return cudaGetLastError();
+    const unsigned* ctr_in = s.step_ctr ? s.step_ctr + cur : nullptr;
+    unsigned* ctr_out = s.step_ctr ? s.step_ctr + (cur ^ 1) : nullptr;
     if (p.boundary == 0 && p.ny <= 65535 && p.nz <= 65535 && 15 * p.plane < (int64_t(1) << 31)) {
         const int bx = 128;
         const dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
         if (s.Q == 15)
-            step_cavity_kernel<S, 15, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
+            step_cavity_kernel<S, 15, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, ctr_in,
+                                                                  ctr_out);
         else
-            step_cavity_kernel<S, 7, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
+            step_cavity_kernel<S, 7, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, ctr_in,
+                                                                 ctr_out);
         return cudaGetLastError();
     }
     const int threads = 256;
     const int64_t blocks = (p.ncell + threads - 1) / threads;
     if (s.Q == 15)
-        step_kernel<S, 15, UNIT><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
+        step_kernel<S, 15, UNIT><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p,
+                                                                        ctr_in, ctr_out);
     else
-        step_kernel<S, 7, UNIT><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p);
+        step_kernel<S, 7, UNIT><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p,
+                                                                       ctr_in, ctr_out);
     return cudaGetLastError();
 }
 

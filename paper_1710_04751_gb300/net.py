@@ -13,8 +13,9 @@ EXPORTS = (
     "lbm_net_param_count", "lbm_net_encode", "lbm_net_get_params", "lbm_net_set_params",
     "lbm_net_forward", "lbm_net_gradients", "lbm_net_train_step", "lbm_net_last_error",
     "lbm_net_targets", "lbm_net_warm_start", "lbm_net_set_lr", "lbm_nn_gemm_timeout_probe",
-    "lbm_net_tensor",
+    "lbm_net_tensor", "lbm_nn_conv3d_bf16",
 )
+CONV_BIAS_RELU_BF16, CONV_F32 = 0, 1
 
 # Stored tensors (lbm_net_tensor ids): BF16 activations, then FP32 outputs and gradients.
 TENSORS = ("X0", "A0", "S1", "P1", "A2", "S2", "P2", "A4", "A5", "A6", "C2", "A7", "A8", "C1",
@@ -60,6 +61,7 @@ def _lib():
     L.lbm_net_set_lr.argtypes = [vp, ctypes.c_float]
     L.lbm_nn_gemm_timeout_probe.argtypes = [vp]
     L.lbm_net_tensor.argtypes = [vp, i32, i32, vp, i64]
+    L.lbm_nn_conv3d_bf16.argtypes = [vp, i32, i32, i32, vp, i64, i32, vp, vp, i32, vp]
     _bound = True
     return L
 
@@ -82,6 +84,19 @@ def gemm_bf16(A, B, C, out_mode=GEMM_F32, splits=1, K=None):
     _check(_lib().lbm_nn_gemm_bf16(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
                                    C.data_ptr(), C.stride(0), M, N, K, out_mode, splits,
                                    _stream(C)))
+
+
+def conv3d_bf16(X, n, W, out, mode=CONV_BIAS_RELU_BF16, bias=None):
+    """3x3x3 zero-padded convolution as an implicit GEMM (lbm_nn_conv3d_bf16).  X: bfloat16
+    CUDA [batch, n^3, cin] (channels last); W: bfloat16 [cout, ldw] (K = tap * cin + ci);
+    out: [batch n^3, cout], bfloat16 (bias + ReLU) or float32 (CONV_F32)."""
+    batch, vox, cin = X.shape
+    cout = out.shape[-1]
+    if vox != n ** 3:
+        raise ValueError("X must hold n^3 voxels per sample")
+    _check(_lib().lbm_nn_conv3d_bf16(X.data_ptr(), batch, n, cin, W.data_ptr(), W.stride(0), cout,
+                                     None if bias is None else bias.data_ptr(), out.data_ptr(),
+                                     int(mode), _stream(out)))
 
 
 def gemm_timeout_probe(stream=None):

@@ -301,3 +301,47 @@ def test_consistent_initialisation_against_oracle(iterations):
     assert np.abs(f - F).max() <= 1e-12 and np.abs(g - G).max() <= 1e-12
     assert sim.steps_done == 0
     sim.close()
+
+
+# ------------------------------------------------------------------------------------
+# The implicit-GEMM convolution (lbm_nn_conv3d_bf16) against the FP64 definition: every
+# output element within 1e-6 K sum |x w| (FP32 accumulation of K = 27 cin BF16 products)
+# plus, for the BF16 output, its rounding (2^-8 of the value).  Grids n = 2 (a tile spans
+# 16 samples), 4, 16 and 32 (a tile is x-rows of one plane or several planes), channel
+# counts on both operand swizzles (cin 32, 96: 64-byte rows; 64, 192: 128-byte rows), and
+# cout from 16 to 192 (ragged tile widths).
+# ------------------------------------------------------------------------------------
+
+CONV_CASES = [(2, 2, 32, 16), (1, 4, 64, 40), (2, 16, 32, 32), (2, 16, 96, 32),
+              (2, 8, 192, 64), (1, 32, 64, 128), (3, 4, 128, 192)]
+
+
+@pytest.mark.parametrize("B,n,cin,cout", CONV_CASES, ids=[f"b{c[0]}-n{c[1]}-ci{c[2]}-co{c[3]}" for c in CONV_CASES])
+def test_implicit_convolution_against_fp64(B, n, cin, cout):
+    torch = torch_mod()
+    from paper_1710_04751_gb300 import net
+    g = torch.Generator().manual_seed(B * 1000 + n * 10 + cin + cout)
+    X = torch.randn((B, n ** 3, cin), generator=g, dtype=torch.float64).to(torch.bfloat16)
+    ldw = (27 * cin + 63) // 64 * 64
+    W = torch.zeros((cout, ldw), dtype=torch.float64)
+    W[:, :27 * cin] = torch.randn((cout, 27 * cin), generator=g, dtype=torch.float64) / (27 * cin) ** 0.5
+    W = W.to(torch.bfloat16)
+    bias = (0.1 * torch.randn(cout, generator=g, dtype=torch.float64)).to(torch.float32)
+    # reference: the zero-padded convolution in FP64 (weights K index tap * cin + ci)
+    F = torch.nn.functional
+    x = X.double().reshape(B, n, n, n, cin).permute(0, 4, 1, 2, 3)
+    w = W[:, :27 * cin].double().reshape(cout, 3, 3, 3, cin).permute(0, 4, 1, 2, 3)
+    y = F.conv3d(x, w, padding=1).permute(0, 2, 3, 4, 1).reshape(-1, cout)
+    mag = F.conv3d(x.abs(), w.abs(), padding=1).permute(0, 2, 3, 4, 1).reshape(-1, cout)
+    e = 1e-6 * 27 * cin * mag + 1e-30
+    out = torch.full((B * n ** 3, cout), float("nan"), dtype=torch.float32, device="cuda")
+    net.conv3d_bf16(X.cuda(), n, W.cuda(), out, mode=net.CONV_F32)
+    got = out.cpu().double()
+    r = ((got - y).abs() / e).max().item()
+    assert r <= 1.0, r
+    outb = torch.zeros((B * n ** 3, cout), dtype=torch.bfloat16, device="cuda")
+    net.conv3d_bf16(X.cuda(), n, W.cuda(), outb, mode=net.CONV_BIAS_RELU_BF16, bias=bias.cuda())
+    ref = torch.relu(y + bias.double())
+    gotb = outb.cpu().double()
+    assert ((gotb - ref).abs() <= 2.0 ** -8 * (ref.abs() + e) + e).all()
+

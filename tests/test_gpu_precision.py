@@ -3,9 +3,12 @@ w^phi_a T_node for the scalar -- with FP32 arithmetic) against the FP64 oracle a
 path.
 
 One step from a state both sides share (the GPU's own decoded state): each population
-may differ from the oracle by the rounding of its stored deviation, 2^-11 |p - p_rest|
-(FP16) or 2^-8 |p - p_rest| (BF16), plus the FP32 bound of the FP32 tests and, for FP16,
-half the smallest subnormal step (2^-25)."""
+may differ from the oracle by the rounding of its stored deviation plus the FP32 bound of
+the FP32 tests.  The scalar deviations are rounded to nearest: half a unit in the last
+place, 2^-11 |p - p_rest| (FP16) or 2^-8 |p - p_rest| (BF16), and for FP16 half the
+smallest subnormal step (2^-25).  The flow deviations (and the scalar's where the build
+selects it) are rounded stochastically (storage.cuh): less than one unit in the last
+place, twice those bounds; the tests take twice them for both."""
 import math
 
 import numpy as np
@@ -27,8 +30,10 @@ def _bound(p, prec_name, ref_f, ref_g):
     wt = oracle.weights_thermal(p.q_g, p.cs2_phi)[:, None, None, None] * ref_g.sum(axis=0)[None]
     floor_g = thermal_floor(p.q_g, p.cs2_phi, p.T_hot - p.T_cold)[:, None, None, None]
     e, sub = EPS[prec_name], SUBNORMAL_HALF[prec_name]
-    bf = e * np.abs(ref_f - wf) + FP32_REL * np.maximum(np.abs(ref_f), wf) + sub
-    bg = e * np.abs(ref_g - wt) + FP32_REL * np.maximum(np.abs(ref_g), floor_g) + sub
+    # stochastic rounding (the flow; the scalar where the build selects it): under one unit
+    # in the last place, twice the bound of rounding to nearest
+    bf = 2 * e * np.abs(ref_f - wf) + FP32_REL * np.maximum(np.abs(ref_f), wf) + 2 * sub
+    bg = 2 * e * np.abs(ref_g - wt) + FP32_REL * np.maximum(np.abs(ref_g), floor_g) + 2 * sub
     return bf, bg
 
 
@@ -84,7 +89,9 @@ def test_steady_nusselt_of_the_16bit_forms():
     # 48^3, Ra = 1e4, every form from rest for 60 000 steps (FP32 is steady, max |dT| per
     # 100 steps < 1e-6, from about 22 000 on; the 16-bit forms' max |dT| has a rounding
     # floor above that and cannot signal their own convergence): steady Nu of FP16 within
-    # 0.5% of FP32; BF16 (8 significant bits) within 2%
+    # 0.5% of FP32, the precision form's target (measured -0.09% with its stochastically
+    # rounded flow stores); BF16 (8 significant bits, rounded to nearest) within 1%
+    # (measured +0.32% mid-plane, +0.56% hot wall: just above the target)
     from paper_1710_04751_gb300.precision import run_steps
     out = {}
     for name in ("FP32", "FP16_DEV", "BF16_DEV"):
@@ -94,7 +101,7 @@ def test_steady_nusselt_of_the_16bit_forms():
     print({k: (v["nu"]["mid_mean"], v["nu"]["hot_wall_mean"], v["residual_per_100"]) for k, v in out.items()})
     assert 0 <= out["FP32"]["residual_per_100"] < 1e-6
     ref = out["FP32"]["nu"]
-    for name, tol in (("FP16_DEV", 5e-3), ("BF16_DEV", 2e-2)):
+    for name, tol in (("FP16_DEV", 5e-3), ("BF16_DEV", 1e-2)):
         for k in ("mid_mean", "hot_wall_mean"):
             assert out[name]["nu"][k] == pytest.approx(ref[k], rel=tol), (name, k)
 
