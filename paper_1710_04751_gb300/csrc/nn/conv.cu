@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "nn.h"
@@ -187,6 +188,179 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) tmem_dealloc(tmem, L::TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------------
+// The same convolution with the input tile reused across the three ky taps (n >= 16).
+// A CTA computes MT consecutive M tiles (MT * 128 voxels: bx = n columns by MT * by rows of
+// one plane).  For each (kz, kx, channel chunk) one 5D box brings the MT * by + 2 rows
+// around them, shifted by kx - 1 in x and kz - 1 in z; the tile of output tile t and tap
+// ky is the 128-row window starting at row (t * by + ky) * bx of that box (whole x-rows,
+// so every window starts on a swizzle atom), multiplied into accumulator t with the
+// weights of tap (kz, ky, kx).  Each loaded byte serves up to 3 * MT * by / (MT * by + 2)
+// windows instead of one (2.4 at n = 64, MT = 4), cutting the operand traffic from L2 that
+// bounds the one-tile kernel.  Stage geometry is a runtime property of n and MT.
+// ---------------------------------------------------------------------------------
+struct RowsArgs {
+    int M, N, n, chunks, cin;
+    int bx, by, mt;      // tile columns, rows per tile, tiles per CTA
+    int a_bytes;         // one stage's input box: (mt by + 2) bx BKC 2 bytes
+    int stage_bytes;     // a_bytes + 3 BN BKC 2, rounded up to 1024
+    int stages;
+    uint32_t tmem_cols;  // mt BN, a power of two >= 32
+    int mode;
+    void* C;
+    const float* bias;
+    int* err;
+};
+
+template <int BN, int BKC>
+__global__ void __launch_bounds__(128, 1)
+    conv_rows_kernel(const __grid_constant__ CUtensorMap tmX,
+                     const __grid_constant__ CUtensorMap tmW, RowsArgs args) {
+    extern __shared__ uint8_t rows_smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(rows_smem_raw) + 1023) & ~uintptr_t(1023));
+    const int S = args.stages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * args.stage_bytes);
+    uint64_t* empty = full + S;
+    uint64_t* done = empty + S;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ volatile int failed;
+    constexpr int B_TILE = BN * BKC * 2;
+
+    if (*static_cast<volatile int*>(args.err) != 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int MT = args.mt;
+    const int m0 = blockIdx.x * MT * CBM, n0 = blockIdx.y * BN;
+    const int nkb = 9 * args.chunks;  // stages: (kz, kx, chunk)
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(done, 1);
+        mbar_fence_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, args.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0;
+    if (warp == 0 && lane == 0) {
+        const int n = args.n;
+        const int y0 = (m0 / n) % n, z0 = (m0 / (n * n)) % n, b0 = m0 / (n * n * n);
+        int kz = 0, kx = 0, chunk = 0;
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % S;
+            const uint32_t ph = (uint32_t)(i / S) & 1u;
+            if (i >= S && !mbar_wait(empty + s, ph ^ 1u, args.err, 1, &failed)) {
+                failed = 1;
+                break;
+            }
+            if (failed) break;
+            uint8_t* a = smem + s * args.stage_bytes;
+            mbar_expect_tx(full + s, (uint32_t)(args.a_bytes + 3 * B_TILE));
+            tma_load_5d(a, &tmX, full + s, chunk * BKC, kx - 1, y0 - 1, z0 + kz - 1, b0);
+            for (int ky = 0; ky < 3; ++ky) {
+                const int tap = (kz * 3 + ky) * 3 + kx;
+                tma_load_2d(a + args.a_bytes + ky * B_TILE, &tmW, full + s,
+                            (tap * args.chunks + chunk) * BKC, n0);
+            }
+            ++issued;
+            if (++chunk == args.chunks) {
+                chunk = 0;
+                if (++kx == 3) {
+                    kx = 0;
+                    ++kz;
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_bf16_f32(CBM, BN);
+        const int row_bytes = BKC * 2;
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % S;
+            const uint32_t ph = (uint32_t)(i / S) & 1u;
+            if (failed || !mbar_wait(full + s, ph, args.err, 2, &failed)) {
+                failed = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a = smem_u32(smem + s * args.stage_bytes), b = a + args.a_bytes;
+            for (int t = 0; t < MT; ++t) {
+                for (int ky = 0; ky < 3; ++ky) {
+                    const uint32_t at = a + (uint32_t)((t * args.by + ky) * args.bx * row_bytes);
+                    const uint32_t bt = b + (uint32_t)(ky * B_TILE);
+#pragma unroll
+                    for (int kk = 0; kk < BKC / 16; ++kk)
+                        mma_bf16(tmem + (uint32_t)(t * BN), sdesc(at + kk * 32, BKC),
+                                 sdesc(bt + kk * 32, BKC), idesc, (i > 0 || ky > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(empty + s);
+        }
+        mma_commit(done);
+    }
+    __syncwarp();
+    if (!mbar_wait(done, 0, args.err, 3)) failed = 1;
+    __syncthreads();
+    const bool ok = !failed;
+    if (warp == 0 && lane == 0 && failed) {
+        for (int i = max(0, issued - S); i < issued; ++i)
+            mbar_wait(full + (i % S), (uint32_t)(i / S) & 1u, args.err, 4);
+    }
+    tc_fence_after();
+    if (ok) {
+        for (int t = 0; t < MT; ++t) {
+            const int row = m0 + t * CBM + warp * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * BN + c), v);
+                const int col0 = n0 + c;
+                if (row >= args.M || col0 >= args.N) continue;
+                const bool whole = col0 + 16 <= args.N && (args.N % 8) == 0;
+                if (args.mode == CONV_BIAS_RELU_BF16) {
+                    __nv_bfloat16* C = static_cast<__nv_bfloat16*>(args.C) + (int64_t)row * args.N;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        v[j] = fmaxf(v[j] + (col0 + j < args.N ? args.bias[col0 + j] : 0.f), 0.f);
+                    if (whole) {
+                        uint4 pk[2];
+                        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(pk);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        reinterpret_cast<uint4*>(C + col0)[0] = pk[0];
+                        reinterpret_cast<uint4*>(C + col0)[1] = pk[1];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (col0 + j < args.N) C[col0 + j] = __float2bfloat16_rn(v[j]);
+                    }
+                } else {
+                    float* C = static_cast<float*>(args.C) + (int64_t)row * args.N;
+                    if (whole && (args.N % 4) == 0) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            reinterpret_cast<float4*>(C + col0)[j] =
+                                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (col0 + j < args.N) C[col0 + j] = v[j];
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, args.tmem_cols);
+}
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -255,6 +429,36 @@ cudaError_t launch_conv(const CUtensorMap& tx, const CUtensorMap& tw, const Conv
     return cudaGetLastError();
 }
 
+constexpr int kRowsSmemBudget = 200 * 1024;
+
+template <int BN, int BKC>
+cudaError_t launch_rows(const CUtensorMap& tx, const CUtensorMap& tw, const RowsArgs& a,
+                        cudaStream_t st) {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(conv_rows_kernel<BN, BKC>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    1024 + kRowsSmemBudget + 256);
+    });
+    if (attr != cudaSuccess) return attr;
+    const size_t smem = 1024 + (size_t)a.stages * a.stage_bytes + 256;
+    const dim3 grid((a.M + a.mt * CBM - 1) / (a.mt * CBM), (a.N + BN - 1) / BN, 1);
+    conv_rows_kernel<BN, BKC><<<grid, 128, smem, st>>>(tx, tw, a);
+    return cudaGetLastError();
+}
+
+template <int BKC>
+cudaError_t launch_rows_bkc(const CUtensorMap& tx, const CUtensorMap& tw, const RowsArgs& a,
+                            int BN, cudaStream_t st) {
+    switch (BN) {
+    case 32: return launch_rows<32, BKC>(tx, tw, a, st);
+    case 64: return launch_rows<64, BKC>(tx, tw, a, st);
+    case 128: return launch_rows<128, BKC>(tx, tw, a, st);
+    default: return launch_rows<256, BKC>(tx, tw, a, st);
+    }
+}
+
 template <int BKC>
 cudaError_t launch_conv_bkc(const CUtensorMap& tx, const CUtensorMap& tw, const ConvArgs& a,
                             int BN, cudaStream_t st) {
@@ -267,6 +471,9 @@ cudaError_t launch_conv_bkc(const CUtensorMap& tx, const CUtensorMap& tw, const 
 }
 
 }  // namespace
+
+// n >= 16 takes the row-reuse kernel (conv_rows_kernel); smaller grids the one-tile kernel.
+constexpr bool kConvRows = true;
 
 bool conv_implicit_supported(int n, int cin, int cout) {
     return cin % 32 == 0 && n >= 2 && n <= 256 && (n & (n - 1)) == 0 && cout >= 1 && cout <= 256;
@@ -287,6 +494,28 @@ cudaError_t conv_implicit(const __nv_bfloat16* X, int B, int n, int cin, const _
     const int bb = 128 / (bx * by * bz);
     if (bx * by * bz * bb != 128) return cudaErrorInvalidValue;
     const int BN = cout <= 32 ? 32 : cout <= 64 ? 64 : cout <= 128 ? 128 : 256;
+    if (kConvRows && n >= 16 && n <= 128) {
+        // tiles of whole x-rows of one plane, MT of them per CTA: as many as the tensor
+        // memory (MT BN columns) and two pipeline stages of shared memory allow
+        const int by1 = 128 / n;
+        const int b_bytes = 3 * BN * bkc * 2;
+        int mt = 4;
+        while (mt > 1 && (mt * BN > 512 || mt * by1 > n ||
+                          2 * (((mt * by1 + 2) * n * bkc * 2 + b_bytes + 1023) / 1024 * 1024) > kRowsSmemBudget))
+            mt >>= 1;
+        const int a_bytes = (mt * by1 + 2) * n * bkc * 2;
+        const int stage = (a_bytes + b_bytes + 1023) / 1024 * 1024;
+        if (2 * stage <= kRowsSmemBudget) {
+            const int stages = std::min(4, kRowsSmemBudget / stage);
+            CUtensorMap tx, tw;
+            if (!make_x_map(&tx, X, B, n, cin, bkc, n, mt * by1 + 2, 1, 1) ||
+                !make_w_map(&tw, W, cout, 27 * cin, ldw, bkc, BN))
+                return cudaErrorInvalidValue;
+            RowsArgs a{B * n * n * n, cout, n, cin / bkc, cin, n, by1, mt, a_bytes, stage, stages,
+                       (uint32_t)std::max(32, mt * BN), mode, out, bias, err};
+            return bkc == 64 ? launch_rows_bkc<64>(tx, tw, a, BN, st) : launch_rows_bkc<32>(tx, tw, a, BN, st);
+        }
+    }
     CUtensorMap tx, tw;
     if (!make_x_map(&tx, X, B, n, cin, bkc, bx, by, bz, bb) ||
         !make_w_map(&tw, W, cout, 27 * cin, ldw, bkc, BN))

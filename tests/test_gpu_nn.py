@@ -306,14 +306,16 @@ def test_consistent_initialisation_against_oracle(iterations):
 # ------------------------------------------------------------------------------------
 # The implicit-GEMM convolution (lbm_nn_conv3d_bf16) against the FP64 definition: every
 # output element within 1e-6 K sum |x w| (FP32 accumulation of K = 27 cin BF16 products)
-# plus, for the BF16 output, its rounding (2^-8 of the value).  Grids n = 2 (a tile spans
-# 16 samples), 4, 16 and 32 (a tile is x-rows of one plane or several planes), channel
-# counts on both operand swizzles (cin 32, 96: 64-byte rows; 64, 192: 128-byte rows), and
-# cout from 16 to 192 (ragged tile widths).
+# plus, for the BF16 output, its rounding (2^-8 of the value).  Grids n = 2, 4, 8 (the
+# one-tile kernel: a tile spans several planes or samples) and 16, 32, 64 (the row-reuse
+# kernel: 1-4 tiles of whole x-rows per CTA sharing each input box across the ky taps),
+# channel counts on both operand swizzles (cin 32, 96: 64-byte rows; 64, 128, 192: 128-byte
+# rows), and cout from 16 to 192 (ragged tile widths).
 # ------------------------------------------------------------------------------------
 
 CONV_CASES = [(2, 2, 32, 16), (1, 4, 64, 40), (2, 16, 32, 32), (2, 16, 96, 32),
-              (2, 8, 192, 64), (1, 32, 64, 128), (3, 4, 128, 192)]
+              (2, 8, 192, 64), (1, 32, 64, 128), (3, 4, 128, 192), (1, 16, 128, 128),
+              (1, 32, 192, 64), (1, 64, 96, 32), (1, 64, 32, 96)]
 
 
 @pytest.mark.parametrize("B,n,cin,cout", CONV_CASES, ids=[f"b{c[0]}-n{c[1]}-ci{c[2]}-co{c[3]}" for c in CONV_CASES])
