@@ -34,7 +34,7 @@ __global__ void init_kernel(S* __restrict__ F, S* __restrict__ G, float* __restr
     const double T = amp * (2.0 * u01 - 1.0);
 #pragma unroll
     for (int a = 0; a < 15; ++a)
-        F[a * p.plane + c] = Storage<S>::store((real)(a == 0 ? w0 : a < 7 ? w1 : w7), p.wf[a]);
+        F[a * p.plane + c] = Storage<S>::store_f((real)(a == 0 ? w0 : a < 7 ? w1 : w7), p.wf[a]);
     // 16-bit forms: g is stored as its deviation from w^phi_a T of this node (zero here)
     real Tref = real(0);
     if constexpr (Storage<S>::deviation) {
@@ -94,14 +94,16 @@ __global__ void to_storage_kernel(S* __restrict__ dst, const double* __restrict_
     using real = typename Storage<S>::real;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x)
-        dst[c] = Storage<S>::store((real)src[c], conv_offset<S>(offset, Tn, c));
+        dst[c] = Tn ? Storage<S>::store((real)src[c], conv_offset<S>(offset, Tn, c))
+                    : Storage<S>::store_f((real)src[c], (real)offset);
 }
 template <typename S>
 __global__ void to_double_kernel(double* __restrict__ dst, const S* __restrict__ src, int64_t n,
                                  double offset, const float* __restrict__ Tn) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x)
-        dst[c] = (double)Storage<S>::load(src[c], conv_offset<S>(offset, Tn, c));
+        dst[c] = (double)(Tn ? Storage<S>::load(src[c], conv_offset<S>(offset, Tn, c))
+                             : Storage<S>::load_f(src[c], (typename Storage<S>::real)offset));
 }
 // Tn[c] (+)= (float) src[c]: the node temperature of a state being uploaded (16-bit forms)
 __global__ void accumulate_T_kernel(float* __restrict__ Tn, const double* __restrict__ src,
@@ -156,7 +158,7 @@ __device__ __forceinline__ void node_macro(const S* __restrict__ F, const S* __r
     double r = 0, jx = 0, jy = 0, jz = 0, t = 0;
 #pragma unroll
     for (int a = 0; a < 15; ++a) {
-        const double v = (double)Storage<S>::load(F[a * p.plane + c], p.wf[a]);
+        const double v = (double)Storage<S>::load_f(F[a * p.plane + c], p.wf[a]);
         r += v;
         jx += ex(a) * v;
         jy += ey(a) * v;

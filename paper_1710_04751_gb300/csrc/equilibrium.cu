@@ -49,7 +49,7 @@ __global__ void set_fields_kernel(S* __restrict__ F, S* __restrict__ G, float* _
     if constexpr (Q == 15) collide_thermal15<real>(g, u[0], u[1], u[2], q);
     else collide_thermal7<real>(g, u[0], u[1], u[2], q);
 #pragma unroll
-    for (int a = 0; a < 15; ++a) F[a * p.plane + c] = St::store(f[a], p.wf[a]);
+    for (int a = 0; a < 15; ++a) F[a * p.plane + c] = St::store_f(f[a], p.wf[a]);
     if constexpr (St::deviation) Tn[c] = (float)t;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
@@ -105,7 +105,7 @@ __global__ void reimpose_kernel(S* __restrict__ F, S* __restrict__ G, float* __r
     real r = 0, jx = 0, jy = 0, jz = 0, t = 0;
 #pragma unroll
     for (int a = 0; a < 15; ++a) {
-        f[a] = St::load(F[a * p.plane + c], p.wf[a]);
+        f[a] = St::load_f(F[a * p.plane + c], p.wf[a]);
         r += f[a];
         jx += ex(a) * f[a];
         jy += ey(a) * f[a];
@@ -127,7 +127,7 @@ __global__ void reimpose_kernel(S* __restrict__ F, S* __restrict__ G, float* __r
     equilibria<real, Q>(q, r, uc, t, fc, gc);
     equilibria<real, Q>(q, r, ut, tt, ft, gt);
 #pragma unroll
-    for (int a = 0; a < 15; ++a) F[a * p.plane + c] = St::store(f[a] - fc[a] + ft[a], p.wf[a]);
+    for (int a = 0; a < 15; ++a) F[a * p.plane + c] = St::store_f(f[a] - fc[a] + ft[a], p.wf[a]);
     if constexpr (St::deviation) Tn[c] = (float)tt;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {

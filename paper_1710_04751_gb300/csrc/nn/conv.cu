@@ -472,8 +472,12 @@ cudaError_t launch_conv_bkc(const CUtensorMap& tx, const CUtensorMap& tw, const 
 
 }  // namespace
 
-// n >= 16 takes the row-reuse kernel (conv_rows_kernel); smaller grids the one-tile kernel.
-constexpr bool kConvRows = true;
+// Tiles of >= 128 output channels at n >= 16 take the row-reuse kernel (conv_rows_kernel);
+// the rest the one-tile kernel.
+#ifndef LBM_CONV_ROWS
+#define LBM_CONV_ROWS 1
+#endif
+constexpr bool kConvRows = LBM_CONV_ROWS != 0;
 
 bool conv_implicit_supported(int n, int cin, int cout) {
     return cin % 32 == 0 && n >= 2 && n <= 256 && (n & (n - 1)) == 0 && cout >= 1 && cout <= 256;
@@ -494,7 +498,10 @@ cudaError_t conv_implicit(const __nv_bfloat16* X, int B, int n, int cin, const _
     const int bb = 128 / (bx * by * bz);
     if (bx * by * bz * bb != 128) return cudaErrorInvalidValue;
     const int BN = cout <= 32 ? 32 : cout <= 64 ? 64 : cout <= 128 ? 128 : 256;
-    if (kConvRows && n >= 16 && n <= 128) {
+    // the row-reuse kernel where it measured faster: tiles of 128 or more output channels
+    // (at 64 and fewer the tensor pipe's reads of the A operand from shared memory bound both
+    // kernels, and the one-tile kernel keeps more CTAs per SM)
+    if (kConvRows && BN >= 128 && n >= 16 && n <= 128) {
         // tiles of whole x-rows of one plane, MT of them per CTA: as many as the tensor
         // memory (MT BN columns) and two pipeline stages of shared memory allow
         const int by1 = 128 / n;

@@ -68,9 +68,9 @@ __device__ __forceinline__ void pull(const S* __restrict__ Fin, const S* __restr
         const int64_t s = ((int64_t)sk * ny + sj) * nx + si;
         // opposite / mirrored directions have the same rest weight as a
         if (in_x && in_y && in_z) {
-            f[a] = St::load(Fin[a * P + s], p.wf[a]);
+            f[a] = St::load_f(Fin[a * P + s], p.wf[a]);
         } else {
-            f[a] = St::load(Fin[opp(a) * P + c], p.wf[a]);  // no-slip: half-way bounce-back
+            f[a] = St::load_f(Fin[opp(a) * P + c], p.wf[a]);  // no-slip: half-way bounce-back
         }
         if (a < Q) {
             if (in_x && in_y && in_z) {
@@ -130,7 +130,7 @@ __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15]
         populations15<real>(D, f);  // f~ - w_a: the 16-bit forms store it as it is
 #pragma unroll
         for (int a = 0; a < 15; ++a) {
-            if constexpr (St::deviation) Fout[a * P + c] = store16<S, St::sr_flow>(f[a], dither_of(seed, a));
+            if constexpr (St::deviation) Fout[a * P + c] = store16<S, St::sr_flow, true>(f[a], dither_of(seed, a));
             else Fout[a * P + c] = St::store(f[a] + p.wf[a], real(0));
         }
         if constexpr (Q == 15) {
@@ -159,9 +159,9 @@ __device__ __forceinline__ void collide_store(typename Storage<S>::real (&f)[15]
 #pragma unroll
     for (int a = 0; a < 15; ++a) {
         if constexpr (St::deviation)
-            Fout[a * P + c] = store16<S, St::sr_flow>(f[a] - p.wf[a], dither_of(seed, a));
+            Fout[a * P + c] = store16<S, St::sr_flow, true>(f[a] - p.wf[a], dither_of(seed, a));
         else
-            Fout[a * P + c] = St::store(f[a], p.wf[a]);
+            Fout[a * P + c] = St::store_f(f[a], p.wf[a]);
     }
     if constexpr (Q == 15) collide_thermal15<real>(g, ux, uy, uz, p);
     else collide_thermal7<real>(g, ux, uy, uz, p);
@@ -222,7 +222,7 @@ __device__ __forceinline__ void cavity_node(const S* __restrict__ Fin, const S* 
             const int shift = ex(a) + ey(a) * nxi + ez(a) * nxyi;
             const bool out = (ex(a) > 0 && lo) || (ex(a) < 0 && hi);
             const S* Fa = Fin + (int64_t)a * P - shift;
-            f[a] = St::load(Fa[out ? ci + shift + (opp(a) - a) * Pi : ci], p.wf[a]);
+            f[a] = St::load_f(Fa[out ? ci + shift + (opp(a) - a) * Pi : ci], p.wf[a]);
         }
     } else {
         pull<S, Q>(Fin, Gin, Tin, p, i, j, k, c, f, g);

@@ -81,6 +81,18 @@ struct Pack<__half> {
         if constexpr (SR) return from_float2_sr(v, dx, dy);
         else return from_float2(v);
     }
+    // flow deviations: stored times 2^flow_exp (storage.cuh)
+    static constexpr float up = Storage<__half>::fup, down = Storage<__half>::fdown;
+    __device__ __forceinline__ static float2 flow2(two v) {
+        return mul2(__half22float2(v), make_float2(down, down));
+    }
+    __device__ __forceinline__ static float2 flow2(__half x, __half y) {
+        return mul2(make_float2(__half2float(x), __half2float(y)), make_float2(down, down));
+    }
+    template <bool SR>
+    __device__ __forceinline__ static two store2f(float2 v, uint32_t dx, uint32_t dy) {
+        return store2<SR>(mul2(v, make_float2(up, up)), dx, dy);
+    }
 };
 template <>
 struct Pack<__nv_bfloat16> {
@@ -97,10 +109,17 @@ struct Pack<__nv_bfloat16> {
         if constexpr (SR) return from_float2_sr(v, dx, dy);
         else return from_float2(v);
     }
+    // flow deviations: stored as they are
+    __device__ __forceinline__ static float2 flow2(two v) { return to_float2(v); }
+    __device__ __forceinline__ static float2 flow2(__nv_bfloat16 x, __nv_bfloat16 y) {
+        return make_float2(to_float(x), to_float(y));
+    }
+    template <bool SR>
+    __device__ __forceinline__ static two store2f(float2 v, uint32_t dx, uint32_t dy) {
+        return store2<SR>(v, dx, dy);
+    }
 };
 
-// The dither seed of node c0 + 1 from that of node c0 (dither_seed is linear in the node).
-__device__ __forceinline__ uint32_t next_node_seed(uint32_t seed) { return seed + 0x2C1B3C6Du; }
 
 // Two lanes of FP32 as one arithmetic value (the unit-rate collisions of
 // collide_unit.cuh are templates over it): every operator is one packed instruction.
@@ -405,11 +424,11 @@ __device__ __forceinline__ void pair_collide_store(float2 (&f)[15], float2 (&g)[
     const float2 Fz = fma2(q.gbeta, sub2(T, q.T0), q.fz);
     Vel2 vu;
     collide_flow2(f, Fz, q, vu);
-    const uint32_t seed1 = next_node_seed(seed);
+    const uint32_t seed0 = dither_from_weyl(seed), seed1 = dither_from_weyl(seed + kDitherNodeStep);
 #pragma unroll
     for (int a = 0; a < 15; ++a)
         *reinterpret_cast<two*>(Fout + a * P + c0) =
-            Pk::template store2<Storage<S>::sr_flow>(sub2(f[a], q.wf[a]), dither_of(seed, a),
+            Pk::template store2f<Storage<S>::sr_flow>(sub2(f[a], q.wf[a]), dither_of(seed0, a),
                                                      dither_of(seed1, a));
     if constexpr (Q == 15) collide_thermal15_2(g, vu, q);
     else collide_thermal7_2(g, vu, q);
@@ -576,11 +595,11 @@ __device__ __forceinline__ void pair_collide_store_lean(float2 (&f)[15], float2 
             *reinterpret_cast<two*>(Gout + a * P + c0) = Pk::from_float2(fma2(q.nwg[a], T, g[a]));
     }
     populations15_2(add15_2(df, flow_increment2(mf, inv_rho, Fz, q, vu)), f);
-    const uint32_t seed1 = next_node_seed(seed);
+    const uint32_t seed0 = dither_from_weyl(seed), seed1 = dither_from_weyl(seed + kDitherNodeStep);
 #pragma unroll
     for (int a = 0; a < 15; ++a)
         *reinterpret_cast<two*>(Fout + a * P + c0) =
-            Pk::template store2<Storage<S>::sr_flow>(f[a], dither_of(seed, a), dither_of(seed1, a));
+            Pk::template store2f<Storage<S>::sr_flow>(f[a], dither_of(seed0, a), dither_of(seed1, a));
 }
 
 // The pair update after the pull: f holds the pulled flow deviations (f - w_a), g the pulled
@@ -657,15 +676,15 @@ __device__ __forceinline__ void pair_node(const S* __restrict__ Fin, const S* __
         const int r = ey(a) * nx + ez(a) * nxy;
         const S* Fa = Fin + a * P;
         if (ex(a) == 0) {
-            f[a] = Pk::to_float2(*reinterpret_cast<const two*>(Fa + c0 - r));
+            f[a] = Pk::flow2(*reinterpret_cast<const two*>(Fa + c0 - r));
         } else if (ex(a) > 0) {
             const S* Fs = Fa - r - 1;
             const int i0 = lo ? c0 + r + 1 + (opp(a) - a) * P : c0;
-            f[a] = make_float2(Pk::to_float(Fs[i0]), Pk::to_float(Fs[c0 + 1]));
+            f[a] = Pk::flow2(Fs[i0], Fs[c0 + 1]);
         } else {
             const S* Fs = Fa - r + 1;
             const int i1 = hi ? c0 + r + (opp(a) - a) * P : c0 + 1;
-            f[a] = make_float2(Pk::to_float(Fs[c0]), Pk::to_float(Fs[i1]));
+            f[a] = Pk::flow2(Fs[c0], Fs[i1]);
         }
     }
     pair_finish<S, Q>(f, g, Fout, Gout, Tout, q, P, c0, seed);
@@ -677,6 +696,12 @@ __device__ __forceinline__ void pair_node(const S* __restrict__ Fin, const S* __
 // reduced to those four pairs at once and the flow update runs with no scalar population
 // held in registers.  Pull addressing and wall rules as pair_node.
 // ---------------------------------------------------------------------------------
+template <typename S, int Q>
+__device__ __forceinline__ void pair_unit_update(Pair m0, Pair mx, Pair my, Pair mz, Pair (&f)[15],
+                                                 S* __restrict__ Fout, S* __restrict__ Gout,
+                                                 float* __restrict__ Tout, const PairParams& q,
+                                                 int P, int c0, uint32_t seed);
+
 template <typename S, int Q>
 __device__ __forceinline__ void pair_node_unit(const S* __restrict__ Fin, const S* __restrict__ Gin,
                                                const float* __restrict__ Tin, S* __restrict__ Fout,
@@ -727,17 +752,29 @@ __device__ __forceinline__ void pair_node_unit(const S* __restrict__ Fin, const 
         const int r = ey(a) * nx + ez(a) * nxy;
         const S* Fa = Fin + a * P;
         if (ex(a) == 0) {
-            f[a].v = Pk::to_float2(*reinterpret_cast<const two*>(Fa + c0 - r));
+            f[a].v = Pk::flow2(*reinterpret_cast<const two*>(Fa + c0 - r));
         } else if (ex(a) > 0) {
             const S* Fs = Fa - r - 1;
             const int i0 = lo ? c0 + r + 1 + (opp(a) - a) * P : c0;
-            f[a].v = make_float2(Pk::to_float(Fs[i0]), Pk::to_float(Fs[c0 + 1]));
+            f[a].v = Pk::flow2(Fs[i0], Fs[c0 + 1]);
         } else {
             const S* Fs = Fa - r + 1;
             const int i1 = hi ? c0 + r + (opp(a) - a) * P : c0 + 1;
-            f[a].v = make_float2(Pk::to_float(Fs[c0]), Pk::to_float(Fs[i1]));
+            f[a].v = Pk::flow2(Fs[c0], Fs[i1]);
         }
     }
+    pair_unit_update<S, Q>(m0, mx, my, mz, f, Fout, Gout, Tout, q, P, c0, seed);
+}
+
+// The unit-rate pair update from the pulled scalar sums (phi and the first moments of g)
+// and the pulled flow deviations f - w_a: collision, then the stores of both nodes.
+template <typename S, int Q>
+__device__ __forceinline__ void pair_unit_update(Pair m0, Pair mx, Pair my, Pair mz, Pair (&f)[15],
+                                                 S* __restrict__ Fout, S* __restrict__ Gout,
+                                                 float* __restrict__ Tout, const PairParams& q,
+                                                 int P, int c0, uint32_t seed) {
+    using Pk = Pack<S>;
+    using two = typename Pk::two;
     const UnitRates<Pair>& ur = q.ur;
     const Pair T = m0 + ur.halfR;  // Eq. (25)
     const Pair Fz = {fma2(q.gbeta, sub2(T.v, q.T0), q.fz)};
@@ -748,11 +785,11 @@ __device__ __forceinline__ void pair_node_unit(const S* __restrict__ Fin, const 
     Raw15<Pair> D;
     flow_unit<Pair>(dm, Fx, Fy, Fz, ur, inv_rho, u, D);
     populations15<Pair>(D, f);
-    const uint32_t seed1 = next_node_seed(seed);
+    const uint32_t seed0 = dither_from_weyl(seed), seed1 = dither_from_weyl(seed + kDitherNodeStep);
 #pragma unroll
     for (int a = 0; a < 15; ++a)
         *reinterpret_cast<two*>(Fout + a * P + c0) =
-            Pk::template store2<Storage<S>::sr_flow>(f[a].v, dither_of(seed, a), dither_of(seed1, a));
+            Pk::template store2f<Storage<S>::sr_flow>(f[a].v, dither_of(seed0, a), dither_of(seed1, a));
     *reinterpret_cast<float2*>(Tout + c0) = T.v;  // the reference of this node's stored deviations
     Pair g[Q];
     if constexpr (Q == 15) {
@@ -764,7 +801,7 @@ __device__ __forceinline__ void pair_node_unit(const S* __restrict__ Fin, const 
 #pragma unroll
     for (int a = 0; a < Q; ++a)
         *reinterpret_cast<two*>(Gout + a * P + c0) = Pk::template store2<Storage<S>::sr_thermal>(
-            g[a].v, dither_of(seed, 15 + a), dither_of(seed1, 15 + a));
+            g[a].v, dither_of(seed0, 15 + a), dither_of(seed1, 15 + a));
 }
 
 }  // namespace lbm

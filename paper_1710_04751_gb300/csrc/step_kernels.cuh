@@ -103,22 +103,19 @@ constexpr int pair_min_blocks() {
                 : (Q == 15 ? LBM_PAIR_MIN_BLOCKS_Q15 : LBM_PAIR_MIN_BLOCKS_Q7);
 }
 
+// Pair t of row (j, k): the packed pair update away from the y and z walls, the general
+// pull for the two nodes of a row at one of them.
 template <typename S, int Q, bool UNIT>
-__global__ void __launch_bounds__(kPairThreads, (pair_min_blocks<Q, UNIT>()))
-    step_pair_kernel(const S* __restrict__ Fin, const S* __restrict__ Gin,
-                     const float* __restrict__ Tin, S* __restrict__ Fout,
-                     S* __restrict__ Gout, float* __restrict__ Tout, ParamsOf<S> p,
-                     PairParams q, const unsigned* __restrict__ ctr_in,
-                     unsigned* __restrict__ ctr_out) {
-    const uint32_t step = step_of<S>(ctr_in, ctr_out);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
+__device__ __forceinline__ void pair_row(const S* __restrict__ Fin, const S* __restrict__ Gin,
+                                         const float* __restrict__ Tin, S* __restrict__ Fout,
+                                         S* __restrict__ Gout, float* __restrict__ Tout, const ParamsOf<S>& p,
+                                         const PairParams& q, int t, int j, int k, uint32_t step) {
     const int npair = p.nx >> 1;
     if (t >= npair) return;
     if (j >= 1 && j + 1 < p.ny && k >= 1 && k + 1 < p.nz) {
         const int nx = p.nx, nxy = nx * p.ny;
         const int c0 = k * nxy + j * nx + 2 * t;
-        const uint32_t seed = dither_seed((uint32_t)(p.cell0 + c0), step);
+        const uint32_t seed = dither_weyl((uint32_t)(p.cell0 + c0), step);  // the pair hashes it
         if constexpr (UNIT)
             pair_node_unit<S, Q>(Fin, Gin, Tin, Fout, Gout, Tout, q, nx, nxy, (int)p.plane, c0,
                                  t == 0, t == npair - 1, seed);
@@ -130,6 +127,18 @@ __global__ void __launch_bounds__(kPairThreads, (pair_min_blocks<Q, UNIT>()))
         for (int e = 0; e < 2; ++e)
             cavity_node<S, Q, false, UNIT>(Fin, Gin, Tin, Fout, Gout, Tout, p, 2 * t + e, j, k, step);
     }
+}
+
+template <typename S, int Q, bool UNIT>
+__global__ void __launch_bounds__(kPairThreads, (pair_min_blocks<Q, UNIT>()))
+    step_pair_kernel(const S* __restrict__ Fin, const S* __restrict__ Gin,
+                     const float* __restrict__ Tin, S* __restrict__ Fout,
+                     S* __restrict__ Gout, float* __restrict__ Tout, ParamsOf<S> p,
+                     PairParams q, const unsigned* __restrict__ ctr_in,
+                     unsigned* __restrict__ ctr_out) {
+    const uint32_t step = step_of<S>(ctr_in, ctr_out);
+    pair_row<S, Q, UNIT>(Fin, Gin, Tin, Fout, Gout, Tout, p, q, blockIdx.x * blockDim.x + threadIdx.x,
+                         blockIdx.y, blockIdx.z, step);
 }
 
 // The pair parameters of a context's FP32 parameters, every value broadcast to both lanes.
