@@ -9,8 +9,9 @@ from the GPU's own pre-step state.
 Tolerances: FP32 |d| <= 1e-5 max(|p_oracle|, w_a) (flow) and 1e-5 max(|p_oracle|,
 w^phi_a dT) (scalar), as in test_gpu_parity.py; the 16-bit forms add the rounding of the
 stored deviation: under one unit in the last place, 2 x 2^-11 (FP16) or 2 x 2^-8 (BF16) of
-|p - p_rest| and for FP16 the smallest subnormal step (2^-24) -- the bound of stochastic
-rounding (the flow), twice that of rounding to nearest (the scalar)."""
+|p - p_rest| and for FP16 the smallest subnormal step (2^-24; the flow deviations, stored
+times 2^12, have a finer one) -- the bound of stochastic rounding (the flow), twice that of
+rounding to nearest (the scalar)."""
 import math
 
 import numpy as np
