@@ -49,7 +49,7 @@ enum { LBM_THERMAL_D3Q15 = 15, LBM_THERMAL_D3Q7 = 7 };
  * of the node holding it, kept in an FP32 plane) with FP32 arithmetic: FP16 (11 significant
  * bits; the flow deviations stored times 2^12, rounded stochastically, so that deviations
  * down to 1.5e-8 stay normal FP16 numbers) or BF16 (8 significant bits, FP32 range,
- * rounded to nearest).  The rounding of the stored deviations
+ * rounded to nearest); the scalar deviations are rounded to nearest.  The rounding of the stored deviations
  * puts a floor under the residual of lbm_residual (max |dT| per 100 steps about 2e-5 in
  * FP16 and 2e-4 in BF16 on 64^3-256^3 cavities), so a convergence test below that floor is
  * never met in those forms. */

@@ -81,6 +81,14 @@ struct Pack<__half> {
         if constexpr (SR) return from_float2_sr(v, dx, dy);
         else return from_float2(v);
     }
+    // from raw bits: a 32-bit word holding two values, or two 16-bit values
+    __device__ __forceinline__ static float2 word2(uint32_t w) {
+        return __half22float2(__halves2half2(__ushort_as_half((unsigned short)(w & 0xFFFFu)),
+                                             __ushort_as_half((unsigned short)(w >> 16))));
+    }
+    __device__ __forceinline__ static float2 bits2(unsigned short x, unsigned short y) {
+        return make_float2(__half2float(__ushort_as_half(x)), __half2float(__ushort_as_half(y)));
+    }
     // flow deviations: stored times 2^flow_exp (storage.cuh)
     static constexpr float up = Storage<__half>::fup, down = Storage<__half>::fdown;
     __device__ __forceinline__ static float2 flow2(two v) {
@@ -109,6 +117,13 @@ struct Pack<__nv_bfloat16> {
         if constexpr (SR) return from_float2_sr(v, dx, dy);
         else return from_float2(v);
     }
+    __device__ __forceinline__ static float2 word2(uint32_t w) {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+    }
+    __device__ __forceinline__ static float2 bits2(unsigned short x, unsigned short y) {
+        return make_float2(__uint_as_float((uint32_t)x << 16), __uint_as_float((uint32_t)y << 16));
+    }
+    static constexpr float up = 1.f, down = 1.f;
     // flow deviations: stored as they are
     __device__ __forceinline__ static float2 flow2(two v) { return to_float2(v); }
     __device__ __forceinline__ static float2 flow2(__nv_bfloat16 x, __nv_bfloat16 y) {
@@ -762,6 +777,124 @@ __device__ __forceinline__ void pair_node_unit(const S* __restrict__ Fin, const 
             const int i1 = hi ? c0 + r + (opp(a) - a) * P : c0 + 1;
             f[a].v = Pk::flow2(Fs[c0], Fs[i1]);
         }
+    }
+    pair_unit_update<S, Q>(m0, mx, my, mz, f, Fout, Gout, Tout, q, P, c0, seed);
+}
+
+// Read-only global loads as volatile statements: they keep their program order, so a
+// block of them is issued before the arithmetic that follows it.
+__device__ __forceinline__ uint32_t ldnc_b32(const void* p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned short ldnc_b16(const void* p) {
+    unsigned short v;
+    asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float2 ldnc_f2(const float* p) {
+    float2 v;
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ldnc_f(const float* p) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+// Whether the lattice of Q scalar directions has a link with these y, z components and an
+// x component of the given sign (sx = 0: any).
+template <int Q>
+__host__ __device__ constexpr bool has_link(int sx, int dy, int dz) {
+    for (int a = 0; a < Q; ++a)
+        if (ey(a) == dy && ez(a) == dz && (sx == 0 || ex(a) == sx)) return true;
+    return false;
+}
+
+// pair_node_unit with every load of the pair -- the raw 16-bit scalar and flow words and
+// the node temperatures, one pair per source row and one value per shifted source -- issued
+// in one block before any arithmetic, so that a warp waits for memory once per pair rather
+// than once per batch the compiler would otherwise form.  The same values as
+// pair_node_unit, bit for bit.
+template <typename S, int Q>
+__device__ __forceinline__ void pair_node_unit_early(const S* __restrict__ Fin, const S* __restrict__ Gin,
+                                                     const float* __restrict__ Tin, S* __restrict__ Fout,
+                                                     S* __restrict__ Gout, float* __restrict__ Tout,
+                                                     const PairParams& q, int nx, int nxy, int P, int c0,
+                                                     bool lo, bool hi, uint32_t seed) {
+    using Pk = Pack<S>;
+    uint32_t gw[Q], fw[15];
+    unsigned short gx[Q], gy[Q], fx[15], fy[15];
+    float2 Tp[9];
+    float T0[9], T1[9];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int r = ey(a) * nx + ez(a) * nxy;
+        const S* Ga = Gin + a * P;
+        if (ex(a) == 0) {
+            gw[a] = ldnc_b32(Ga + c0 - r);
+        } else if (ex(a) > 0) {
+            const S* Gs = Ga - r - 1;
+            gx[a] = ldnc_b16(Gs + (lo ? c0 + r + 1 + (opp(a) - a) * P : c0));
+            gy[a] = ldnc_b16(Gs + c0 + 1);
+        } else {
+            const S* Gs = Ga - r + 1;
+            gx[a] = ldnc_b16(Gs + c0);
+            gy[a] = ldnc_b16(Gs + (hi ? c0 + r + (opp(a) - a) * P : c0 + 1));
+        }
+    }
+#pragma unroll
+    for (int sl = 0; sl < 9; ++sl) {
+        const int dy = sl / 3 - 1, dz = sl % 3 - 1;
+        if (!has_link<Q>(0, dy, dz)) continue;
+        const int r = dy * nx + dz * nxy;
+        Tp[sl] = ldnc_f2(Tin + c0 - r);
+        if (has_link<Q>(1, dy, dz)) T0[sl] = ldnc_f(lo ? Tin + c0 : Tin + c0 - r - 1);
+        if (has_link<Q>(-1, dy, dz)) T1[sl] = ldnc_f(hi ? Tin + c0 + 1 : Tin + c0 - r + 2);
+    }
+#pragma unroll
+    for (int a = 0; a < 15; ++a) {
+        const int r = ey(a) * nx + ez(a) * nxy;
+        const S* Fa = Fin + a * P;
+        if (ex(a) == 0) {
+            fw[a] = ldnc_b32(Fa + c0 - r);
+        } else if (ex(a) > 0) {
+            const S* Fs = Fa - r - 1;
+            fx[a] = ldnc_b16(Fs + (lo ? c0 + r + 1 + (opp(a) - a) * P : c0));
+            fy[a] = ldnc_b16(Fs + c0 + 1);
+        } else {
+            const S* Fs = Fa - r + 1;
+            fx[a] = ldnc_b16(Fs + c0);
+            fy[a] = ldnc_b16(Fs + (hi ? c0 + r + (opp(a) - a) * P : c0 + 1));
+        }
+    }
+    Pair m0, mx, my, mz;
+    {
+        Pair g[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int sl = (ey(a) + 1) * 3 + (ez(a) + 1);
+            if (ex(a) == 0) {
+                g[a].v = fma2(q.wg[a], Tp[sl], Pk::word2(gw[a]));
+            } else if (ex(a) > 0) {
+                float2 v = fma2(q.wg[a], make_float2(T0[sl], Tp[sl].x), Pk::bits2(gx[a], gy[a]));
+                v.x = lo ? q.wTc2[a] - v.x : v.x;
+                g[a].v = v;
+            } else {
+                float2 v = fma2(q.wg[a], make_float2(Tp[sl].y, T1[sl]), Pk::bits2(gx[a], gy[a]));
+                v.y = hi ? q.wTh2[a] - v.y : v.y;
+                g[a].v = v;
+            }
+        }
+        raw_first<Pair, Q>(g, m0, mx, my, mz);
+    }
+    Pair f[15];  // the stored flow deviations f - w_a
+#pragma unroll
+    for (int a = 0; a < 15; ++a) {
+        f[a].v = ex(a) == 0 ? Pk::word2(fw[a]) : Pk::bits2(fx[a], fy[a]);
+        if constexpr (Pk::down != 1.f) f[a].v = mul2(f[a].v, make_float2(Pk::down, Pk::down));
     }
     pair_unit_update<S, Q>(m0, mx, my, mz, f, Fout, Gout, Tout, q, P, c0, seed);
 }

@@ -6,6 +6,8 @@
 // parallel).
 #pragma once
 
+#include <type_traits>
+
 #include "node.cuh"
 #include "pair.cuh"
 
@@ -90,21 +92,34 @@ constexpr int kPairThreads = 64;
 #endif
 // The unit-rate pair update (fewer live values): D3Q15 measured best at 8 blocks of 64
 // (128 registers; 10 and 14 blocks were 4% and 7% slower at 128^3), D3Q7 at 14 (72
-// registers; 10% faster than 8 at 128^3 and 256^3).
+// registers; 10% faster than 8 at 128^3 and 256^3).  FP16 D3Q15 with every load issued
+// ahead of the arithmetic (pair_node_unit_early) needs 106 registers, and at 10 blocks it
+// is 4.5% faster than the compiler's order at 8 (68.4 against 71.6 us at 128^3, 426 against
+// 443 us at 256^3); BF16 measured 2% slower that way and keeps the compiler's order.
 #ifndef LBM_PAIR_UNIT_MIN_BLOCKS_Q15
 #define LBM_PAIR_UNIT_MIN_BLOCKS_Q15 8
 #endif
 #ifndef LBM_PAIR_UNIT_MIN_BLOCKS_Q7
 #define LBM_PAIR_UNIT_MIN_BLOCKS_Q7 14
 #endif
-template <int Q, bool UNIT>
-constexpr int pair_min_blocks() {
-    return UNIT ? (Q == 15 ? LBM_PAIR_UNIT_MIN_BLOCKS_Q15 : LBM_PAIR_UNIT_MIN_BLOCKS_Q7)
-                : (Q == 15 ? LBM_PAIR_MIN_BLOCKS_Q15 : LBM_PAIR_MIN_BLOCKS_Q7);
+#ifndef LBM_PAIR_EARLY_MIN_BLOCKS
+#define LBM_PAIR_EARLY_MIN_BLOCKS 10
+#endif
+#ifndef LBM_PAIR_EARLY_LOADS
+#define LBM_PAIR_EARLY_LOADS 1
+#endif
+template <typename S, int Q, bool UNIT>
+constexpr bool pair_early_loads() {
+    return LBM_PAIR_EARLY_LOADS && UNIT && Q == 15 && std::is_same<S, __half>::value;
 }
 
-// Pair t of row (j, k): the packed pair update away from the y and z walls, the general
-// pull for the two nodes of a row at one of them.
+template <typename S, int Q, bool UNIT>
+constexpr int pair_min_blocks() {
+    return pair_early_loads<S, Q, UNIT>() ? LBM_PAIR_EARLY_MIN_BLOCKS
+           : UNIT ? (Q == 15 ? LBM_PAIR_UNIT_MIN_BLOCKS_Q15 : LBM_PAIR_UNIT_MIN_BLOCKS_Q7)
+                  : (Q == 15 ? LBM_PAIR_MIN_BLOCKS_Q15 : LBM_PAIR_MIN_BLOCKS_Q7);
+}
+
 template <typename S, int Q, bool UNIT>
 __device__ __forceinline__ void pair_row(const S* __restrict__ Fin, const S* __restrict__ Gin,
                                          const float* __restrict__ Tin, S* __restrict__ Fout,
@@ -116,9 +131,14 @@ __device__ __forceinline__ void pair_row(const S* __restrict__ Fin, const S* __r
         const int nx = p.nx, nxy = nx * p.ny;
         const int c0 = k * nxy + j * nx + 2 * t;
         const uint32_t seed = dither_weyl((uint32_t)(p.cell0 + c0), step);  // the pair hashes it
-        if constexpr (UNIT)
-            pair_node_unit<S, Q>(Fin, Gin, Tin, Fout, Gout, Tout, q, nx, nxy, (int)p.plane, c0,
-                                 t == 0, t == npair - 1, seed);
+        if constexpr (UNIT) {
+            if constexpr (pair_early_loads<S, Q, UNIT>())
+                pair_node_unit_early<S, Q>(Fin, Gin, Tin, Fout, Gout, Tout, q, nx, nxy, (int)p.plane, c0,
+                                           t == 0, t == npair - 1, seed);
+            else
+                pair_node_unit<S, Q>(Fin, Gin, Tin, Fout, Gout, Tout, q, nx, nxy, (int)p.plane, c0,
+                                     t == 0, t == npair - 1, seed);
+        }
         else
             pair_node<S, Q>(Fin, Gin, Tin, Fout, Gout, Tout, q, nx, nxy, (int)p.plane, c0,
                             t == 0, t == npair - 1, seed);
@@ -130,7 +150,7 @@ __device__ __forceinline__ void pair_row(const S* __restrict__ Fin, const S* __r
 }
 
 template <typename S, int Q, bool UNIT>
-__global__ void __launch_bounds__(kPairThreads, (pair_min_blocks<Q, UNIT>()))
+__global__ void __launch_bounds__(kPairThreads, (pair_min_blocks<S, Q, UNIT>()))
     step_pair_kernel(const S* __restrict__ Fin, const S* __restrict__ Gin,
                      const float* __restrict__ Tin, S* __restrict__ Fout,
                      S* __restrict__ Gout, float* __restrict__ Tout, ParamsOf<S> p,

@@ -68,12 +68,15 @@ __device__ __forceinline__ uint32_t dither_of(uint32_t seed, int a) {
     return seed + (uint32_t)a * 0x632BE5ABu;
 }
 
-// Which stores of the 16-bit forms round stochastically (the others round to nearest).
-// Measured on the 48^3, Ra = 1e4 cavity from rest (steady mid-plane / hot-wall Nu against
-// FP32): FP16 with stochastic flow stores -0.09% / -0.08% (to nearest: +0.56% / +0.46%);
-// BF16, whose 8 significant bits make the stochastic noise itself bias the state, is best
-// to nearest in both (+0.32% / +0.56%; stochastic flow -1.18% / -0.91%, both stochastic
-// -1.05% / -0.80%, stochastic scalar only +0.46% / +0.71%).
+// Which stores of the 16-bit forms round stochastically (the others round to nearest):
+// FP16's flow deviations.  Measured against FP32 at the FP32 steady state's step count
+// (mid-plane / hot-wall Nu, u_max): FP16 at 128^3, Ra = 1e5: +0.019% / +0.021% / +0.006%;
+// at 256^3, Ra = 1e6: -0.15% / -0.17% / -0.55% (to nearest: -0.98% / +0.44% / +15.7%).
+// BF16, 8 significant bits, to nearest: +4.5% / +2.9% / +35% at 128^3, +1.9% / +1.0% / +104%
+// at 256^3; with stochastic flow stores it is within 0.1% at 48^3 and 128^3 but -2.5% at
+// 64^3 (against FP64) and drifts away at 256^3, Ra = 1e6 (-12% / -9% after 288 000 steps,
+// still falling): its rounding noise, eight times FP16's, stirs the low-viscosity flow.
+// BF16 therefore rounds to nearest, a bias that does not grow.
 #ifndef LBM_SR_FLOW_FP16
 #define LBM_SR_FLOW_FP16 1
 #endif

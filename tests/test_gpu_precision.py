@@ -89,9 +89,7 @@ def test_steady_nusselt_of_the_16bit_forms():
     # 48^3, Ra = 1e4, every form from rest for 60 000 steps (FP32 is steady, max |dT| per
     # 100 steps < 1e-6, from about 22 000 on; the 16-bit forms' max |dT| has a rounding
     # floor above that and cannot signal their own convergence): steady Nu of FP16 within
-    # 0.5% of FP32, the precision form's target (measured -0.09% with its stochastically
-    # rounded flow stores); BF16 (8 significant bits, rounded to nearest) within 1%
-    # (measured +0.32% mid-plane, +0.56% hot wall: just above the target)
+    # 0.5% of FP32, the precision form's target; BF16 (8 significant bits) within 1%
     from paper_1710_04751_gb300.precision import run_steps
     out = {}
     for name in ("FP32", "FP16_DEV", "BF16_DEV"):
