@@ -37,13 +37,6 @@
 #define LBM_PAIR_LEAN_Q7 0
 #endif
 
-// 1: the unit-rate pair update issues the flow loads only after the scalar pull has been
-// reduced to its four sums (fewer registers, more resident warps); 0: the compiler may
-// overlap the two pulls.
-#ifndef LBM_PAIR_UNIT_PHASES
-#define LBM_PAIR_UNIT_PHASES 0
-#endif
-
 namespace lbm {
 
 // ---------------------------------------------------------------------------------
@@ -758,9 +751,6 @@ __device__ __forceinline__ void pair_node_unit(const S* __restrict__ Fin, const 
         }
         raw_first<Pair, Q>(g, m0, mx, my, mz);
     }
-#if LBM_PAIR_UNIT_PHASES
-    asm volatile("" ::: "memory");  // the flow loads are issued after the scalar sums
-#endif
     Pair f[15];  // the stored flow deviations f - w_a
 #pragma unroll
     for (int a = 0; a < 15; ++a) {
