@@ -1,7 +1,8 @@
 // gemm.cu -- BF16 GEMM with FP32 accumulation on the tcgen05 tensor cores:
 //   C[M][N] (+)= sum_k A[m][k] * B[n][k]      (both operands K-major, row-major storage)
-// One CTA of 128 threads computes a 128 x BN tile: warp 0 lane 0 streams 128 x 64 and
-// BN x 64 operand tiles into a 4-stage shared-memory ring with TMA (128-byte swizzle);
+// One CTA of 128 threads computes a 128 x BN tile (two of them, sharing each B tile, for a
+// tall GEMM of 256 columns): warp 0 lane 0 streams 128 x 64 and BN x 64 operand tiles into
+// a shared-memory ring of up to 4 stages with TMA (128-byte swizzle);
 // warp 1 lane 0 issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a TMEM
 // accumulator and frees each stage with tcgen05.commit; then all four warps read the
 // accumulator back (warp w owns TMEM lanes 32w..32w+31 = rows 32w..32w+31) and store it.
@@ -23,15 +24,18 @@
 namespace lbm {
 namespace nn {
 
-constexpr int BM = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BK = 64;
 
-template <int BN>
+// MT 128-row tiles per CTA share each staged B tile (MT = 2 halves the B traffic from L2
+// of a tall GEMM); the ring takes what shared memory allows, at most 4 stages.
+template <int BN, int MT = 1>
 struct GemmSmem {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
-    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGE = MT * A_BYTES + B_BYTES;
+    static constexpr int STAGES = (200 * 1024) / STAGE < 4 ? (200 * 1024) / STAGE : 4;
     static constexpr int BYTES = 1024 + STAGES * STAGE + 256;  // + alignment + barriers
-    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+    static constexpr uint32_t TMEM_COLS = MT * BN < 32 ? 32 : MT * BN;
 };
 
 struct GemmArgs {
@@ -46,11 +50,12 @@ struct GemmArgs {
     int withhold_loads;  // diagnostic only: issue no operand loads, so the ring wait runs out
 };
 
-template <int BN>
+template <int BN, int MT>
 __global__ void __launch_bounds__(128, 1)
     gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB, GemmArgs args) {
-    using L = GemmSmem<BN>;
+    using L = GemmSmem<BN, MT>;
+    constexpr int STAGES = L::STAGES;
     extern __shared__ uint8_t gemm_smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -63,7 +68,7 @@ __global__ void __launch_bounds__(128, 1)
     // a CTA that starts after another one timed out does nothing
     if (*static_cast<volatile int*>(args.err) != 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int m0 = blockIdx.x * BM * MT, n0 = blockIdx.y * BN;
     const int kb_total = (args.K + BK - 1) / BK;
     const int kb0 = blockIdx.z * args.kblocks_per_split;
     const int nkb = min(args.kblocks_per_split, kb_total - kb0);
@@ -95,8 +100,10 @@ __global__ void __launch_bounds__(128, 1)
             if (failed) break;
             uint8_t* a = smem + s * L::STAGE;
             mbar_expect_tx(full + s, L::STAGE);
-            tma_load_2d(a, &tmA, full + s, (kb0 + i) * BK, m0);
-            tma_load_2d(a + L::A_BYTES, &tmB, full + s, (kb0 + i) * BK, n0);
+#pragma unroll
+            for (int t = 0; t < MT; ++t)
+                tma_load_2d(a + t * L::A_BYTES, &tmA, full + s, (kb0 + i) * BK, m0 + t * BM);
+            tma_load_2d(a + MT * L::A_BYTES, &tmB, full + s, (kb0 + i) * BK, n0);
             ++issued;
         }
     } else if (nkb > 0 && warp == 1 && lane == 0) {
@@ -109,11 +116,13 @@ __global__ void __launch_bounds__(128, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t a = smem_u32(smem + s * L::STAGE), b = a + L::A_BYTES;
+            const uint32_t a = smem_u32(smem + s * L::STAGE), b = a + MT * L::A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-                mma_bf16(tmem, sdesc_k_sw128(a + kk * 32), sdesc_k_sw128(b + kk * 32), idesc,
-                         (i > 0 || kk > 0) ? 1u : 0u);
+            for (int t = 0; t < MT; ++t)
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    mma_bf16(tmem + (uint32_t)(t * BN), sdesc_k_sw128(a + t * L::A_BYTES + kk * 32),
+                             sdesc_k_sw128(b + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
             mma_commit(empty + s);
         }
         mma_commit(done);  // also when stopped early: every issued MMA drains before dealloc
@@ -129,12 +138,13 @@ __global__ void __launch_bounds__(128, 1)
             mbar_wait(full + (i % STAGES), (uint32_t)(i / STAGES) & 1u, args.err, 4);
     }
     tc_fence_after();
-    if (ok) {
-        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int t = 0; t < MT && ok; ++t) {
+        const int row = m0 + t * BM + warp * 32 + lane;
 #pragma unroll 1
         for (int c = 0; c < BN; c += 16) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * BN + c), v);
             if (row < args.M) {
                 const int col0 = n0 + c;
                 const bool full = args.vec && col0 + 16 <= args.N;  // 16-byte stores
@@ -219,19 +229,19 @@ static bool make_map(CUtensorMap* map, const void* base, int rows, int cols, lon
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int MT = 1>
 static cudaError_t launch(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& a,
                           int splits, cudaStream_t st) {
-    using L = GemmSmem<BN>;
+    using L = GemmSmem<BN, MT>;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(gemm_bf16_tn_kernel<BN>,
+        attr = cudaFuncSetAttribute(gemm_bf16_tn_kernel<BN, MT>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
     });
     if (attr != cudaSuccess) return attr;
-    const dim3 grid((a.M + BM - 1) / BM, (a.N + BN - 1) / BN, splits);
-    gemm_bf16_tn_kernel<BN><<<grid, 128, L::BYTES, st>>>(ta, tb, a);
+    const dim3 grid((a.M + BM * MT - 1) / (BM * MT), (a.N + BN - 1) / BN, splits);
+    gemm_bf16_tn_kernel<BN, MT><<<grid, 128, L::BYTES, st>>>(ta, tb, a);
     return cudaGetLastError();
 }
 
@@ -243,6 +253,12 @@ static int split_count(int K, int splits, int* per) {
     *per = (kb_total + splits - 1) / splits;
     return (kb_total + *per - 1) / *per;
 }
+
+// Rows from which a 256-column GEMM takes two M tiles per CTA (enough CTAs for 152 SMs).
+#ifndef LBM_GEMM_TALL_ROWS
+#define LBM_GEMM_TALL_ROWS 16384
+#endif
+constexpr int kTallRows = LBM_GEMM_TALL_ROWS;
 
 cudaError_t gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B,
                       long long ldb, void* C, long long ldc, int M, int N, int K, int out_mode,
@@ -265,7 +281,10 @@ cudaError_t gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16
     case 32: return launch<32>(ta, tb, a, splits, st);
     case 64: return launch<64>(ta, tb, a, splits, st);
     case 128: return launch<128>(ta, tb, a, splits, st);
-    default: return launch<256>(ta, tb, a, splits, st);
+    default:
+        // a tall GEMM: two 128-row tiles per CTA share the B tile (half the L2 reads of B)
+        if (a.M >= kTallRows) return launch<256, 2>(ta, tb, a, splits, st);
+        return launch<256>(ta, tb, a, splits, st);
     }
 }
 
