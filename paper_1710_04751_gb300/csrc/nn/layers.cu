@@ -78,6 +78,63 @@ cudaError_t im2col(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_b
     return cudaGetLastError();
 }
 
+// ---- im2col, transposed: XcolT[k][m] = Xcol[m][k], written directly ---------------------
+// One block per (tap, 32-channel chunk, 64 consecutive voxels): the 64 shifted source
+// voxels' 32 channels (64 B each) are read into shared memory, and the 32 rows of XcolT
+// they form are written as 128-byte row segments.  Rows k >= 27 cin are not touched.
+__global__ void __launch_bounds__(256) im2colT_kernel(const __nv_bfloat16* __restrict__ X, int B, int n,
+                                                      int cin, int64_t M, __nv_bfloat16* __restrict__ XcolT) {
+    __shared__ __align__(16) __nv_bfloat16 tile[64][40];  // 80-byte rows: 16-byte aligned, fewer conflicts
+    const int chunks = cin / 32;
+    const int tap = blockIdx.y / chunks, c0 = (blockIdx.y - tap * chunks) * 32;
+    const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
+    const int64_t m0 = (int64_t)blockIdx.x * 64;
+    const int t = threadIdx.x;
+    {
+        const int v = t >> 2, g = t & 3;  // voxel of the block, 8-channel group
+        const int64_t m = m0 + v;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (m < M) {
+            const int x = (int)(m % n), y = (int)((m / n) % n), z = (int)((m / ((int64_t)n * n)) % n);
+            const int b = (int)(m / ((int64_t)n * n * n));
+            const int sz = z + kz - 1, sy = y + ky - 1, sx = x + kx - 1;
+            if ((unsigned)sz < (unsigned)n && (unsigned)sy < (unsigned)n && (unsigned)sx < (unsigned)n)
+                val = *reinterpret_cast<const uint4*>(X + vox(b, sz, sy, sx, n) * cin + c0 + g * 8);
+        }
+        *reinterpret_cast<uint4*>(&tile[v][g * 8]) = val;
+    }
+    __syncthreads();
+    {
+        const int j = t >> 3, sgm = t & 7;  // channel row of the block, 8-voxel segment
+        const int64_t m = m0 + sgm * 8;
+        if (m + 8 <= M) {
+            __align__(16) __nv_bfloat16 out[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) out[e] = tile[sgm * 8 + e][j];
+            *reinterpret_cast<uint4*>(XcolT + (int64_t)(tap * cin + c0 + j) * M + m) =
+                *reinterpret_cast<const uint4*>(out);
+        } else {
+            for (int e = 0; e < 8 && m + e < M; ++e) XcolT[(int64_t)(tap * cin + c0 + j) * M + m + e] = tile[sgm * 8 + e][j];
+        }
+    }
+}
+
+bool im2colT_supported(int cin, int64_t M) { return cin % 32 == 0 && M % 8 == 0; }
+
+cudaError_t im2colT(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_bfloat16* XcolT,
+                    cudaStream_t st) {
+    const int64_t M = (int64_t)B * n * n * n;
+    if (!im2colT_supported(cin, M) || Kp < 27 * cin || ((uintptr_t)X & 15) || ((uintptr_t)XcolT & 15))
+        return cudaErrorInvalidValue;
+    const int64_t gx = (M + 63) / 64;
+    if (gx > 2147483647LL) return cudaErrorInvalidValue;
+    im2colT_kernel<<<dim3((unsigned)gx, 27 * (cin / 32)), 256, 0, st>>>(X, B, n, cin, M, XcolT);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || Kp == 27 * cin) return e;
+    // the padding rows 27 cin .. Kp - 1 read as zeros
+    return cudaMemsetAsync(XcolT + (int64_t)27 * cin * M, 0, (size_t)(Kp - 27 * cin) * M * 2, st);
+}
+
 // ---- transpose of a BF16 matrix (32 x 32 tiles through shared memory) -----------------
 __global__ void transpose_kernel(const __nv_bfloat16* __restrict__ in, int64_t R, int64_t C,
                                  int64_t ld_in, __nv_bfloat16* __restrict__ out, int64_t ld_out) {
