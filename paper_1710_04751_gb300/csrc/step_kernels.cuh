@@ -13,6 +13,37 @@
 
 namespace lbm {
 
+// Programmatic dependent launch of the step kernels (LBM_PDL): a step kernel is launched
+// so that its blocks may be scheduled while the kernel before it on the stream drains its
+// last wave; every block first waits (griddepcontrol.wait) for that kernel's completion
+// and memory -- before it reads or writes anything -- and then allows the next step's
+// launch to begin (griddepcontrol.launch_dependents).  Launched without the attribute
+// (the batched and slab paths) both instructions do nothing.
+#ifndef LBM_PDL
+#define LBM_PDL 1
+#endif
+__device__ __forceinline__ void pdl_begin() {
+    if (LBM_PDL) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    }
+}
+
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = LBM_PDL ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Generic kernel: one thread per node of the flattened grid, any boundary mode.
 // The step number of the 16-bit forms' rounding dither: read from the counter of the
 // source buffer's parity; the launch's first thread writes the next value into the other
@@ -40,6 +71,7 @@ __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ Fin,
                                                    const unsigned* __restrict__ ctr_in,
                                                    unsigned* __restrict__ ctr_out) {
     using real = typename Storage<S>::real;
+    pdl_begin();
     const uint32_t step = step_of<S>(ctr_in, ctr_out);
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= p.ncell) return;
@@ -64,6 +96,7 @@ __global__ void __launch_bounds__(128, (cavity_min_blocks<S, Q>()))
                        const float* __restrict__ Tin, S* __restrict__ Fout,
                        S* __restrict__ Gout, float* __restrict__ Tout, ParamsOf<S> p,
                        const unsigned* __restrict__ ctr_in, unsigned* __restrict__ ctr_out) {
+    pdl_begin();
     const uint32_t step = step_of<S>(ctr_in, ctr_out);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
@@ -156,6 +189,7 @@ __global__ void __launch_bounds__(kPairThreads, (pair_min_blocks<S, Q, UNIT>()))
                      S* __restrict__ Gout, float* __restrict__ Tout, ParamsOf<S> p,
                      PairParams q, const unsigned* __restrict__ ctr_in,
                      unsigned* __restrict__ ctr_out) {
+    pdl_begin();
     const uint32_t step = step_of<S>(ctr_in, ctr_out);
     pair_row<S, Q, UNIT>(Fin, Gin, Tin, Fout, Gout, Tout, p, q, blockIdx.x * blockDim.x + threadIdx.x,
                          blockIdx.y, blockIdx.z, step);
@@ -228,11 +262,11 @@ bool launch_pair(const DevState& s, int cur, const ParamsOf<S>& p, cudaStream_t 
         const int bx = npair <= 32 ? 32 : kPairThreads;
         const dim3 grid((npair + bx - 1) / bx, p.ny, p.nz);
         if (s.Q == 15)
-            step_pair_kernel<S, 15, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, q,
-                                                                s.step_ctr + cur, s.step_ctr + (cur ^ 1));
+            launch_pdl(step_pair_kernel<S, 15, UNIT>, grid, dim3(bx), st, Fin, Gin, Tin, Fout, Gout, Tout, p, q,
+                       (const unsigned*)(s.step_ctr + cur), s.step_ctr + (cur ^ 1));
         else
-            step_pair_kernel<S, 7, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, q,
-                                                               s.step_ctr + cur, s.step_ctr + (cur ^ 1));
+            launch_pdl(step_pair_kernel<S, 7, UNIT>, grid, dim3(bx), st, Fin, Gin, Tin, Fout, Gout, Tout, p, q,
+                       (const unsigned*)(s.step_ctr + cur), s.step_ctr + (cur ^ 1));
         return true;
     }
 }
@@ -253,22 +287,18 @@ cudaError_t launch_step_as(const DevState& s, int cur, const ParamsOf<S>& p, cud
         const int bx = 128;
         const dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
         if (s.Q == 15)
-            step_cavity_kernel<S, 15, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, ctr_in,
-                                                                  ctr_out);
-        else
-            step_cavity_kernel<S, 7, UNIT><<<grid, bx, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p, ctr_in,
-                                                                 ctr_out);
-        return cudaGetLastError();
+            return launch_pdl(step_cavity_kernel<S, 15, UNIT>, grid, dim3(bx), st, Fin, Gin, Tin, Fout, Gout,
+                              Tout, p, ctr_in, ctr_out);
+        return launch_pdl(step_cavity_kernel<S, 7, UNIT>, grid, dim3(bx), st, Fin, Gin, Tin, Fout, Gout, Tout,
+                          p, ctr_in, ctr_out);
     }
     const int threads = 256;
     const int64_t blocks = (p.ncell + threads - 1) / threads;
     if (s.Q == 15)
-        step_kernel<S, 15, UNIT><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p,
-                                                                        ctr_in, ctr_out);
-    else
-        step_kernel<S, 7, UNIT><<<(unsigned)blocks, threads, 0, st>>>(Fin, Gin, Tin, Fout, Gout, Tout, p,
-                                                                       ctr_in, ctr_out);
-    return cudaGetLastError();
+        return launch_pdl(step_kernel<S, 15, UNIT>, dim3((unsigned)blocks), dim3(threads), st, Fin, Gin, Tin,
+                          Fout, Gout, Tout, p, ctr_in, ctr_out);
+    return launch_pdl(step_kernel<S, 7, UNIT>, dim3((unsigned)blocks), dim3(threads), st, Fin, Gin, Tin, Fout,
+                      Gout, Tout, p, ctr_in, ctr_out);
 }
 
 }  // namespace lbm
