@@ -84,6 +84,8 @@ def sum_over_ranks(dist, value, device=None):
 # clocks sampled during the timed region
 # ----------------------------------------------------------------------------------
 
+CLOCK_LOAD_STEPS = 6000  # about 0.5 s of 128^3 steps
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -175,10 +177,20 @@ def run_variant(lbm, q, steps, warmup, dist, device, clocks=None, precision=None
     torch.cuda.synchronize()
     barrier(dist)
     if clocks is not None:
+        # the timed region is a few ms, shorter than nvidia-smi's sampling period: the
+        # sampler runs over a window of back-to-back steps (about 0.5 s each side) that
+        # encloses it, so that its samples are taken under the same load
         clocks.start()
-        time.sleep(0.3)
+        time.sleep(0.15)
+        sim.step(CLOCK_LOAD_STEPS)
+        torch.cuda.synchronize()
     elapsed = time_steps(sim, steps, stream)
+    if clocks is not None:
+        sim.step(CLOCK_LOAD_STEPS)
+        torch.cuda.synchronize()
     clk = clocks.stop() if clocks is not None else None
+    if clk is not None:
+        clk["window"] = f"{CLOCK_LOAD_STEPS} steps before and after the timed region"
     barrier(dist)
     elapsed_max = max_over_ranks(dist, elapsed, device)
     nu = sim.nusselt()
