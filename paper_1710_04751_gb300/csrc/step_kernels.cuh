@@ -141,14 +141,24 @@ constexpr int kPairThreads = 64;
 #ifndef LBM_PAIR_EARLY_LOADS
 #define LBM_PAIR_EARLY_LOADS 1
 #endif
+#ifndef LBM_PAIR_EARLY_Q7
+#define LBM_PAIR_EARLY_Q7 0
+#endif
+#ifndef LBM_PAIR_EARLY_BF16
+#define LBM_PAIR_EARLY_BF16 0
+#endif
+#ifndef LBM_PAIR_EARLY_MIN_BLOCKS_Q7
+#define LBM_PAIR_EARLY_MIN_BLOCKS_Q7 14
+#endif
 template <typename S, int Q, bool UNIT>
 constexpr bool pair_early_loads() {
-    return LBM_PAIR_EARLY_LOADS && UNIT && Q == 15 && std::is_same<S, __half>::value;
+    return LBM_PAIR_EARLY_LOADS && UNIT && (Q == 15 || LBM_PAIR_EARLY_Q7) &&
+           (std::is_same<S, __half>::value || LBM_PAIR_EARLY_BF16);
 }
 
 template <typename S, int Q, bool UNIT>
 constexpr int pair_min_blocks() {
-    return pair_early_loads<S, Q, UNIT>() ? LBM_PAIR_EARLY_MIN_BLOCKS
+    return pair_early_loads<S, Q, UNIT>() ? (Q == 15 ? LBM_PAIR_EARLY_MIN_BLOCKS : LBM_PAIR_EARLY_MIN_BLOCKS_Q7)
            : UNIT ? (Q == 15 ? LBM_PAIR_UNIT_MIN_BLOCKS_Q15 : LBM_PAIR_UNIT_MIN_BLOCKS_Q7)
                   : (Q == 15 ? LBM_PAIR_MIN_BLOCKS_Q15 : LBM_PAIR_MIN_BLOCKS_Q7);
 }
