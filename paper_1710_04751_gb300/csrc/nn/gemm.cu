@@ -254,9 +254,10 @@ static int split_count(int K, int splits, int* per) {
     return (kb_total + *per - 1) / *per;
 }
 
-// Rows from which a 256-column GEMM takes two M tiles per CTA (enough CTAs for 152 SMs).
+// Rows from which a 256-column GEMM takes two M tiles per CTA: from 160 pairs of tiles up,
+// so that the CTAs still cover the 152 SMs (at 16384 rows the pairs would leave 88 idle).
 #ifndef LBM_GEMM_TALL_ROWS
-#define LBM_GEMM_TALL_ROWS 16384
+#define LBM_GEMM_TALL_ROWS 40960
 #endif
 constexpr int kTallRows = LBM_GEMM_TALL_ROWS;
 

@@ -34,7 +34,7 @@ def reference(A, B):
                                    (1024, 256, 1024), (130, 16, 72), (512, 200, 640),
                                    (4096, 128, 1728),
                                    # tall 256-column GEMMs: two M tiles per CTA, ragged last pair
-                                   (16584, 256, 320), (16400, 200, 136)])
+                                   (41000, 256, 192), (40968, 200, 136)])
 def test_gemm_f32_against_fp64(M, N, K):
     torch = torch_mod()
     from paper_1710_04751_gb300 import net
