@@ -594,7 +594,7 @@ def gpu_arm(args):
     lbm.load()
 
     peak, peak_kind = measured_peak_gbs()
-    clocks = ClockSampler(local)
+    clocks = None if args.no_clocks else ClockSampler(local)
     main = run_variant(lbm, 15, args.steps, args.warmup, dist, device, clocks)
     variant = run_variant(lbm, 7, args.steps, args.warmup, dist, device, None)
     half_steps = max(1, args.steps // 4)
@@ -772,6 +772,8 @@ def main(argv=None):
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--no-net", action="store_true", help="skip the warm-start network timings")
     ap.add_argument("--no-slabs", action="store_true", help="skip the z-slab decomposition timings")
+    ap.add_argument("--no-clocks", action="store_true",
+                    help="no clock sampling (and none of its load steps around the timed region)")
     ap.add_argument("--warmstart", action="store_true",
                     help="also run the learned warm start end to end (about 15 minutes)")
     ap.add_argument("--ws-train", type=int, default=400)
