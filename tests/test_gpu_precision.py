@@ -104,6 +104,25 @@ def test_steady_nusselt_of_the_16bit_forms():
             assert out[name]["nu"][k] == pytest.approx(ref[k], rel=tol), (name, k)
 
 
+@pytest.mark.timeout(600)
+def test_fp16_steady_state_of_the_bench_cavity():
+    # 128^3, Ra = 1e5 (the bench's cavity), from rest for FP32's 112 000 steps to its steady
+    # state: FP16, whose stochastic rounding draws its dither from a hash of (node, step),
+    # ends within 0.1% of FP32 in every Nusselt number and peak velocity (measured 0.005-0.05%
+    # except Nu_min -0.04%).  With a dither regular over the nodes (a Weyl sequence) the same
+    # comparison was off by 0.35% at this size and drifted by 12-16% at 256^3, Ra = 1e6.
+    from paper_1710_04751_gb300.precision import run_steps
+    out = {}
+    for name in ("FP32", "FP16_DEV"):
+        sim, rec = run_steps(128, 1e5, name, 112_000)
+        sim.close()
+        out[name] = rec["nu"]
+    print(out)
+    for k in ("hot_wall_mean", "cold_wall_mean", "mid_mean", "mid_max", "umax", "wmax"):
+        assert out["FP16_DEV"][k] == pytest.approx(out["FP32"][k], rel=1e-3), k
+    assert out["FP16_DEV"]["mid_min"] == pytest.approx(out["FP32"]["mid_min"], rel=2e-3)
+
+
 # ------------------------------------------------------------------------------------
 # The pair kernel of the 16-bit forms: a cavity with an even nx updates two x-neighbours
 # per thread with packed FP32 pair arithmetic in every row away from the y and z walls
