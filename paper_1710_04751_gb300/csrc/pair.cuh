@@ -15,7 +15,12 @@
 //
 // Used for rows away from the y and z walls of the cavity with an even nx (the pair
 // (2t, 2t+1) then starts at an even node index, so the 32-bit and 64-bit accesses are
-// aligned); the kernel falls back to node.cuh's update for the other rows.
+// aligned); the kernel falls back to node.cuh's update for the other rows.  At the paper's
+// unit higher-order rates the update is pair_node_unit (collide_unit.cuh), for FP16 D3Q15
+// with every load issued ahead of the arithmetic (pair_node_unit_early).  The `seed` of a
+// pair is the Weyl value of its first node (dither_weyl of the global node index and the
+// step); the stores hash it into each node's rounding dither (storage.cuh), the same
+// dither node.cuh draws for the node.
 #pragma once
 
 #include <cuda_bf16.h>
