@@ -68,10 +68,35 @@ __global__ void im2col1_kernel(const __nv_bfloat16* __restrict__ X, int B, int n
     }
 }
 
+// cin a multiple of 4 (the network's 4-channel input layer): 4 channels (8 bytes) per thread.
+__global__ void im2col4_kernel(const __nv_bfloat16* __restrict__ X, int B, int n, int cin, int Kp,
+                               __nv_bfloat16* __restrict__ Xcol) {
+    const int kq = Kp / 4;
+    const int64_t total = (int64_t)B * n * n * n * kq;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = q / kq;
+        const int k = (int)(q - m * kq) * 4;
+        uint2 v = make_uint2(0, 0);
+        if (k < 27 * cin) {
+            const int tap = k / cin, ci = k - tap * cin;
+            const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
+            const int x = (int)(m % n), y = (int)((m / n) % n), z = (int)((m / ((int64_t)n * n)) % n);
+            const int b = (int)(m / ((int64_t)n * n * n));
+            const int sz = z + kz - 1, sy = y + ky - 1, sx = x + kx - 1;
+            if ((unsigned)sz < (unsigned)n && (unsigned)sy < (unsigned)n && (unsigned)sx < (unsigned)n)
+                v = *reinterpret_cast<const uint2*>(X + vox(b, sz, sy, sx, n) * cin + ci);
+        }
+        *reinterpret_cast<uint2*>(Xcol + m * Kp + k) = v;
+    }
+}
+
 cudaError_t im2col(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_bfloat16* Xcol,
                    cudaStream_t st) {
     const int64_t M = (int64_t)B * n * n * n;
-    if (cin % 8 == 0)
+    if (cin % 4 == 0 && cin % 8 != 0 && Kp % 4 == 0 && ((uintptr_t)X & 7) == 0 && ((uintptr_t)Xcol & 7) == 0)
+        im2col4_kernel<<<blocks_for(M * (Kp / 4), 256), 256, 0, st>>>(X, B, n, cin, Kp, Xcol);
+    else if (cin % 8 == 0)
         im2col8_kernel<<<blocks_for(M * (Kp / 8), 256), 256, 0, st>>>(X, B, n, cin, Kp, Xcol);
     else
         im2col1_kernel<<<blocks_for(M * Kp, 256), 256, 0, st>>>(X, B, n, cin, Kp, Xcol);
@@ -79,56 +104,71 @@ cudaError_t im2col(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_b
 }
 
 // ---- im2col, transposed: XcolT[k][m] = Xcol[m][k], written directly ---------------------
-// One block per (tap, 32-channel chunk, 64 consecutive voxels): the 64 shifted source
-// voxels' 32 channels (64 B each) are read into shared memory, and the 32 rows of XcolT
-// they form are written as 128-byte row segments.  Rows k >= 27 cin are not touched.
-__global__ void __launch_bounds__(256) im2colT_kernel(const __nv_bfloat16* __restrict__ X, int B, int n,
-                                                      int cin, int64_t M, __nv_bfloat16* __restrict__ XcolT) {
-    __shared__ __align__(16) __nv_bfloat16 tile[64][40];  // 80-byte rows: 16-byte aligned, fewer conflicts
-    const int chunks = cin / 32;
-    const int tap = blockIdx.y / chunks, c0 = (blockIdx.y - tap * chunks) * 32;
-    const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
-    const int64_t m0 = (int64_t)blockIdx.x * 64;
+// A tile is (tap, 32-channel chunk, 64 consecutive voxels); blocks take tiles by grid
+// stride, the 27 cin / 32 tiles of a voxel block one after the other (their sources stay
+// in cache while the XcolT rows stream out).  Each thread reads 8 channels (16 B) of one shifted source voxel and scatters them
+// into a shared [32 channels][66] BF16 tile (rows of 33 words: the 8 channel rows a warp
+// writes, and the 32 row segments it reads back, fall in distinct banks); each thread then
+// writes 8 voxels of one channel row (16 B) of XcolT.  Rows k >= 27 cin are not touched.
+__global__ void __launch_bounds__(256) im2colT_kernel(const __nv_bfloat16* __restrict__ X, int ln, int cin,
+                                                      int M, int tiles, __nv_bfloat16* __restrict__ XcolT) {
+    __shared__ uint32_t tileW[32 * 33];
+    unsigned short* tileH = reinterpret_cast<unsigned short*>(tileW);
+    const int n = 1 << ln, mask = n - 1;
+    const int chunks = cin >> 5, tcs = 27 * chunks;
     const int t = threadIdx.x;
-    {
-        const int v = t >> 2, g = t & 3;  // voxel of the block, 8-channel group
-        const int64_t m = m0 + v;
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (m < M) {
-            const int x = (int)(m % n), y = (int)((m / n) % n), z = (int)((m / ((int64_t)n * n)) % n);
-            const int b = (int)(m / ((int64_t)n * n * n));
-            const int sz = z + kz - 1, sy = y + ky - 1, sx = x + kx - 1;
-            if ((unsigned)sz < (unsigned)n && (unsigned)sy < (unsigned)n && (unsigned)sx < (unsigned)n)
-                val = *reinterpret_cast<const uint4*>(X + vox(b, sz, sy, sx, n) * cin + c0 + g * 8);
-        }
-        *reinterpret_cast<uint4*>(&tile[v][g * 8]) = val;
-    }
-    __syncthreads();
-    {
-        const int j = t >> 3, sgm = t & 7;  // channel row of the block, 8-voxel segment
-        const int64_t m = m0 + sgm * 8;
-        if (m + 8 <= M) {
-            __align__(16) __nv_bfloat16 out[8];
+    const int v = t >> 2, g = t & 3;   // load phase: voxel of the tile, 8-channel group
+    const int c = t >> 3, sg = t & 7;  // store phase: channel row, 8-voxel segment
+    for (int it = blockIdx.x; it < tiles; it += gridDim.x) {
+        // the (tap, chunk) index runs fastest: the tiles in flight share their source voxels
+        const int vb = it / tcs, tc = it - vb * tcs;
+        const int tap = tc / chunks, c0 = (tc - tap * chunks) << 5;
+        const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
+        const int m0 = vb << 6;
+        {
+            const int m = m0 + v;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (m < M) {
+                const int sx = (m & mask) + kx - 1, sy = ((m >> ln) & mask) + ky - 1;
+                const int sz = ((m >> (2 * ln)) & mask) + kz - 1, b = m >> (3 * ln);
+                if ((unsigned)sz < (unsigned)n && (unsigned)sy < (unsigned)n && (unsigned)sx < (unsigned)n) {
+                    const int src = (((b << ln) + sz) << ln | sy) << ln | sx;
+                    val = *reinterpret_cast<const uint4*>(X + (int64_t)src * cin + c0 + g * 8);
+                }
+            }
+            const uint32_t w[4] = {val.x, val.y, val.z, val.w};
 #pragma unroll
-            for (int e = 0; e < 8; ++e) out[e] = tile[sgm * 8 + e][j];
-            *reinterpret_cast<uint4*>(XcolT + (int64_t)(tap * cin + c0 + j) * M + m) =
-                *reinterpret_cast<const uint4*>(out);
-        } else {
-            for (int e = 0; e < 8 && m + e < M; ++e) XcolT[(int64_t)(tap * cin + c0 + j) * M + m + e] = tile[sgm * 8 + e][j];
+            for (int e = 0; e < 8; ++e)
+                tileH[(g * 8 + e) * 66 + v] = (unsigned short)(w[e >> 1] >> ((e & 1) * 16));
         }
+        __syncthreads();
+        {
+            const int m = m0 + sg * 8;
+            if (m < M) {  // M is a multiple of 8: the segment is whole
+                const uint32_t* row = tileW + c * 33 + sg * 4;
+                *reinterpret_cast<uint4*>(XcolT + (int64_t)(tap * cin + c0 + c) * M + m) =
+                    make_uint4(row[0], row[1], row[2], row[3]);
+            }
+        }
+        __syncthreads();
     }
 }
 
-bool im2colT_supported(int cin, int64_t M) { return cin % 32 == 0 && M % 8 == 0; }
+bool im2colT_supported(int n, int cin, int64_t M) {
+    return cin % 32 == 0 && M % 8 == 0 && n >= 1 && (n & (n - 1)) == 0 && M < (int64_t(1) << 31) &&
+           (M + 63) / 64 * 27 * (cin / 32) < (int64_t(1) << 31);
+}
 
 cudaError_t im2colT(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_bfloat16* XcolT,
                     cudaStream_t st) {
     const int64_t M = (int64_t)B * n * n * n;
-    if (!im2colT_supported(cin, M) || Kp < 27 * cin || ((uintptr_t)X & 15) || ((uintptr_t)XcolT & 15))
+    if (!im2colT_supported(n, cin, M) || Kp < 27 * cin || ((uintptr_t)X & 15) || ((uintptr_t)XcolT & 15))
         return cudaErrorInvalidValue;
-    const int64_t gx = (M + 63) / 64;
-    if (gx > 2147483647LL) return cudaErrorInvalidValue;
-    im2colT_kernel<<<dim3((unsigned)gx, 27 * (cin / 32)), 256, 0, st>>>(X, B, n, cin, M, XcolT);
+    int ln = 0;
+    while ((1 << ln) < n) ++ln;
+    const int tiles = (int)((M + 63) / 64 * 27 * (cin / 32));
+    const unsigned grid = (unsigned)std::min(tiles, 152 * 8 * 4);
+    im2colT_kernel<<<grid, 256, 0, st>>>(X, ln, cin, (int)M, tiles, XcolT);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || Kp == 27 * cin) return e;
     // the padding rows 27 cin .. Kp - 1 read as zeros
@@ -187,17 +227,30 @@ cudaError_t bias_relu(const float* Y, const float* bias, int64_t M, int C, __nv_
 }
 
 // Gradient sums over rows are taken in a fixed order -- rows ascending within a thread,
-// then the threads of a block, then the blocks (sum_partials_kernel) -- so that training
-// gives the same result on every run.
+// then the threads of a block, then the blocks in a fixed tree (sum_partials_kernel) -- so
+// that training gives the same result on every run.
 
-// out[i] += sum_b part[b * ld + first + i] for i < count, blocks b in ascending order.
-__global__ void sum_partials_kernel(const float* __restrict__ part, int nblocks, int ld, int first,
-                                    int count, float* __restrict__ out) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-        float s = out[i];
-        for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * ld + first + i];
-        out[i] = s;
+// out[i] += sum over b of part[b ld + first + i], one block of 256 threads per i: thread t
+// adds the partials t, t + 256, ... in order, then the 256 sums are added pairwise in a
+// fixed tree (the same order on every run, independent of timing).
+__global__ void __launch_bounds__(256) sum_partials_kernel(const float* __restrict__ part, int nblocks, int ld,
+                                                           int first, float* __restrict__ out) {
+    __shared__ float red[256];
+    const int i = blockIdx.x, t = threadIdx.x;
+    float s = 0.f;
+    for (int b = t; b < nblocks; b += 256) s += part[(int64_t)b * ld + first + i];
+    red[t] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
     }
+    if (t == 0) out[i] += red[0];
+}
+
+static void sum_partials(const float* part, int nblocks, int ld, int first, int count, float* out,
+                         cudaStream_t st) {
+    sum_partials_kernel<<<count, 256, 0, st>>>(part, nblocks, ld, first, out);
 }
 
 static int64_t rows_per_block(int64_t M, int64_t at_least, int max_blocks) {
@@ -237,7 +290,7 @@ cudaError_t relu_bwd(const float* dA, const __nv_bfloat16* A, int64_t ldA, int a
     const int64_t rows = rows_per_block(M, 256 / C, kMaxPartialBlocks);
     const int nblocks = (int)((M + rows - 1) / rows);
     relu_bwd_kernel<<<nblocks, 256, 0, st>>>(dA, A, ldA, a_off, M, C, rows, dZ, part);
-    sum_partials_kernel<<<1, 256, 0, st>>>(part, nblocks, C, 0, C, db);
+    sum_partials(part, nblocks, C, 0, C, db, st);
     return cudaGetLastError();
 }
 
@@ -427,8 +480,8 @@ cudaError_t head_bwd(const float* dOut, const __nv_bfloat16* A, int64_t M, int C
     const int nblocks = (int)((M + rows - 1) / rows);
     const int E = 4 * C + 4;
     head_dW_kernel<<<nblocks, 256, 0, st>>>(dOut, A, M, C, rows, part);
-    sum_partials_kernel<<<1, 256, 0, st>>>(part, nblocks, E, 0, 4 * C, dW);
-    sum_partials_kernel<<<1, 32, 0, st>>>(part, nblocks, E, 4 * C, 4, db);
+    sum_partials(part, nblocks, E, 0, 4 * C, dW, st);
+    sum_partials(part, nblocks, E, 4 * C, 4, db, st);
     return cudaGetLastError();
 }
 
@@ -456,10 +509,20 @@ __global__ void mse_kernel(const float* __restrict__ out, const float* __restric
     }
 }
 
-__global__ void sum_loss_kernel(const double* __restrict__ part, int nblocks, double* __restrict__ loss) {
-    double s = *loss;
-    for (int b = 0; b < nblocks; ++b) s += part[b];
-    *loss = s;
+// *loss += the block partials, in the fixed order of sum_partials_kernel (FP64).
+__global__ void __launch_bounds__(256) sum_loss_kernel(const double* __restrict__ part, int nblocks,
+                                                       double* __restrict__ loss) {
+    __shared__ double red[256];
+    const int t = threadIdx.x;
+    double s = 0.0;
+    for (int b = t; b < nblocks; b += 256) s += part[b];
+    red[t] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) *loss += red[0];
 }
 
 cudaError_t mse(const float* out, const float* target, int64_t count, float* dOut, double* loss,
@@ -467,7 +530,7 @@ cudaError_t mse(const float* out, const float* target, int64_t count, float* dOu
     unsigned blocks = blocks_for(count, 256);
     if (blocks > (unsigned)kMaxPartialBlocks) blocks = kMaxPartialBlocks;
     mse_kernel<<<blocks, 256, 0, st>>>(out, target, count, dOut, part);
-    sum_loss_kernel<<<1, 1, 0, st>>>(part, (int)blocks, loss);
+    sum_loss_kernel<<<1, 256, 0, st>>>(part, (int)blocks, loss);
     return cudaGetLastError();
 }
 

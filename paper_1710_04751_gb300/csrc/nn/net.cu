@@ -242,7 +242,7 @@ int conv_bwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, const __nv_bfloat
     cudaStream_t st = N->stream;
     NET_CUDA(N, relu_bwd(dA, A, k.cout, 0, M, k.cout, N->dZ, k.gb, N->part, st));
     NET_CUDA(N, transpose(N->dZ, M, k.cout, k.cout, N->dZT, M, st));
-    if (im2colT_supported(k.cin, M)) {  // written transposed: no im2col matrix in between
+    if (im2colT_supported(n, k.cin, M)) {  // written transposed: no im2col matrix in between
         NET_CUDA(N, im2colT(X, B, n, k.cin, k.Kp, N->xcolT, st));
     } else {
         NET_CUDA(N, im2col(X, B, n, k.cin, k.Kp, N->xcol, st));

@@ -51,8 +51,8 @@ namespace nn {
 cudaError_t im2col(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_bfloat16* Xcol,
                    cudaStream_t st);
 // XcolT [Kp][M] = im2col(X) transposed (M = B n^3 voxels, row stride M), without the
-// intermediate matrix; cin a multiple of 32, M of 8; padding rows zeroed.
-bool im2colT_supported(int cin, int64_t M);
+// intermediate matrix; n a power of two, cin a multiple of 32, M of 8; padding rows zeroed.
+bool im2colT_supported(int n, int cin, int64_t M);
 cudaError_t im2colT(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_bfloat16* XcolT,
                     cudaStream_t st);
 cudaError_t transpose(const __nv_bfloat16* in, int64_t R, int64_t C, int64_t ld_in,
