@@ -69,33 +69,35 @@ __global__ void im2col1_kernel(const __nv_bfloat16* __restrict__ X, int B, int n
 }
 
 // cin a multiple of 4 (the network's 4-channel input layer): 4 channels (8 bytes) per thread.
-__global__ void im2col4_kernel(const __nv_bfloat16* __restrict__ X, int B, int n, int cin, int Kp,
+__global__ void im2col4_kernel(const __nv_bfloat16* __restrict__ X, int n, int cin, int Kp, int total,
                                __nv_bfloat16* __restrict__ Xcol) {
     const int kq = Kp / 4;
-    const int64_t total = (int64_t)B * n * n * n * kq;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = q / kq;
-        const int k = (int)(q - m * kq) * 4;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const int m = q / kq;
+        const int k = (q - m * kq) * 4;
         uint2 v = make_uint2(0, 0);
         if (k < 27 * cin) {
             const int tap = k / cin, ci = k - tap * cin;
             const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
-            const int x = (int)(m % n), y = (int)((m / n) % n), z = (int)((m / ((int64_t)n * n)) % n);
-            const int b = (int)(m / ((int64_t)n * n * n));
+            int r = m / n;
+            const int x = m - r * n;
+            const int y = r % n;
+            r /= n;
+            const int z = r % n, b = r / n;
             const int sz = z + kz - 1, sy = y + ky - 1, sx = x + kx - 1;
             if ((unsigned)sz < (unsigned)n && (unsigned)sy < (unsigned)n && (unsigned)sx < (unsigned)n)
-                v = *reinterpret_cast<const uint2*>(X + vox(b, sz, sy, sx, n) * cin + ci);
+                v = *reinterpret_cast<const uint2*>(X + (int64_t)(((b * n + sz) * n + sy) * n + sx) * cin + ci);
         }
-        *reinterpret_cast<uint2*>(Xcol + m * Kp + k) = v;
+        *reinterpret_cast<uint2*>(Xcol + (int64_t)m * Kp + k) = v;
     }
 }
 
 cudaError_t im2col(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_bfloat16* Xcol,
                    cudaStream_t st) {
     const int64_t M = (int64_t)B * n * n * n;
-    if (cin % 4 == 0 && cin % 8 != 0 && Kp % 4 == 0 && ((uintptr_t)X & 7) == 0 && ((uintptr_t)Xcol & 7) == 0)
-        im2col4_kernel<<<blocks_for(M * (Kp / 4), 256), 256, 0, st>>>(X, B, n, cin, Kp, Xcol);
+    if (cin % 4 == 0 && cin % 8 != 0 && Kp % 4 == 0 && ((uintptr_t)X & 7) == 0 && ((uintptr_t)Xcol & 7) == 0 &&
+        M * (Kp / 4) < (int64_t(1) << 31))
+        im2col4_kernel<<<blocks_for(M * (Kp / 4), 256), 256, 0, st>>>(X, n, cin, Kp, (int)(M * (Kp / 4)), Xcol);
     else if (cin % 8 == 0)
         im2col8_kernel<<<blocks_for(M * (Kp / 8), 256), 256, 0, st>>>(X, B, n, cin, Kp, Xcol);
     else
@@ -362,25 +364,146 @@ __global__ void upsample_bwd_kernel(const float* __restrict__ dU, int64_t ldU, i
     }
 }
 
+// The same four operations, 8 channels per thread (16-byte accesses) and 32-bit indices,
+// when C and the row strides are multiples of 8 and the totals fit in 31 bits.
+__device__ __forceinline__ void voxel_of(int v, int n, int& b, int& z, int& y, int& x) {
+    x = v % n;
+    int r = v / n;
+    y = r % n;
+    r /= n;
+    z = r % n;
+    b = r / n;
+}
+
+__global__ void avgpool8_kernel(const __nv_bfloat16* __restrict__ X, int n, int C8, int total,
+                                __nv_bfloat16* __restrict__ P) {
+    const int h = n / 2;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const int v = q / C8, cg = q - v * C8;
+        int b, z, y, x;
+        voxel_of(v, h, b, z, y, x);
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int src = ((b * n + 2 * z + (d >> 2)) * n + 2 * y + ((d >> 1) & 1)) * n + 2 * x + (d & 1);
+            const uint4 w = *reinterpret_cast<const uint4*>(X + ((int64_t)src * C8 + cg) * 8);
+            const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&w);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(h2[e]);
+                s[2 * e] += f.x;
+                s[2 * e + 1] += f.y;
+            }
+        }
+        uint4 o;
+        __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) o2[e] = __floats2bfloat162_rn(0.125f * s[2 * e], 0.125f * s[2 * e + 1]);
+        *reinterpret_cast<uint4*>(P + (int64_t)q * 8) = o;
+    }
+}
+
+__global__ void avgpool_bwd8_kernel(const float* __restrict__ dP, int n, int C8, int total,
+                                    float* __restrict__ dX, int accumulate) {
+    const int h = n / 2;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const int v = q / C8, cg = q - v * C8;
+        int b, z, y, x;
+        voxel_of(v, n, b, z, y, x);
+        const int src = ((b * h + z / 2) * h + y / 2) * h + x / 2;
+        const float4* g = reinterpret_cast<const float4*>(dP + ((int64_t)src * C8 + cg) * 8);
+        float4* d = reinterpret_cast<float4*>(dX + (int64_t)q * 8);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            float4 a = g[e];
+            a.x *= 0.125f, a.y *= 0.125f, a.z *= 0.125f, a.w *= 0.125f;
+            if (accumulate) {
+                const float4 o = d[e];
+                a.x += o.x, a.y += o.y, a.z += o.z, a.w += o.w;
+            }
+            d[e] = a;
+        }
+    }
+}
+
+__global__ void upsample8_kernel(const __nv_bfloat16* __restrict__ X, int n, int C8, int total,
+                                 __nv_bfloat16* __restrict__ U, int ldU, int c_off) {
+    const int h = n / 2;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const int v = q / C8, cg = q - v * C8;
+        int b, z, y, x;
+        voxel_of(v, n, b, z, y, x);
+        const int src = ((b * h + z / 2) * h + y / 2) * h + x / 2;
+        *reinterpret_cast<uint4*>(U + (int64_t)v * ldU + c_off + cg * 8) =
+            *reinterpret_cast<const uint4*>(X + ((int64_t)src * C8 + cg) * 8);
+    }
+}
+
+__global__ void upsample_bwd8_kernel(const float* __restrict__ dU, int ldU, int c_off, int n, int C8,
+                                     int total, float* __restrict__ dX) {
+    const int h = n / 2;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const int v = q / C8, cg = q - v * C8;
+        int b, z, y, x;
+        voxel_of(v, h, b, z, y, x);
+        float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int src = ((b * n + 2 * z + (d >> 2)) * n + 2 * y + ((d >> 1) & 1)) * n + 2 * x + (d & 1);
+            const float4* g = reinterpret_cast<const float4*>(dU + (int64_t)src * ldU + c_off + cg * 8);
+            const float4 a = g[0], c = g[1];
+            s0.x += a.x, s0.y += a.y, s0.z += a.z, s0.w += a.w;
+            s1.x += c.x, s1.y += c.y, s1.z += c.z, s1.w += c.w;
+        }
+        float4* d = reinterpret_cast<float4*>(dX + (int64_t)q * 8);
+        d[0] = s0;
+        d[1] = s1;
+    }
+}
+
+static bool vec8_ok(int64_t total, int C, int64_t ld, int c_off, const void* a, const void* b) {
+    return C % 8 == 0 && ld % 8 == 0 && c_off % 8 == 0 && total / 8 < (int64_t(1) << 31) &&
+           ((uintptr_t)a & 15) == 0 && ((uintptr_t)b & 15) == 0;
+}
+
 cudaError_t avgpool(const __nv_bfloat16* X, int B, int n, int C, __nv_bfloat16* P, cudaStream_t st) {
     const int64_t total = (int64_t)B * (n / 2) * (n / 2) * (n / 2) * C;
+    if (vec8_ok((int64_t)B * n * n * n * C, C, C, 0, X, P)) {
+        avgpool8_kernel<<<blocks_for(total / 8, 256), 256, 0, st>>>(X, n, C / 8, (int)(total / 8), P);
+        return cudaGetLastError();
+    }
     avgpool_kernel<<<blocks_for(total, 256), 256, 0, st>>>(X, B, n, C, P);
     return cudaGetLastError();
 }
 cudaError_t avgpool_bwd(const float* dP, int B, int n, int C, float* dX, int accumulate, cudaStream_t st) {
     const int64_t total = (int64_t)B * n * n * n * C;
+    if (vec8_ok(total, C, C, 0, dP, dX)) {
+        avgpool_bwd8_kernel<<<blocks_for(total / 8, 256), 256, 0, st>>>(dP, n, C / 8, (int)(total / 8), dX,
+                                                                         accumulate);
+        return cudaGetLastError();
+    }
     avgpool_bwd_kernel<<<blocks_for(total, 256), 256, 0, st>>>(dP, B, n, C, dX, accumulate);
     return cudaGetLastError();
 }
 cudaError_t upsample(const __nv_bfloat16* X, int B, int n, int C, __nv_bfloat16* U, int64_t ldU,
                      int c_off, cudaStream_t st) {
     const int64_t total = (int64_t)B * n * n * n * C;
+    if (vec8_ok(total, C, ldU, c_off, X, U) && (int64_t)B * n * n * n * ldU < (int64_t(1) << 31)) {
+        upsample8_kernel<<<blocks_for(total / 8, 256), 256, 0, st>>>(X, n, C / 8, (int)(total / 8), U, (int)ldU,
+                                                                      c_off);
+        return cudaGetLastError();
+    }
     upsample_kernel<<<blocks_for(total, 256), 256, 0, st>>>(X, B, n, C, U, ldU, c_off);
     return cudaGetLastError();
 }
 cudaError_t upsample_bwd(const float* dU, int64_t ldU, int c_off, int B, int n, int C, float* dX,
                          cudaStream_t st) {
     const int64_t total = (int64_t)B * (n / 2) * (n / 2) * (n / 2) * C;
+    if (vec8_ok((int64_t)B * n * n * n * C, C, ldU, c_off, dU, dX) && (int64_t)B * n * n * n * ldU < (int64_t(1) << 31)) {
+        upsample_bwd8_kernel<<<blocks_for(total / 8, 256), 256, 0, st>>>(dU, (int)ldU, c_off, n, C / 8,
+                                                                          (int)(total / 8), dX);
+        return cudaGetLastError();
+    }
     upsample_bwd_kernel<<<blocks_for(total, 256), 256, 0, st>>>(dU, ldU, c_off, B, n, C, dX);
     return cudaGetLastError();
 }
