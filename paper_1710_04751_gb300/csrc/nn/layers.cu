@@ -112,6 +112,9 @@ cudaError_t im2col(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_b
 // into a shared [32 channels][66] BF16 tile (rows of 33 words: the 8 channel rows a warp
 // writes, and the 32 row segments it reads back, fall in distinct banks); each thread then
 // writes 8 voxels of one channel row (16 B) of XcolT.  Rows k >= 27 cin are not touched.
+#ifndef LBM_IM2COLT_VOXELS_FASTEST
+#define LBM_IM2COLT_VOXELS_FASTEST 0
+#endif
 __global__ void __launch_bounds__(256) im2colT_kernel(const __nv_bfloat16* __restrict__ X, int ln, int cin,
                                                       int M, int tiles, __nv_bfloat16* __restrict__ XcolT) {
     __shared__ uint32_t tileW[32 * 33];
@@ -121,9 +124,15 @@ __global__ void __launch_bounds__(256) im2colT_kernel(const __nv_bfloat16* __res
     const int t = threadIdx.x;
     const int v = t >> 2, g = t & 3;   // load phase: voxel of the tile, 8-channel group
     const int c = t >> 3, sg = t & 7;  // store phase: channel row, 8-voxel segment
+    const int vblocks = (M + 63) >> 6;
     for (int it = blockIdx.x; it < tiles; it += gridDim.x) {
+#if LBM_IM2COLT_VOXELS_FASTEST
+        // the voxel block runs fastest: long runs of each XcolT row are written together
+        const int tc = it / vblocks, vb = it - tc * vblocks;
+#else
         // the (tap, chunk) index runs fastest: the tiles in flight share their source voxels
         const int vb = it / tcs, tc = it - vb * tcs;
+#endif
         const int tap = tc / chunks, c0 = (tc - tap * chunks) << 5;
         const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
         const int m0 = vb << 6;
