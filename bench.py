@@ -483,6 +483,26 @@ def net_variant():
         return {"M": M, "N": N, "K": K, "ms": round(best * 1e3, 4), "tflops": round(tf, 1),
                 "frac": round(tf / peak, 4)}
 
+    def wgrad_rate(B, n, cin, cout, splits, reps=10):
+        """The implicit weight gradient (lbm_nn_conv3d_wgrad_bf16), scratch allocated once."""
+        M = B * n ** 3
+        Kp = (27 * cin + 63) // 64 * 64
+        X = torch.randn((B, n ** 3, cin), device="cuda", generator=gen).to(torch.bfloat16)
+        dZT = (torch.randn((cout, M), device="cuda", generator=gen) / 64).to(torch.bfloat16)
+        dWT = torch.zeros((Kp, cout), device="cuda")
+        xt = torch.empty(3 * cin * M, dtype=torch.bfloat16, device="cuda")
+        ws = torch.empty(splits * Kp * cout, dtype=torch.float32, device="cuda")
+        L = net._lib()
+
+        def call():
+            net._check(L.lbm_nn_conv3d_wgrad_bf16(X.data_ptr(), B, n, cin, dZT.data_ptr(), cout, Kp, xt.data_ptr(),
+                                                  ws.data_ptr(), ws.numel(), splits, dWT.data_ptr(),
+                                                  net._stream(dWT)))
+        best = back_to_back(call, reps)
+        tf = 2.0 * M * 27 * cin * cout / best / 1e12
+        return {"M": 27 * cin, "N": cout, "K": M, "ms": round(best * 1e3, 4), "tflops": round(tf, 1),
+                "frac": round(tf / peak, 4)}
+
     def conv_rate(B, n, cin, cout, mode, reps=10):
         """The implicit-GEMM convolution (no im2col matrix): time, TFLOP/s and the bytes it
         must move at least (input and output once)."""
@@ -500,16 +520,15 @@ def net_variant():
                 "tflops": round(tf, 1), "frac": round(tf / peak, 4),
                 "min_bytes": nbytes, "GB_per_s_of_min_bytes": round(nbytes / best / 1e9, 1)}
 
-    M0 = 2 * 64 ** 3
     out = {
         "peak_tflops": peak, "peak_kind": kind,
         "gemm_large": gemm_rate(65536, 256, 8192, net.GEMM_F32),
         # the network's layer 9 at 64^3, batch 2 (96 -> 32 channels): the forward pass and
-        # the input gradient as implicit GEMMs, the weight gradient as a split-K GEMM over
-        # an im2col matrix
+        # the input gradient and the weight gradient as implicit GEMMs (the weight gradient
+        # split 64 ways over the voxels, its x-shifted transposes included)
         "conv_fwd_L9": conv_rate(2, 64, 96, 32, net.CONV_BIAS_RELU_BF16),
         "conv_dgrad_L9": conv_rate(2, 64, 32, 96, net.CONV_F32),
-        "conv_wgrad_L9": gemm_rate(2624, 32, M0, net.GEMM_F32_ADD, splits=64),
+        "conv_wgrad_L9": wgrad_rate(2, 64, 96, 32, 64),
     }
     for B in (2, 4):
         netw = net.Net(n=64, max_batch=B, seed=1)

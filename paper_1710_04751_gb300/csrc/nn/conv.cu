@@ -413,6 +413,162 @@ bool make_w_map(CUtensorMap* map, const void* W, int N, int K, long long ld, int
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// ---------------------------------------------------------------------------------
+// Weight gradient as an implicit GEMM: dW^T[r][co] += sum over voxels v of
+// X[v + shift(tap)][ci] dZ[v][co], r = tap cin + ci.  The A operand of the K block (64
+// consecutive voxels of one x-row, n >= 64) and M tile (128 rows = four (tap, 32-channel)
+// groups) is four 5D TMA boxes {64 x, 1, 1, 1, 32 channels} of the x-shifted transposes
+// XT[kx] [cin][B][n][n][n] at (x0, y0 + ky - 1, z0 + kz - 1, b0, ci0): the tap's x-shift is
+// in the choice of copy (a TMA box cannot start at an odd innermost coordinate), its y- and
+// z-shifts in the outer coordinates (zero fill beyond the grid).  Each box lands as 32 rows
+// of 64 K values (128 bytes, 128-byte swizzle), so the four make the canonical K-major
+// tile of the GEMM.  B is dZ^T [cout][voxels].  Split K over the voxels: split z stores its
+// partial tile in slice z of the workspace; the slices are added in order afterwards.
+// ---------------------------------------------------------------------------------
+constexpr int WG_STAGES = 4;
+
+template <int BN>
+struct WgradSmem {
+    static constexpr int A_BYTES = CBM * 64 * 2, B_BYTES = BN * 64 * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int BYTES = 1024 + WG_STAGES * STAGE + 256;
+    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+struct WgradArgs {
+    int rows;            // 27 cin (rows beyond it, up to the padded count, read as zeros)
+    int N;               // cout
+    int cin, ln;         // input channels, log2 of the grid edge
+    int kblocks;         // 64-voxel blocks in all (B n^3 / 64)
+    int kb_per_split;
+    int Mrows;           // rows of a workspace slice (the padded 27 cin)
+    float* ws;           // [splits][Mrows][N]
+    int* err;
+};
+
+struct XShiftMaps {
+    CUtensorMap x[3];    // XT[kx], kx = 0, 1, 2 (shift -1, 0, +1)
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    conv_wgrad_kernel(const __grid_constant__ XShiftMaps xm, const __grid_constant__ CUtensorMap tmB,
+                      WgradArgs args) {
+    using L = WgradSmem<BN>;
+    extern __shared__ uint8_t wg_smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(wg_smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + WG_STAGES * L::STAGE);
+    uint64_t* empty = full + WG_STAGES;
+    uint64_t* done = empty + WG_STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ volatile int failed;
+
+    if (*static_cast<volatile int*>(args.err) != 0) return;  // another CTA timed out
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * BN;
+    const int kb0 = blockIdx.z * args.kb_per_split;
+    const int nkb = min(args.kb_per_split, args.kblocks - kb0);
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int s = 0; s < WG_STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(done, 1);
+        mbar_fence_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, L::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0;
+    if (nkb > 0 && warp == 0 && lane == 0) {
+        const int ln = args.ln, mask = (1 << ln) - 1;
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % WG_STAGES;
+            const uint32_t ph = (uint32_t)(i / WG_STAGES) & 1u;
+            if (i >= WG_STAGES && !mbar_wait(empty + s, ph ^ 1u, args.err, 1, &failed)) {
+                failed = 1;
+                break;
+            }
+            if (failed) break;
+            uint8_t* a = smem + s * L::STAGE;
+            mbar_expect_tx(full + s, L::STAGE);
+            const int v0 = (kb0 + i) << 6;
+            const int x0 = v0 & mask, y0 = (v0 >> ln) & mask, z0 = (v0 >> (2 * ln)) & mask, b0 = v0 >> (3 * ln);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const int r = m0 + 32 * g;
+                int kx = 1, dy = 0, dz = 0, c0 = args.cin;  // padding rows: a box past the channels
+                if (r < args.rows) {
+                    const int tap = r / args.cin;
+                    c0 = r - tap * args.cin;
+                    kx = tap % 3;
+                    dy = (tap / 3) % 3 - 1;
+                    dz = tap / 9 - 1;
+                }
+                tma_load_5d(a + g * 4096, &xm.x[kx], full + s, x0, y0 + dy, z0 + dz, b0, c0);
+            }
+            tma_load_2d(a + L::A_BYTES, &tmB, full + s, v0, n0);
+            ++issued;
+        }
+    } else if (nkb > 0 && warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_bf16_f32(CBM, BN);
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % WG_STAGES;
+            const uint32_t ph = (uint32_t)(i / WG_STAGES) & 1u;
+            if (failed || !mbar_wait(full + s, ph, args.err, 2, &failed)) {
+                failed = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a = smem_u32(smem + s * L::STAGE), b = a + L::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_bf16(tmem, sdesc_k_sw128(a + kk * 32), sdesc_k_sw128(b + kk * 32), idesc,
+                         (i > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(empty + s);
+        }
+        mma_commit(done);  // also when stopped early: every issued MMA drains before dealloc
+    }
+    __syncwarp();
+    if (nkb > 0 && !mbar_wait(done, 0, args.err, 3)) failed = 1;
+    __syncthreads();
+    const bool ok = nkb > 0 && !failed;
+    if (warp == 0 && lane == 0 && failed) {  // let every started copy land
+        for (int i = max(0, issued - WG_STAGES); i < issued; ++i)
+            mbar_wait(full + (i % WG_STAGES), (uint32_t)(i / WG_STAGES) & 1u, args.err, 4);
+    }
+    tc_fence_after();
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        float* C = args.ws + ((int64_t)blockIdx.z * args.Mrows + row) * args.N;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            const int col0 = n0 + c;
+            if (row >= args.Mrows || col0 >= args.N) continue;
+            if (col0 + 16 <= args.N && (args.N % 4) == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    reinterpret_cast<float4*>(C + col0)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (col0 + j < args.N) C[col0 + j] = v[j];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, L::TMEM_COLS);
+}
+
 template <int BN, int BKC>
 cudaError_t launch_conv(const CUtensorMap& tx, const CUtensorMap& tw, const ConvArgs& a,
                         cudaStream_t st) {
@@ -468,6 +624,35 @@ cudaError_t launch_conv_bkc(const CUtensorMap& tx, const CUtensorMap& tw, const 
     case 128: return launch_conv<128, BKC>(tx, tw, a, st);
     default: return launch_conv<256, BKC>(tx, tw, a, st);
     }
+}
+
+// XT [cin][B][n][n][n] read in boxes {64 x, 1, 1, 1, 32 channels}, 128-byte swizzle.
+bool make_xt_map(CUtensorMap* map, const void* XT, int B, int n, int cin) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[5] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)B, (cuuint64_t)cin};
+    const cuuint64_t row = (cuuint64_t)n * 2;
+    const cuuint64_t strides[4] = {row, row * n, row * n * n, row * n * n * B};
+    const cuuint32_t box[5] = {64, 1, 1, 1, 32};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(XT), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_wgrad(const XShiftMaps& xm, const CUtensorMap& tb, const WgradArgs& a, int mtiles, int splits,
+                         cudaStream_t st) {
+    using L = WgradSmem<BN>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(conv_wgrad_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+    });
+    if (attr != cudaSuccess) return attr;
+    const dim3 grid(mtiles, (a.N + BN - 1) / BN, splits);
+    conv_wgrad_kernel<BN><<<grid, 128, L::BYTES, st>>>(xm, tb, a);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -529,6 +714,45 @@ cudaError_t conv_implicit(const __nv_bfloat16* X, int B, int n, int cin, const _
         return cudaErrorInvalidValue;
     ConvArgs a{B * n * n * n, cout, n, cin / bkc, bx, by, bz, mode, out, bias, err};
     return bkc == 64 ? launch_conv_bkc<64>(tx, tw, a, BN, st) : launch_conv_bkc<32>(tx, tw, a, BN, st);
+}
+
+bool conv_wgrad_implicit_supported(int B, int n, int cin, int cout) {
+    const int64_t M = (int64_t)B * n * n * n;
+    return n >= 64 && (n & (n - 1)) == 0 && cin % 32 == 0 && cout >= 1 && cout <= 256 && B >= 1 &&
+           3 * (int64_t)cin * M < (int64_t(1) << 40) && M < (int64_t(1) << 31);
+}
+
+cudaError_t conv_wgrad_implicit(const __nv_bfloat16* X, int B, int n, int cin, const __nv_bfloat16* dZT, int cout,
+                                int Kp, __nv_bfloat16* xt, float* ws, size_t ws_floats, int splits, float* dWT,
+                                int* err, cudaStream_t st) {
+    if (!conv_wgrad_implicit_supported(B, n, cin, cout) || Kp < 27 * cin || splits < 1 || ((uintptr_t)dZT & 15) ||
+        ((uintptr_t)xt & 15))
+        return cudaErrorInvalidValue;
+    const int64_t M = (int64_t)B * n * n * n;
+    const int kblocks = (int)(M / 64);
+    const int per = (kblocks + splits - 1) / splits;
+    const int used = (kblocks + per - 1) / per;
+    const int mtiles = (Kp + CBM - 1) / CBM;
+    if ((size_t)used * Kp * cout > ws_floats) return cudaErrorInvalidValue;
+    cudaError_t e = transpose_shift_x(X, B, n, cin, xt, st);
+    if (e != cudaSuccess) return e;
+    XShiftMaps xm;
+    for (int k = 0; k < 3; ++k)
+        if (!make_xt_map(&xm.x[k], xt + (int64_t)k * cin * M, B, n, cin)) return cudaErrorInvalidValue;
+    const int BN = cout <= 32 ? 32 : cout <= 64 ? 64 : cout <= 128 ? 128 : 256;
+    CUtensorMap tb;
+    if (!make_w_map(&tb, dZT, cout, (int)M, M, 64, BN)) return cudaErrorInvalidValue;
+    int ln = 0;
+    while ((1 << ln) < n) ++ln;
+    WgradArgs a{27 * cin, cout, cin, ln, kblocks, per, Kp, ws, err};
+    switch (BN) {
+    case 32: e = launch_wgrad<32>(xm, tb, a, mtiles, used, st); break;
+    case 64: e = launch_wgrad<64>(xm, tb, a, mtiles, used, st); break;
+    case 128: e = launch_wgrad<128>(xm, tb, a, mtiles, used, st); break;
+    default: e = launch_wgrad<256>(xm, tb, a, mtiles, used, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    return add_splits(ws, used, Kp, cout, cout, dWT, st);
 }
 
 }  // namespace nn

@@ -316,6 +316,13 @@ __global__ void add_splits_kernel(const float* __restrict__ ws, int splits, int 
     }
 }
 
+cudaError_t add_splits(const float* ws, int splits, int M, int N, long long ldc, float* C, cudaStream_t st) {
+    const int64_t total = (int64_t)M * N;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+    add_splits_kernel<<<blocks, 256, 0, st>>>(ws, splits, M, N, ldc, C);
+    return cudaGetLastError();
+}
+
 cudaError_t gemm_bf16_add_splitk(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B,
                                  long long ldb, float* C, long long ldc, int M, int N, int K,
                                  int splits, float* ws, size_t ws_floats, int* err, cudaStream_t st) {

@@ -186,6 +186,42 @@ cudaError_t im2colT(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_
     return cudaMemsetAsync(XcolT + (int64_t)27 * cin * M, 0, (size_t)(Kp - 27 * cin) * M * 2, st);
 }
 
+// ---- x-shifted transposes: XT[s][c][v] = X[v + (s - 1) e_x][c], zero across the x faces --
+// (s = 0, 1, 2; v = ((b n + z) n + y) n + x; n a power of two.)  32 voxels x 32 channels per
+// block and copy, through a padded shared tile.
+__global__ void transpose_shift_x_kernel(const __nv_bfloat16* __restrict__ X, int ln, int cin, int M,
+                                         __nv_bfloat16* __restrict__ XT) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int n = 1 << ln;
+    const int v0 = blockIdx.x * 32, c0 = blockIdx.y * 32, sh = (int)blockIdx.z - 1;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int v = v0 + i, c = c0 + threadIdx.x;
+        __nv_bfloat16 val = __float2bfloat16_rn(0.f);
+        if (v < M && c < cin) {
+            const int sx = (v & (n - 1)) + sh;
+            if ((unsigned)sx < (unsigned)n) val = X[(int64_t)(v + sh) * cin + c];
+        }
+        tile[i][threadIdx.x] = val;
+    }
+    __syncthreads();
+    __nv_bfloat16* out = XT + (int64_t)blockIdx.z * cin * M;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, v = v0 + threadIdx.x;
+        if (c < cin && v < M) out[(int64_t)c * M + v] = tile[threadIdx.x][i];
+    }
+}
+
+cudaError_t transpose_shift_x(const __nv_bfloat16* X, int B, int n, int cin, __nv_bfloat16* XT, cudaStream_t st) {
+    const int64_t M = (int64_t)B * n * n * n;
+    if (n < 1 || (n & (n - 1)) || M >= (int64_t(1) << 31) || cin < 1) return cudaErrorInvalidValue;
+    int ln = 0;
+    while ((1 << ln) < n) ++ln;
+    const dim3 grid((unsigned)((M + 31) / 32), (unsigned)((cin + 31) / 32), 3);
+    if (grid.x > 2147483647u || grid.y > 65535u) return cudaErrorInvalidValue;
+    transpose_shift_x_kernel<<<grid, dim3(32, 8), 0, st>>>(X, ln, cin, (int)M, XT);
+    return cudaGetLastError();
+}
+
 // ---- transpose of a BF16 matrix (32 x 32 tiles through shared memory) -----------------
 __global__ void transpose_kernel(const __nv_bfloat16* __restrict__ in, int64_t R, int64_t C,
                                  int64_t ld_in, __nv_bfloat16* __restrict__ out, int64_t ld_out) {

@@ -242,14 +242,20 @@ int conv_bwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, const __nv_bfloat
     cudaStream_t st = N->stream;
     NET_CUDA(N, relu_bwd(dA, A, k.cout, 0, M, k.cout, N->dZ, k.gb, N->part, st));
     NET_CUDA(N, transpose(N->dZ, M, k.cout, k.cout, N->dZT, M, st));
-    if (im2colT_supported(n, k.cin, M)) {  // written transposed: no im2col matrix in between
-        NET_CUDA(N, im2colT(X, B, n, k.cin, k.Kp, N->xcolT, st));
+    if (N->implicit && conv_wgrad_implicit_supported(B, n, k.cin, k.cout)) {
+        // no im2col matrix at all: A tiles straight from x-shifted transposes of X
+        NET_CUDA(N, conv_wgrad_implicit(X, B, n, k.cin, N->dZT, k.cout, k.Kp, N->xcolT, N->ws, N->ws_floats,
+                                        wgrad_splits(N, k, M), k.dWT, N->err, st));
     } else {
-        NET_CUDA(N, im2col(X, B, n, k.cin, k.Kp, N->xcol, st));
-        NET_CUDA(N, transpose(N->xcol, M, k.Kp, k.Kp, N->xcolT, M, st));
+        if (im2colT_supported(n, k.cin, M)) {  // written transposed: no im2col matrix in between
+            NET_CUDA(N, im2colT(X, B, n, k.cin, k.Kp, N->xcolT, st));
+        } else {
+            NET_CUDA(N, im2col(X, B, n, k.cin, k.Kp, N->xcol, st));
+            NET_CUDA(N, transpose(N->xcol, M, k.Kp, k.Kp, N->xcolT, M, st));
+        }
+        NET_CUDA(N, gemm_bf16_add_splitk(N->xcolT, M, N->dZT, M, k.dWT, k.cout, k.Kp, k.cout, (int)M,
+                                         wgrad_splits(N, k, M), N->ws, N->ws_floats, N->err, st));
     }
-    NET_CUDA(N, gemm_bf16_add_splitk(N->xcolT, M, N->dZT, M, k.dWT, k.cout, k.Kp, k.cout, (int)M,
-                                     wgrad_splits(N, k, M), N->ws, N->ws_floats, N->err, st));
     if (dX) {  // dX = im2col(dZ) Wf^T: the convolution of dZ with the mirrored weights
         if (N->implicit && conv_implicit_supported(n, k.cout, k.cin)) {
             NET_CUDA(N, conv_implicit(N->dZ, B, n, k.cout, k.Wf, k.Kpf, k.cin, nullptr, dX, CONV_F32,

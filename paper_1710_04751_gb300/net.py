@@ -13,7 +13,7 @@ EXPORTS = (
     "lbm_net_param_count", "lbm_net_encode", "lbm_net_get_params", "lbm_net_set_params",
     "lbm_net_forward", "lbm_net_gradients", "lbm_net_train_step", "lbm_net_last_error",
     "lbm_net_targets", "lbm_net_warm_start", "lbm_net_set_lr", "lbm_nn_gemm_timeout_probe",
-    "lbm_net_tensor", "lbm_nn_conv3d_bf16",
+    "lbm_net_tensor", "lbm_nn_conv3d_bf16", "lbm_nn_conv3d_wgrad_bf16",
 )
 CONV_BIAS_RELU_BF16, CONV_F32 = 0, 1
 
@@ -62,6 +62,7 @@ def _lib():
     L.lbm_nn_gemm_timeout_probe.argtypes = [vp]
     L.lbm_net_tensor.argtypes = [vp, i32, i32, vp, i64]
     L.lbm_nn_conv3d_bf16.argtypes = [vp, i32, i32, i32, vp, i64, i32, vp, vp, i32, vp]
+    L.lbm_nn_conv3d_wgrad_bf16.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, vp, i64, i32, vp, vp]
     _bound = True
     return L
 
@@ -97,6 +98,21 @@ def conv3d_bf16(X, n, W, out, mode=CONV_BIAS_RELU_BF16, bias=None):
     _check(_lib().lbm_nn_conv3d_bf16(X.data_ptr(), batch, n, cin, W.data_ptr(), W.stride(0), cout,
                                      None if bias is None else bias.data_ptr(), out.data_ptr(),
                                      int(mode), _stream(out)))
+
+
+def conv3d_wgrad_bf16(X, n, dZT, dWT, splits=8):
+    """dWT [Kp, cout] (float32) += the weight gradient of conv3d_bf16 as an implicit GEMM
+    (lbm_nn_conv3d_wgrad_bf16).  X: bfloat16 CUDA [batch, n^3, cin]; dZT: bfloat16
+    [cout, batch n^3] (the output gradient, transposed).  Scratch is allocated here."""
+    import torch
+    batch, vox, cin = X.shape
+    cout, Kp = dZT.shape[0], dWT.shape[0]
+    if vox != n ** 3 or dZT.shape[1] != batch * vox or dWT.shape[1] != cout:
+        raise ValueError("shapes: X [batch, n^3, cin], dZT [cout, batch n^3], dWT [Kp, cout]")
+    xt = torch.empty(3 * cin * batch * vox, dtype=torch.bfloat16, device=X.device)
+    ws = torch.empty(splits * Kp * cout, dtype=torch.float32, device=X.device)
+    _check(_lib().lbm_nn_conv3d_wgrad_bf16(X.data_ptr(), batch, n, cin, dZT.data_ptr(), cout, Kp, xt.data_ptr(),
+                                           ws.data_ptr(), ws.numel(), splits, dWT.data_ptr(), _stream(dWT)))
 
 
 def gemm_timeout_probe(stream=None):

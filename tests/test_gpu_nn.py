@@ -349,3 +349,48 @@ def test_implicit_convolution_against_fp64(B, n, cin, cout):
     gotb = outb.cpu().double()
     assert ((gotb - ref).abs() <= 2.0 ** -8 * (ref.abs() + e) + e).all()
 
+
+# ------------------------------------------------------------------------------------
+# The implicit weight gradient (lbm_nn_conv3d_wgrad_bf16) against the FP64 definition
+# dW^T[tap cin + ci][co] = sum over voxels v of X[v + shift(tap)][ci] dZ[v][co] (zero outside
+# the grid): every element within (K_split + splits) 2^-24 sum |x dz| -- the first-order bound
+# of FP32 summation of the split's K products and of the split partials -- after adding to
+# an initial 1 (it accumulates); the padding rows 27 cin .. Kp - 1 stay at 1.  Grids 64^3 and
+# 128^3 (the A tiles are 64-voxel x-row segments), one and two samples, cin 32 / 96,
+# cout 32 / 96 (a 128-wide tile over 96 columns) / 64, uneven splits.
+# ------------------------------------------------------------------------------------
+
+WGRAD_CASES = [(1, 64, 32, 32, 8), (2, 64, 96, 32, 5), (1, 64, 32, 96, 3), (1, 128, 32, 64, 16)]
+
+
+@pytest.mark.parametrize("B,n,cin,cout,splits", WGRAD_CASES,
+                         ids=[f"b{c[0]}-n{c[1]}-ci{c[2]}-co{c[3]}-s{c[4]}" for c in WGRAD_CASES])
+def test_implicit_weight_gradient_against_fp64(B, n, cin, cout, splits):
+    torch = torch_mod()
+    from paper_1710_04751_gb300 import net
+    g = torch.Generator().manual_seed(B * 7 + n + cin * 3 + cout)
+    M = B * n ** 3
+    X = torch.randn((B, n ** 3, cin), generator=g, dtype=torch.float64).to(torch.bfloat16)
+    dZ = (torch.randn((M, cout), generator=g, dtype=torch.float64) / 64).to(torch.bfloat16)
+    Kp = (27 * cin + 63) // 64 * 64
+    x = X.double().reshape(B, n, n, n, cin).numpy()
+    dz = dZ.double().numpy()
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (1, 1), (0, 0)))
+    ref = np.zeros((27 * cin, cout))
+    mag = np.zeros((27 * cin, cout))
+    for tap in range(27):
+        kz, ky, kx = tap // 9, (tap // 3) % 3, tap % 3
+        xs = xp[:, kz:kz + n, ky:ky + n, kx:kx + n, :].reshape(M, cin)
+        ref[tap * cin:(tap + 1) * cin] = xs.T @ dz
+        mag[tap * cin:(tap + 1) * cin] = np.abs(xs).T @ np.abs(dz)
+    kblocks = M // 64
+    per = -(-kblocks // splits)
+    # plus the FP32 rounding of 1 + sum (the accumulation test) and of the subtraction
+    bound = (per * 64 + splits) * 2.0 ** -24 * mag + 2.0 ** -23 * np.maximum(1.0, np.abs(ref)) + 1e-30
+    dWT = torch.ones((Kp, cout), dtype=torch.float32, device="cuda")
+    net.conv3d_wgrad_bf16(X.cuda(), n, dZ.t().contiguous().cuda(), dWT, splits=splits)
+    got = dWT.cpu().double().numpy() - 1.0
+    r = np.abs(got[:27 * cin] - ref) / bound
+    assert r.max() <= 1.0, (np.unravel_index(r.argmax(), r.shape), r.max())
+    assert (got[27 * cin:] == 0).all()
+
