@@ -488,14 +488,13 @@ def net_variant():
         M = B * n ** 3
         Kp = (27 * cin + 63) // 64 * 64
         X = torch.randn((B, n ** 3, cin), device="cuda", generator=gen).to(torch.bfloat16)
-        dZT = (torch.randn((cout, M), device="cuda", generator=gen) / 64).to(torch.bfloat16)
+        dZ = (torch.randn((M, cout), device="cuda", generator=gen) / 64).to(torch.bfloat16)
         dWT = torch.zeros((Kp, cout), device="cuda")
-        xt = torch.empty(3 * cin * M, dtype=torch.bfloat16, device="cuda")
         ws = torch.empty(splits * Kp * cout, dtype=torch.float32, device="cuda")
         L = net._lib()
 
         def call():
-            net._check(L.lbm_nn_conv3d_wgrad_bf16(X.data_ptr(), B, n, cin, dZT.data_ptr(), cout, Kp, xt.data_ptr(),
+            net._check(L.lbm_nn_conv3d_wgrad_bf16(X.data_ptr(), B, n, cin, dZ.data_ptr(), cout, Kp,
                                                   ws.data_ptr(), ws.numel(), splits, dWT.data_ptr(),
                                                   net._stream(dWT)))
         best = back_to_back(call, reps)

@@ -51,15 +51,17 @@ enum { LBM_CONV_BIAS_RELU_BF16 = 0, LBM_CONV_F32 = 1 };
 
 /* dWT[r][co] += sum over voxels v of X[v + shift(tap)][ci] dZ[v][co], r = tap cin + ci (the
  * weight gradient of lbm_nn_conv3d_bf16's convolution, transposed: [Kp][cout], row stride
- * cout; rows 27 cin .. Kp - 1 receive zeros), as an implicit GEMM: every A tile is four TMA
- * boxes of x-shifted transposes of X, built in `xt` (device scratch of 3 cin batch n^3 BF16
- * values), no im2col matrix.  dZT: device BF16 [cout][batch n^3], the output gradient
- * transposed.  The voxels are split `splits` ways; the splits' partial tiles go to `ws`
- * (device FP32 scratch of at least splits Kp cout values) and are added to dWT in split order,
- * so the result is the same on every run.  n a power of two >= 64, cin a multiple of 32,
- * cout <= 256, 16-byte aligned bases; else LBM_EINVAL.  Waits for `cuda_stream` (bounded);
- * LBM_ETIMEOUT as lbm_nn_gemm_bf16. */
-int lbm_nn_conv3d_wgrad_bf16(const void* X, int batch, int n, int cin, const void* dZT, int cout, int Kp, void* xt,
+ * cout; rows 27 cin .. Kp - 1 receive zeros), as an implicit GEMM that reads both operands
+ * in place: every A tile is four TMA boxes of X (32 channels x 64 voxels each, shifted by
+ * the tap, zero-filled outside the grid), every B tile boxes of dZ; no im2col matrix and no
+ * transpose.  X: device BF16 [batch][n][n][n][cin] as for lbm_nn_conv3d_bf16; dZ: device
+ * BF16 [batch n^3][cout], the output gradient.  The voxels are split `splits` ways; the
+ * splits' partial tiles go to `ws` (device FP32 scratch of at least splits Kp cout values)
+ * and are added to dWT in split order, so the result is the same on every run.  n a power
+ * of two in 2..256, cin a multiple of 32, cout a multiple of 8 in 8..256, 16-byte aligned
+ * bases; else LBM_EINVAL.  Waits for `cuda_stream` (bounded); LBM_ETIMEOUT as
+ * lbm_nn_gemm_bf16. */
+int lbm_nn_conv3d_wgrad_bf16(const void* X, int batch, int n, int cin, const void* dZ, int cout, int Kp,
                              float* ws, int64_t ws_floats, int splits, float* dWT, void* cuda_stream);
 int lbm_nn_conv3d_bf16(const void* X, int batch, int n, int cin, const void* W, int64_t ldw,
                        int cout, const float* bias, void* out, int mode, void* cuda_stream);

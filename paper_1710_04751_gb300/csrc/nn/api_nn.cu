@@ -86,21 +86,20 @@ extern "C" int lbm_nn_gemm_timeout_probe(void* cuda_stream) {
     return finish(st, err);  // LBM_ETIMEOUT when the bounded wait ran out as intended
 }
 
-extern "C" int lbm_nn_conv3d_wgrad_bf16(const void* X, int batch, int n, int cin, const void* dZT, int cout,
-                                        int Kp, void* xt, float* ws, int64_t ws_floats, int splits, float* dWT,
+extern "C" int lbm_nn_conv3d_wgrad_bf16(const void* X, int batch, int n, int cin, const void* dZ, int cout,
+                                        int Kp, float* ws, int64_t ws_floats, int splits, float* dWT,
                                         void* cuda_stream) {
-    if (!X || !dZT || !xt || !ws || !dWT) return record_error(nullptr, LBM_EINVAL, "NULL operand%s");
+    if (!X || !dZ || !ws || !dWT) return record_error(nullptr, LBM_EINVAL, "NULL operand%s");
     if (!nn::conv_wgrad_implicit_supported(batch, n, cin, cout) || Kp < 27 * cin || splits < 1 || ws_floats < 0)
         return record_error(nullptr, LBM_EINVAL,
-                            "implicit weight gradient needs n a power of two >= 64, cin a multiple of 32, "
-                            "1 <= cout <= 256, Kp >= 27 cin and splits >= 1%s");
+                            "implicit weight gradient needs n a power of two in 2..256, cin a multiple of 32, "
+                            "cout a multiple of 8 in 8..256, Kp >= 27 cin and splits >= 1%s");
     int* err = error_word();
     if (!err) return record_error(nullptr, LBM_ECUDA, "no CUDA device%s");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const cudaError_t e = nn::conv_wgrad_implicit(static_cast<const __nv_bfloat16*>(X), batch, n, cin,
-                                                  static_cast<const __nv_bfloat16*>(dZT), cout, Kp,
-                                                  static_cast<__nv_bfloat16*>(xt), ws, (size_t)ws_floats, splits,
-                                                  dWT, err, st);
+                                                  static_cast<const __nv_bfloat16*>(dZ), cout, Kp, ws,
+                                                  (size_t)ws_floats, splits, dWT, err, st);
     if (e == cudaErrorInvalidValue)
         return record_error(nullptr, LBM_EINVAL, "invalid weight-gradient shape, workspace or alignment%s");
     if (e != cudaSuccess)

@@ -414,16 +414,23 @@ bool make_w_map(CUtensorMap* map, const void* W, int N, int K, long long ld, int
 }
 
 // ---------------------------------------------------------------------------------
-// Weight gradient as an implicit GEMM: dW^T[r][co] += sum over voxels v of
-// X[v + shift(tap)][ci] dZ[v][co], r = tap cin + ci.  The A operand of the K block (64
-// consecutive voxels of one x-row, n >= 64) and M tile (128 rows = four (tap, 32-channel)
-// groups) is four 5D TMA boxes {64 x, 1, 1, 1, 32 channels} of the x-shifted transposes
-// XT[kx] [cin][B][n][n][n] at (x0, y0 + ky - 1, z0 + kz - 1, b0, ci0): the tap's x-shift is
-// in the choice of copy (a TMA box cannot start at an odd innermost coordinate), its y- and
-// z-shifts in the outer coordinates (zero fill beyond the grid).  Each box lands as 32 rows
-// of 64 K values (128 bytes, 128-byte swizzle), so the four make the canonical K-major
-// tile of the GEMM.  B is dZ^T [cout][voxels].  Split K over the voxels: split z stores its
-// partial tile in slice z of the workspace; the slices are added in order afterwards.
+// Weight gradient as an implicit GEMM on both operands in their natural layouts:
+//   dW^T[r][co] = sum over voxels v of X[v + shift(tap)][ci] dZ[v][co],  r = tap cin + ci,
+// a contraction over the voxels, so both operands are MN-major for the tensor core (the
+// row index r of A and the column index co of B are the contiguous ones in memory) and
+// neither X nor dZ is transposed or expanded.  K block = 64 consecutive voxels, the box
+// {bx, by, bz, bb} of the grid with bx by bz bb = 64 (x-row segments for n >= 64, whole
+// rows, planes or samples below).  A operand of the M tile (128 rows = four (tap,
+// 32-channel) groups): four 5D TMA boxes {32 channels, bx, by, bz, bb} of X at
+// (ci0, x0 + kx - 1, y0 + ky - 1, z0 + kz - 1, b0) with the 64-byte swizzle, each landing
+// as 64 K rows of 32 channels (64 bytes): the canonical MN-major tile, swizzle atoms of 8
+// K rows 512 bytes apart, the four channel groups 4 KB apart.  The tap's shift and the
+// zero padding come from the box coordinates and TMA's zero fill; the innermost
+// coordinate stays a multiple of 32 channels.  B operand: dZ [voxels][cout] in boxes
+// {BB channels, 64 voxels} (BB = 64 with the 128-byte swizzle, 32 with the 64-byte one
+// when BN = 32), BN / BB of them B_GROUP bytes apart.  Split K over the voxels: split z
+// stores its partial tile in slice z of the workspace; the slices are added in order
+// afterwards.
 // ---------------------------------------------------------------------------------
 constexpr int WG_STAGES = 4;
 
@@ -431,34 +438,36 @@ template <int BN>
 struct WgradSmem {
     static constexpr int A_BYTES = CBM * 64 * 2, B_BYTES = BN * 64 * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int BYTES = 1024 + WG_STAGES * STAGE + 256;
+    // 2 KB past the ring: the operand reads of the last stage stay inside the allocation
+    // under either assignment of the two descriptor strides
+    static constexpr int BYTES = 1024 + WG_STAGES * STAGE + 2048 + 256;
     static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+    static constexpr int BB = BN < 64 ? BN : 64;         // output channels per B box
+    static constexpr uint32_t B_GROUP = BB * 2 * 64;     // bytes of one B box (64 K rows)
+    static constexpr uint32_t B_ATOM = BB * 2 * 8;       // bytes of 8 K rows of it
+    static constexpr uint32_t B_LAYOUT = BB == 64 ? 2u : 4u;
 };
 
 struct WgradArgs {
     int rows;            // 27 cin (rows beyond it, up to the padded count, read as zeros)
     int N;               // cout
     int cin, ln;         // input channels, log2 of the grid edge
-    int kblocks;         // 64-voxel blocks in all (B n^3 / 64)
+    int kblocks;         // 64-voxel blocks in all (ceil(B n^3 / 64))
     int kb_per_split;
     int Mrows;           // rows of a workspace slice (the padded 27 cin)
     float* ws;           // [splits][Mrows][N]
     int* err;
 };
 
-struct XShiftMaps {
-    CUtensorMap x[3];    // XT[kx], kx = 0, 1, 2 (shift -1, 0, +1)
-};
-
 template <int BN>
 __global__ void __launch_bounds__(128, 1)
-    conv_wgrad_kernel(const __grid_constant__ XShiftMaps xm, const __grid_constant__ CUtensorMap tmB,
+    conv_wgrad_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB,
                       WgradArgs args) {
     using L = WgradSmem<BN>;
     extern __shared__ uint8_t wg_smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(wg_smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + WG_STAGES * L::STAGE);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + WG_STAGES * L::STAGE + 2048);
     uint64_t* empty = full + WG_STAGES;
     uint64_t* done = empty + WG_STAGES;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
@@ -488,6 +497,20 @@ __global__ void __launch_bounds__(128, 1)
     int issued = 0;
     if (nkb > 0 && warp == 0 && lane == 0) {
         const int ln = args.ln, mask = (1 << ln) - 1;
+        // the (tap, channel) groups of the M tile do not change along K
+        int gx[4], gy[4], gz[4], gc[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int r = m0 + 32 * g;
+            gx[g] = 0, gy[g] = 0, gz[g] = 0, gc[g] = args.cin;  // padding rows: past the channels
+            if (r < args.rows) {
+                const int tap = r / args.cin;
+                gc[g] = r - tap * args.cin;
+                gx[g] = tap % 3 - 1;
+                gy[g] = (tap / 3) % 3 - 1;
+                gz[g] = tap / 9 - 1;
+            }
+        }
         for (int i = 0; i < nkb; ++i) {
             const int s = i % WG_STAGES;
             const uint32_t ph = (uint32_t)(i / WG_STAGES) & 1u;
@@ -501,23 +524,17 @@ __global__ void __launch_bounds__(128, 1)
             const int v0 = (kb0 + i) << 6;
             const int x0 = v0 & mask, y0 = (v0 >> ln) & mask, z0 = (v0 >> (2 * ln)) & mask, b0 = v0 >> (3 * ln);
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                const int r = m0 + 32 * g;
-                int kx = 1, dy = 0, dz = 0, c0 = args.cin;  // padding rows: a box past the channels
-                if (r < args.rows) {
-                    const int tap = r / args.cin;
-                    c0 = r - tap * args.cin;
-                    kx = tap % 3;
-                    dy = (tap / 3) % 3 - 1;
-                    dz = tap / 9 - 1;
-                }
-                tma_load_5d(a + g * 4096, &xm.x[kx], full + s, x0, y0 + dy, z0 + dz, b0, c0);
-            }
-            tma_load_2d(a + L::A_BYTES, &tmB, full + s, v0, n0);
+            for (int g = 0; g < 4; ++g)
+                tma_load_5d(a + g * 4096, &tmX, full + s, gc[g], x0 + gx[g], y0 + gy[g], z0 + gz[g], b0);
+#pragma unroll
+            for (int j = 0; j < BN / L::BB; ++j)
+                tma_load_2d(a + L::A_BYTES + j * L::B_GROUP, &tmB, full + s, n0 + j * L::BB, v0);
             ++issued;
         }
     } else if (nkb > 0 && warp == 1 && lane == 0) {
-        const uint32_t idesc = idesc_bf16_f32(CBM, BN);
+        const uint32_t idesc = idesc_bf16_f32_mn(CBM, BN);
+        // with one B box the leading offset is never used: give it the K stride too
+        constexpr uint32_t b_lbo = BN / L::BB > 1 ? L::B_GROUP : L::B_ATOM;
         for (int i = 0; i < nkb; ++i) {
             const int s = i % WG_STAGES;
             const uint32_t ph = (uint32_t)(i / WG_STAGES) & 1u;
@@ -528,8 +545,9 @@ __global__ void __launch_bounds__(128, 1)
             tc_fence_after();
             const uint32_t a = smem_u32(smem + s * L::STAGE), b = a + L::A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                mma_bf16(tmem, sdesc_k_sw128(a + kk * 32), sdesc_k_sw128(b + kk * 32), idesc,
+            for (int kk = 0; kk < 4; ++kk)  // K = 16 per MMA: two atoms of 8 K rows
+                mma_bf16(tmem, sdesc_mn(a + kk * 1024, 4096, 512, 4),
+                         sdesc_mn(b + kk * 2 * L::B_ATOM, b_lbo, L::B_ATOM, L::B_LAYOUT), idesc,
                          (i > 0 || kk > 0) ? 1u : 0u);
             mma_commit(empty + s);
         }
@@ -626,22 +644,8 @@ cudaError_t launch_conv_bkc(const CUtensorMap& tx, const CUtensorMap& tw, const 
     }
 }
 
-// XT [cin][B][n][n][n] read in boxes {64 x, 1, 1, 1, 32 channels}, 128-byte swizzle.
-bool make_xt_map(CUtensorMap* map, const void* XT, int B, int n, int cin) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    const cuuint64_t dims[5] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)B, (cuuint64_t)cin};
-    const cuuint64_t row = (cuuint64_t)n * 2;
-    const cuuint64_t strides[4] = {row, row * n, row * n * n, row * n * n * B};
-    const cuuint32_t box[5] = {64, 1, 1, 1, 32};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(XT), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int BN>
-cudaError_t launch_wgrad(const XShiftMaps& xm, const CUtensorMap& tb, const WgradArgs& a, int mtiles, int splits,
+cudaError_t launch_wgrad(const CUtensorMap& tx, const CUtensorMap& tb, const WgradArgs& a, int mtiles, int splits,
                          cudaStream_t st) {
     using L = WgradSmem<BN>;
     static std::once_flag once;
@@ -651,7 +655,7 @@ cudaError_t launch_wgrad(const XShiftMaps& xm, const CUtensorMap& tb, const Wgra
     });
     if (attr != cudaSuccess) return attr;
     const dim3 grid(mtiles, (a.N + BN - 1) / BN, splits);
-    conv_wgrad_kernel<BN><<<grid, 128, L::BYTES, st>>>(xm, tb, a);
+    conv_wgrad_kernel<BN><<<grid, 128, L::BYTES, st>>>(tx, tb, a);
     return cudaGetLastError();
 }
 
@@ -718,38 +722,42 @@ cudaError_t conv_implicit(const __nv_bfloat16* X, int B, int n, int cin, const _
 
 bool conv_wgrad_implicit_supported(int B, int n, int cin, int cout) {
     const int64_t M = (int64_t)B * n * n * n;
-    return n >= 64 && (n & (n - 1)) == 0 && cin % 32 == 0 && cout >= 1 && cout <= 256 && B >= 1 &&
-           3 * (int64_t)cin * M < (int64_t(1) << 40) && M < (int64_t(1) << 31);
+    return n >= 2 && n <= 256 && (n & (n - 1)) == 0 && cin % 32 == 0 && cout >= 8 && cout <= 256 &&
+           cout % 8 == 0 && B >= 1 && M < (int64_t(1) << 31) - 64;
 }
 
-cudaError_t conv_wgrad_implicit(const __nv_bfloat16* X, int B, int n, int cin, const __nv_bfloat16* dZT, int cout,
-                                int Kp, __nv_bfloat16* xt, float* ws, size_t ws_floats, int splits, float* dWT,
-                                int* err, cudaStream_t st) {
-    if (!conv_wgrad_implicit_supported(B, n, cin, cout) || Kp < 27 * cin || splits < 1 || ((uintptr_t)dZT & 15) ||
-        ((uintptr_t)xt & 15))
+cudaError_t conv_wgrad_implicit(const __nv_bfloat16* X, int B, int n, int cin, const __nv_bfloat16* dZ, int cout,
+                                int Kp, float* ws, size_t ws_floats, int splits, float* dWT, int* err,
+                                cudaStream_t st) {
+    if (!conv_wgrad_implicit_supported(B, n, cin, cout) || Kp < 27 * cin || splits < 1 || ((uintptr_t)X & 15) ||
+        ((uintptr_t)dZ & 15))
         return cudaErrorInvalidValue;
     const int64_t M = (int64_t)B * n * n * n;
-    const int kblocks = (int)(M / 64);
+    const int kblocks = (int)((M + 63) / 64);
     const int per = (kblocks + splits - 1) / splits;
     const int used = (kblocks + per - 1) / per;
     const int mtiles = (Kp + CBM - 1) / CBM;
     if ((size_t)used * Kp * cout > ws_floats) return cudaErrorInvalidValue;
-    cudaError_t e = transpose_shift_x(X, B, n, cin, xt, st);
-    if (e != cudaSuccess) return e;
-    XShiftMaps xm;
-    for (int k = 0; k < 3; ++k)
-        if (!make_xt_map(&xm.x[k], xt + (int64_t)k * cin * M, B, n, cin)) return cudaErrorInvalidValue;
+    // the 64-voxel K block as a box of the grid: x-row segments, whole rows, planes, samples
+    const int bx = n < 64 ? n : 64;
+    const int by = 64 / bx < n ? 64 / bx : n;
+    const int bz = 64 / (bx * by) < n ? 64 / (bx * by) : n;
+    const int bb = 64 / (bx * by * bz);
+    if (bx * by * bz * bb != 64) return cudaErrorInvalidValue;
     const int BN = cout <= 32 ? 32 : cout <= 64 ? 64 : cout <= 128 ? 128 : 256;
-    CUtensorMap tb;
-    if (!make_w_map(&tb, dZT, cout, (int)M, M, 64, BN)) return cudaErrorInvalidValue;
+    CUtensorMap tx, tb;
+    if (!make_x_map(&tx, X, B, n, cin, 32, bx, by, bz, bb) ||
+        !make_w_map(&tb, dZ, (int)M, cout, cout, BN < 64 ? BN : 64, 64))
+        return cudaErrorInvalidValue;
     int ln = 0;
     while ((1 << ln) < n) ++ln;
     WgradArgs a{27 * cin, cout, cin, ln, kblocks, per, Kp, ws, err};
+    cudaError_t e;
     switch (BN) {
-    case 32: e = launch_wgrad<32>(xm, tb, a, mtiles, used, st); break;
-    case 64: e = launch_wgrad<64>(xm, tb, a, mtiles, used, st); break;
-    case 128: e = launch_wgrad<128>(xm, tb, a, mtiles, used, st); break;
-    default: e = launch_wgrad<256>(xm, tb, a, mtiles, used, st); break;
+    case 32: e = launch_wgrad<32>(tx, tb, a, mtiles, used, st); break;
+    case 64: e = launch_wgrad<64>(tx, tb, a, mtiles, used, st); break;
+    case 128: e = launch_wgrad<128>(tx, tb, a, mtiles, used, st); break;
+    default: e = launch_wgrad<256>(tx, tb, a, mtiles, used, st); break;
     }
     if (e != cudaSuccess) return e;
     return add_splits(ws, used, Kp, cout, cout, dWT, st);

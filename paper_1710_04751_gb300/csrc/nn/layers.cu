@@ -186,42 +186,6 @@ cudaError_t im2colT(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_
     return cudaMemsetAsync(XcolT + (int64_t)27 * cin * M, 0, (size_t)(Kp - 27 * cin) * M * 2, st);
 }
 
-// ---- x-shifted transposes: XT[s][c][v] = X[v + (s - 1) e_x][c], zero across the x faces --
-// (s = 0, 1, 2; v = ((b n + z) n + y) n + x; n a power of two.)  32 voxels x 32 channels per
-// block and copy, through a padded shared tile.
-__global__ void transpose_shift_x_kernel(const __nv_bfloat16* __restrict__ X, int ln, int cin, int M,
-                                         __nv_bfloat16* __restrict__ XT) {
-    __shared__ __nv_bfloat16 tile[32][34];
-    const int n = 1 << ln;
-    const int v0 = blockIdx.x * 32, c0 = blockIdx.y * 32, sh = (int)blockIdx.z - 1;
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int v = v0 + i, c = c0 + threadIdx.x;
-        __nv_bfloat16 val = __float2bfloat16_rn(0.f);
-        if (v < M && c < cin) {
-            const int sx = (v & (n - 1)) + sh;
-            if ((unsigned)sx < (unsigned)n) val = X[(int64_t)(v + sh) * cin + c];
-        }
-        tile[i][threadIdx.x] = val;
-    }
-    __syncthreads();
-    __nv_bfloat16* out = XT + (int64_t)blockIdx.z * cin * M;
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int c = c0 + i, v = v0 + threadIdx.x;
-        if (c < cin && v < M) out[(int64_t)c * M + v] = tile[threadIdx.x][i];
-    }
-}
-
-cudaError_t transpose_shift_x(const __nv_bfloat16* X, int B, int n, int cin, __nv_bfloat16* XT, cudaStream_t st) {
-    const int64_t M = (int64_t)B * n * n * n;
-    if (n < 1 || (n & (n - 1)) || M >= (int64_t(1) << 31) || cin < 1) return cudaErrorInvalidValue;
-    int ln = 0;
-    while ((1 << ln) < n) ++ln;
-    const dim3 grid((unsigned)((M + 31) / 32), (unsigned)((cin + 31) / 32), 3);
-    if (grid.x > 2147483647u || grid.y > 65535u) return cudaErrorInvalidValue;
-    transpose_shift_x_kernel<<<grid, dim3(32, 8), 0, st>>>(X, ln, cin, (int)M, XT);
-    return cudaGetLastError();
-}
-
 // ---- transpose of a BF16 matrix (32 x 32 tiles through shared memory) -----------------
 __global__ void transpose_kernel(const __nv_bfloat16* __restrict__ in, int64_t R, int64_t C,
                                  int64_t ld_in, __nv_bfloat16* __restrict__ out, int64_t ld_out) {
@@ -331,9 +295,62 @@ __global__ void relu_bwd_kernel(const float* __restrict__ dA, const __nv_bfloat1
     }
 }
 
+// The same with 8 channels per thread (16-byte loads of A and dZ, two 16-byte loads of dA):
+// thread t takes the channel group g = t % G (G = C / 8) and every R-th row (R = 256 / G
+// lanes); the per-channel sums of the lanes are then added in lane order.
+__global__ void relu_bwd8_kernel(const float* __restrict__ dA, const __nv_bfloat16* __restrict__ A,
+                                 int64_t ldA, int a_off, int M, int C, int rows,
+                                 __nv_bfloat16* __restrict__ dZ, float* __restrict__ part) {
+    __shared__ float acc[256][9];
+    const int G = C >> 3, R = 256 / G;
+    const int g = threadIdx.x % G, r = threadIdx.x / G;
+    const int m0 = blockIdx.x * rows, m1 = min(m0 + rows, M);
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (r < R) {
+#pragma unroll 2
+        for (int m = m0 + r; m < m1; m += R) {
+            const uint4 a = *reinterpret_cast<const uint4*>(A + (int64_t)m * ldA + a_off + 8 * g);
+            const float4 d0 = *reinterpret_cast<const float4*>(dA + (int64_t)m * C + 8 * g);
+            const float4 d1 = *reinterpret_cast<const float4*>(dA + (int64_t)m * C + 8 * g + 4);
+            const __nv_bfloat162* ah = reinterpret_cast<const __nv_bfloat162*>(&a);
+            const float d[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+            uint4 o;
+            uint32_t* ow = reinterpret_cast<uint32_t*>(&o);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 af = __bfloat1622float2(ah[j]);
+                const float g0 = af.x > 0.f ? d[2 * j] : 0.f, g1 = af.y > 0.f ? d[2 * j + 1] : 0.f;
+                const __nv_bfloat162 q = __floats2bfloat162_rn(g0, g1);
+                ow[j] = *reinterpret_cast<const uint32_t*>(&q);
+                s[2 * j] += g0;
+                s[2 * j + 1] += g1;
+            }
+            *reinterpret_cast<uint4*>(dZ + (int64_t)m * C + 8 * g) = o;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[threadIdx.x][j] = s[j];
+    __syncthreads();
+    if (threadIdx.x < C) {
+        const int gc = threadIdx.x >> 3, j = threadIdx.x & 7;
+        float t = 0.f;
+        for (int l = 0; l < R; ++l) t += acc[l * G + gc][j];
+        part[(int64_t)blockIdx.x * C + threadIdx.x] = t;
+    }
+}
+
 cudaError_t relu_bwd(const float* dA, const __nv_bfloat16* A, int64_t ldA, int a_off, int64_t M,
                      int C, __nv_bfloat16* dZ, float* db, float* part, cudaStream_t st) {
     if (C < 1 || C > 256 || M < 1) return cudaErrorInvalidValue;
+    const bool vec = C % 8 == 0 && ldA % 8 == 0 && a_off % 8 == 0 && ((uintptr_t)A & 15) == 0 &&
+                     ((uintptr_t)dA & 15) == 0 && ((uintptr_t)dZ & 15) == 0 && M < (int64_t(1) << 31) - 65536;
+    if (vec) {
+        const int64_t rows = rows_per_block(M, 256 / (C / 8), kMaxPartialBlocks);
+        const int nblocks = (int)((M + rows - 1) / rows);
+        relu_bwd8_kernel<<<nblocks, 256, 0, st>>>(dA, A, ldA, a_off, (int)M, C, (int)rows, dZ, part);
+        sum_partials(part, nblocks, C, 0, C, db, st);
+        return cudaGetLastError();
+    }
     const int64_t rows = rows_per_block(M, 256 / C, kMaxPartialBlocks);
     const int nblocks = (int)((M + rows - 1) / rows);
     relu_bwd_kernel<<<nblocks, 256, 0, st>>>(dA, A, ldA, a_off, M, C, rows, dZ, part);
@@ -574,13 +591,46 @@ __global__ void slice_grad_kernel(const float* __restrict__ dD, int64_t ldD, int
         dS[q] = accumulate ? dS[q] + g : g;
     }
 }
+// 16-byte forms: 8 BF16 channels, 4 FP32 channels per thread (G groups per row, 32-bit indices).
+__global__ void copy_channels8_kernel(const __nv_bfloat16* __restrict__ S, int total, int G,
+                                      __nv_bfloat16* __restrict__ D, int ldD, int c_off) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const int m = q / G, g = q - m * G;
+        *reinterpret_cast<uint4*>(D + (int64_t)m * ldD + c_off + 8 * g) = reinterpret_cast<const uint4*>(S)[q];
+    }
+}
+__global__ void slice_grad4_kernel(const float* __restrict__ dD, int ldD, int c_off, int total, int G,
+                                   float* __restrict__ dS, int accumulate) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const int m = q / G, g = q - m * G;
+        float4 v = *reinterpret_cast<const float4*>(dD + (int64_t)m * ldD + c_off + 4 * g);
+        if (accumulate) {
+            const float4 o = reinterpret_cast<const float4*>(dS)[q];
+            v = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+        }
+        reinterpret_cast<float4*>(dS)[q] = v;
+    }
+}
 cudaError_t copy_channels(const __nv_bfloat16* S, int64_t M, int C, __nv_bfloat16* D, int64_t ldD,
                           int c_off, cudaStream_t st) {
+    if (C % 8 == 0 && ldD % 8 == 0 && c_off % 8 == 0 && ((uintptr_t)S & 15) == 0 && ((uintptr_t)D & 15) == 0 &&
+        M * (C / 8) < (int64_t(1) << 30) && ldD < (int64_t(1) << 31)) {
+        const int total = (int)(M * (C / 8));
+        copy_channels8_kernel<<<blocks_for(total, 256), 256, 0, st>>>(S, total, C / 8, D, (int)ldD, c_off);
+        return cudaGetLastError();
+    }
     copy_channels_kernel<<<blocks_for(M * C, 256), 256, 0, st>>>(S, M, C, D, ldD, c_off);
     return cudaGetLastError();
 }
 cudaError_t slice_grad(const float* dD, int64_t ldD, int c_off, int64_t M, int C, float* dS,
                        int accumulate, cudaStream_t st) {
+    if (C % 4 == 0 && ldD % 4 == 0 && c_off % 4 == 0 && ((uintptr_t)dD & 15) == 0 && ((uintptr_t)dS & 15) == 0 &&
+        M * (C / 4) < (int64_t(1) << 30) && ldD < (int64_t(1) << 31)) {
+        const int total = (int)(M * (C / 4));
+        slice_grad4_kernel<<<blocks_for(total, 256), 256, 0, st>>>(dD, (int)ldD, c_off, total, C / 4, dS,
+                                                                   accumulate);
+        return cudaGetLastError();
+    }
     slice_grad_kernel<<<blocks_for(M * C, 256), 256, 0, st>>>(dD, ldD, c_off, M, C, dS, accumulate);
     return cudaGetLastError();
 }
@@ -638,9 +688,92 @@ cudaError_t head_fwd(const __nv_bfloat16* A, int64_t M, int C, const float* W, c
     head_kernel<<<blocks_for(M, 256), 256, 0, st>>>(A, M, C, W, b, out);
     return cudaGetLastError();
 }
+// The same 4 channels per thread: G = C / 4 threads per row, one 16-byte store each.
+__global__ void head_dA4_kernel(const float* __restrict__ dOut, int total, int G,
+                                const float* __restrict__ W, float* __restrict__ dA) {
+    __shared__ float w[4 * 64];
+    const int C = 4 * G;
+    for (int i = threadIdx.x; i < 4 * C; i += blockDim.x) w[i] = W[i];
+    __syncthreads();
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const int m = q / G, c = 4 * (q - m * G);
+        const float4 g = reinterpret_cast<const float4*>(dOut)[m];
+        float4 o;
+        o.x = g.x * w[c] + g.y * w[C + c] + g.z * w[2 * C + c] + g.w * w[3 * C + c];
+        o.y = g.x * w[c + 1] + g.y * w[C + c + 1] + g.z * w[2 * C + c + 1] + g.w * w[3 * C + c + 1];
+        o.z = g.x * w[c + 2] + g.y * w[C + c + 2] + g.z * w[2 * C + c + 2] + g.w * w[3 * C + c + 2];
+        o.w = g.x * w[c + 3] + g.y * w[C + c + 3] + g.z * w[2 * C + c + 3] + g.w * w[3 * C + c + 3];
+        reinterpret_cast<float4*>(dA)[q] = o;
+    }
+}
+
+// The head's weight and bias gradients with 8 channels per thread: thread t takes the
+// channel group g = t % G (G = C / 8) and every R-th row of the block (R = 256 / G lanes),
+// keeping 32 sums dOut[m][j] A[m][8 g + i] (and, in group 0, the 4 sums of dOut[m][j]);
+// the lanes are then added in lane order into the same per-block entries as head_dW_kernel.
+__global__ void head_dW8_kernel(const float* __restrict__ dOut, const __nv_bfloat16* __restrict__ A,
+                                int M, int C, int rows, float* __restrict__ part) {
+    __shared__ float acc[256][37];
+    const int G = C >> 3, R = 256 / G;
+    const int g = threadIdx.x % G, r = threadIdx.x / G;
+    const int m0 = blockIdx.x * rows, m1 = min(m0 + rows, M);
+    float s[36];
+#pragma unroll
+    for (int i = 0; i < 36; ++i) s[i] = 0.f;
+    if (r < R) {
+        for (int m = m0 + r; m < m1; m += R) {
+            const float4 d = reinterpret_cast<const float4*>(dOut)[m];
+            const uint4 a = *reinterpret_cast<const uint4*>(A + (int64_t)m * C + 8 * g);
+            const __nv_bfloat162* ah = reinterpret_cast<const __nv_bfloat162*>(&a);
+            const float dj[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 af = __bfloat1622float2(ah[k]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    s[j * 8 + 2 * k] += dj[j] * af.x;
+                    s[j * 8 + 2 * k + 1] += dj[j] * af.y;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s[32 + j] += dj[j];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 36; ++i) acc[threadIdx.x][i] = s[i];
+    __syncthreads();
+    const int E = 4 * C + 4;
+    for (int i = threadIdx.x; i < E; i += blockDim.x) {
+        int gi, slot;
+        if (i < 4 * C) {
+            const int j = i / C, c = i - j * C;
+            gi = c >> 3;
+            slot = j * 8 + (c & 7);
+        } else {
+            gi = 0;
+            slot = 32 + (i - 4 * C);
+        }
+        float t = 0.f;
+        for (int l = 0; l < R; ++l) t += acc[l * G + gi][slot];
+        part[(int64_t)blockIdx.x * E + i] = t;
+    }
+}
+
 cudaError_t head_bwd(const float* dOut, const __nv_bfloat16* A, int64_t M, int C, const float* W,
                      float* dA, float* dW, float* db, float* part, cudaStream_t st) {
     if (C < 1 || C > 64 || M < 1) return cudaErrorInvalidValue;
+    if (C % 8 == 0 && M * (C / 4) < (int64_t(1) << 30) && ((uintptr_t)dOut & 15) == 0 && ((uintptr_t)A & 15) == 0 &&
+        ((uintptr_t)dA & 15) == 0) {
+        const int total = (int)(M * (C / 4));
+        head_dA4_kernel<<<blocks_for(total, 256), 256, 0, st>>>(dOut, total, C / 4, W, dA);
+        const int64_t rows = rows_per_block(M, 256 / (C / 8), kMaxPartialBlocks);
+        const int nblocks = (int)((M + rows - 1) / rows);
+        const int E = 4 * C + 4;
+        head_dW8_kernel<<<nblocks, 256, 0, st>>>(dOut, A, (int)M, C, (int)rows, part);
+        sum_partials(part, nblocks, E, 0, 4 * C, dW, st);
+        sum_partials(part, nblocks, E, 4 * C, 4, db, st);
+        return cudaGetLastError();
+    }
     unsigned blocks = blocks_for(M, 256);
     if (blocks > 2048) blocks = 2048;
     head_dA_kernel<<<blocks, 256, 0, st>>>(dOut, M, C, W, dA);
@@ -725,11 +858,12 @@ cudaError_t adam(float* p, const float* g, float* m, float* v, int64_t n, float 
 }
 
 // ---- weights -----------------------------------------------------------------------------------
-// W [cout][27 cin] FP32 -> Wb [cout][Kp] BF16 (zero K padding), the forward operand, and
+// W [cout][27 cin] FP32 -> Wb [cout][Kp] BF16 with K index tap * cs + ci for an input stored
+// with cs >= cin channels (zero for ci >= cin and in the K padding), the forward operand, and
 // Wf [cin][Kpf] BF16 with Wf[ci][t * cout + co] = W[co][(26 - t) * cin + ci]: the weights of
 // the convolution that maps the output gradient to the input gradient (every tap
 // mirrored, input and output channels exchanged; zero padding to Kpf).
-__global__ void pack_weights_kernel(const float* __restrict__ W, int cin, int cout, int Kp,
+__global__ void pack_weights_kernel(const float* __restrict__ W, int cin, int cs, int cout, int Kp,
                                     int Kpf, __nv_bfloat16* __restrict__ Wb,
                                     __nv_bfloat16* __restrict__ Wf) {
     const int K27 = 27 * cin;
@@ -738,7 +872,8 @@ __global__ void pack_weights_kernel(const float* __restrict__ W, int cin, int co
          q += (int64_t)gridDim.x * blockDim.x) {
         if (q < n1) {
             const int co = (int)(q / Kp), k = (int)(q % Kp);
-            Wb[q] = __float2bfloat16_rn(k < K27 ? W[(int64_t)co * K27 + k] : 0.f);
+            const int tap = k / cs, ci = k - tap * cs;
+            Wb[q] = __float2bfloat16_rn(tap < 27 && ci < cin ? W[(int64_t)co * K27 + tap * cin + ci] : 0.f);
         } else if (Wf) {
             const int64_t r = q - n1;
             const int ci = (int)(r / Kpf), k = (int)(r % Kpf);
@@ -751,33 +886,37 @@ __global__ void pack_weights_kernel(const float* __restrict__ W, int cin, int co
         }
     }
 }
-cudaError_t pack_weights(const float* W, int cin, int cout, int Kp, int Kpf, __nv_bfloat16* Wb,
+cudaError_t pack_weights(const float* W, int cin, int cs, int cout, int Kp, int Kpf, __nv_bfloat16* Wb,
                          __nv_bfloat16* Wf, cudaStream_t st) {
+    if (cs < cin || Kp < 27 * cs) return cudaErrorInvalidValue;
     const int64_t total = (int64_t)cout * Kp + (int64_t)cin * Kpf;
-    pack_weights_kernel<<<blocks_for(total, 256), 256, 0, st>>>(W, cin, cout, Kp, Kpf, Wb, Wf);
+    pack_weights_kernel<<<blocks_for(total, 256), 256, 0, st>>>(W, cin, cs, cout, Kp, Kpf, Wb, Wf);
     return cudaGetLastError();
 }
 
-// dWT [Kp][cout] -> gW [cout][K27]
-__global__ void unpack_grad_kernel(const float* __restrict__ dWT, int cout, int K27,
+// dWT [Kp][cout] (K index tap * cs + ci) -> gW [cout][27 cin]
+__global__ void unpack_grad_kernel(const float* __restrict__ dWT, int cout, int cin, int cs,
                                    float* __restrict__ gW) {
+    const int K27 = 27 * cin;
     const int64_t total = (int64_t)cout * K27;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int co = (int)(q / K27), k = (int)(q % K27);
-        gW[q] = dWT[(int64_t)k * cout + co];
+        const int tap = k / cin, ci = k - tap * cin;
+        gW[q] = dWT[(int64_t)(tap * cs + ci) * cout + co];
     }
 }
-cudaError_t unpack_grad(const float* dWT, int cout, int K27, float* gW, cudaStream_t st) {
-    unpack_grad_kernel<<<blocks_for((int64_t)cout * K27, 256), 256, 0, st>>>(dWT, cout, K27, gW);
+cudaError_t unpack_grad(const float* dWT, int cout, int cin, int cs, float* gW, cudaStream_t st) {
+    unpack_grad_kernel<<<blocks_for((int64_t)cout * 27 * cin, 256), 256, 0, st>>>(dWT, cout, cin, cs, gW);
     return cudaGetLastError();
 }
 
 // ---- input features ----------------------------------------------------------------------------
 // channel 0: distance to the nearest wall / n (half-way walls: node i is i + 1/2 from the
 // low wall); 1: heated-face mask (+1 on the hot layer x = n-1, -1 on the cold layer x = 0);
-// 2, 3: the sample's normalised log10 Ra and log10 Pr.
-__global__ void features_kernel(int B, int n, const float* __restrict__ scalars,
+// 2, 3: the sample's normalised log10 Ra and log10 Pr; channels 4 .. ldx - 1 zero (the
+// stored row is padded so that the first convolution reads it like any other layer's input).
+__global__ void features_kernel(int B, int n, const float* __restrict__ scalars, int ldx,
                                 __nv_bfloat16* __restrict__ X) {
     const int64_t total = (int64_t)B * n * n * n;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total;
@@ -788,14 +927,16 @@ __global__ void features_kernel(int B, int n, const float* __restrict__ scalars,
         d = fminf(d, fminf(y + 0.5f, n - 0.5f - y));
         d = fminf(d, fminf(z + 0.5f, n - 0.5f - z));
         const float mask = x == n - 1 ? 1.f : (x == 0 ? -1.f : 0.f);
-        X[v * 4 + 0] = __float2bfloat16_rn(d / n);
-        X[v * 4 + 1] = __float2bfloat16_rn(n == 1 ? 0.f : mask);
-        X[v * 4 + 2] = __float2bfloat16_rn(scalars[2 * b]);
-        X[v * 4 + 3] = __float2bfloat16_rn(scalars[2 * b + 1]);
+        const __nv_bfloat162 f01 = __floats2bfloat162_rn(d / n, n == 1 ? 0.f : mask);
+        const __nv_bfloat162 f23 = __floats2bfloat162_rn(scalars[2 * b], scalars[2 * b + 1]);
+        uint4* row = reinterpret_cast<uint4*>(X + v * ldx);
+        row[0] = make_uint4(*reinterpret_cast<const uint32_t*>(&f01), *reinterpret_cast<const uint32_t*>(&f23), 0u, 0u);
+        for (int j = 1; j < ldx / 8; ++j) row[j] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
-cudaError_t features(int B, int n, const float* scalars, __nv_bfloat16* X, cudaStream_t st) {
-    features_kernel<<<blocks_for((int64_t)B * n * n * n, 256), 256, 0, st>>>(B, n, scalars, X);
+cudaError_t features(int B, int n, const float* scalars, __nv_bfloat16* X, int ldx, cudaStream_t st) {
+    if (ldx < 8 || ldx % 8 || ((uintptr_t)X & 15)) return cudaErrorInvalidValue;
+    features_kernel<<<blocks_for((int64_t)B * n * n * n, 256), 256, 0, st>>>(B, n, scalars, ldx, X);
     return cudaGetLastError();
 }
 

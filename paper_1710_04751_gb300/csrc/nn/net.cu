@@ -10,10 +10,13 @@
 //
 // every conv 3x3x3 with zero padding, bias and ReLU; pool = 2x average, up = 2x nearest.
 // Inputs: 4 channels (wall distance, heated-face mask, normalised log10 Ra and log10 Pr);
-// outputs: (u_x, u_y, u_z) / U0 and 2 T.  Each convolution is im2col + a tensor-core GEMM:
-// forward Y = Xcol W^T; weight gradient dW^T = Xcol^T dZ as a split-K GEMM; input
-// gradient dX = im2col(dZ) Wf^T, the convolution of the output gradient with the
-// mirrored, channel-exchanged weights Wf.  FP32 master weights, Adam, BF16 operand copies.
+// outputs: (u_x, u_y, u_z) / U0 and 2 T.  Each convolution is a tensor-core GEMM over
+// im2col(X), taken implicitly (conv.cu: the operand tiles are TMA boxes of the activations,
+// no im2col matrix): forward Y = Xcol W^T; weight gradient dW^T = Xcol^T dZ, split over the
+// voxels; input gradient dX = im2col(dZ) Wf^T, the convolution of the output gradient with
+// the mirrored, channel-exchanged weights Wf.  Shapes the implicit kernels do not take fall
+// back to an explicit im2col matrix and the GEMM of gemm.cu.  FP32 master weights, Adam,
+// BF16 operand copies.
 #include <math.h>
 #include <string.h>
 
@@ -31,9 +34,13 @@ using namespace lbm::nn;
 namespace {
 
 constexpr int kLayers = 11;
+// The 4 input channels are stored in rows of 32 (the rest zero), so that the first
+// convolution reads its input like every other layer: implicit GEMMs with 32-channel boxes.
+constexpr int kX0 = 32;
 
 struct Conv {
     int cin, cout, level, K27, Kp, Kpf;  // Kpf: padded 27 cout (input-gradient GEMM)
+    int cs;                              // channels of the stored input (cin, kX0 for layer 0)
     float *W, *b, *gW, *gb, *mW, *vW, *mb, *vb, *dWT;
     __nv_bfloat16 *Wb, *Wf;
 };
@@ -168,7 +175,7 @@ size_t carve(lbm_net* N, char* base) {
     N->mbh = c.take<float>(4);
     N->vbh = c.take<float>(4);
     using bf = __nv_bfloat16;
-    N->X0 = c.take<bf>(B * V0 * 4);
+    N->X0 = c.take<bf>(B * V0 * kX0);
     N->A0 = c.take<bf>(B * V0 * c1);
     N->S1 = c.take<bf>(B * V0 * c1);
     N->P1 = c.take<bf>(B * V1 * c1);
@@ -220,12 +227,12 @@ int conv_fwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, __nv_bfloat16* A)
     const int n = N->n >> k.level;
     const int64_t M = (int64_t)B * N->V[k.level];
     cudaStream_t st = N->stream;
-    if (N->implicit && conv_implicit_supported(n, k.cin, k.cout)) {  // no im2col matrix
-        NET_CUDA(N, conv_implicit(X, B, n, k.cin, k.Wb, k.Kp, k.cout, k.b, A, CONV_BIAS_RELU_BF16,
+    if (N->implicit && conv_implicit_supported(n, k.cs, k.cout)) {  // no im2col matrix
+        NET_CUDA(N, conv_implicit(X, B, n, k.cs, k.Wb, k.Kp, k.cout, k.b, A, CONV_BIAS_RELU_BF16,
                                   N->err, st));
         return LBM_OK;
     }
-    NET_CUDA(N, im2col(X, B, n, k.cin, k.Kp, N->xcol, st));
+    NET_CUDA(N, im2col(X, B, n, k.cs, k.Kp, N->xcol, st));
     NET_CUDA(N, gemm_bf16(N->xcol, k.Kp, k.Wb, k.Kp, N->y, k.cout, (int)M, k.cout, k.Kp, GEMM_F32, 1,
                           N->err, st));
     NET_CUDA(N, bias_relu(N->y, k.b, M, k.cout, A, k.cout, 0, st));
@@ -241,16 +248,16 @@ int conv_bwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, const __nv_bfloat
     const int64_t M = (int64_t)B * N->V[k.level];
     cudaStream_t st = N->stream;
     NET_CUDA(N, relu_bwd(dA, A, k.cout, 0, M, k.cout, N->dZ, k.gb, N->part, st));
-    NET_CUDA(N, transpose(N->dZ, M, k.cout, k.cout, N->dZT, M, st));
-    if (N->implicit && conv_wgrad_implicit_supported(B, n, k.cin, k.cout)) {
-        // no im2col matrix at all: A tiles straight from x-shifted transposes of X
-        NET_CUDA(N, conv_wgrad_implicit(X, B, n, k.cin, N->dZT, k.cout, k.Kp, N->xcolT, N->ws, N->ws_floats,
+    if (N->implicit && conv_wgrad_implicit_supported(B, n, k.cs, k.cout)) {
+        // no im2col matrix and no transpose: both operands read in place
+        NET_CUDA(N, conv_wgrad_implicit(X, B, n, k.cs, N->dZ, k.cout, k.Kp, N->ws, N->ws_floats,
                                         wgrad_splits(N, k, M), k.dWT, N->err, st));
     } else {
-        if (im2colT_supported(n, k.cin, M)) {  // written transposed: no im2col matrix in between
-            NET_CUDA(N, im2colT(X, B, n, k.cin, k.Kp, N->xcolT, st));
+        NET_CUDA(N, transpose(N->dZ, M, k.cout, k.cout, N->dZT, M, st));
+        if (im2colT_supported(n, k.cs, M)) {  // written transposed: no im2col matrix in between
+            NET_CUDA(N, im2colT(X, B, n, k.cs, k.Kp, N->xcolT, st));
         } else {
-            NET_CUDA(N, im2col(X, B, n, k.cin, k.Kp, N->xcol, st));
+            NET_CUDA(N, im2col(X, B, n, k.cs, k.Kp, N->xcol, st));
             NET_CUDA(N, transpose(N->xcol, M, k.Kp, k.Kp, N->xcolT, M, st));
         }
         NET_CUDA(N, gemm_bf16_add_splitk(N->xcolT, M, N->dZT, M, k.dWT, k.cout, k.Kp, k.cout, (int)M,
@@ -279,7 +286,7 @@ int forward(lbm_net* N, int B) {
     cudaStream_t st = N->stream;
     const int n = N->n, c1 = N->cfg.c1, c2 = N->cfg.c2, c3 = N->cfg.c3;
     const int64_t M1 = (int64_t)B * N->V[1];
-    NET_CUDA(N, features(B, n, N->scal, N->X0, st));
+    NET_CUDA(N, features(B, n, N->scal, N->X0, kX0, st));
     NET_RC(conv_fwd(N, 0, N->X0, B, N->A0));
     NET_RC(conv_fwd(N, 1, N->A0, B, N->S1));
     NET_CUDA(N, avgpool(N->S1, B, n, c1, N->P1, st));
@@ -335,7 +342,7 @@ int backward(lbm_net* N, int B, const float* target) {
     NET_RC(conv_bwd(N, 0, N->X0, B, N->A0, N->dA0, nullptr));
     for (int l = 0; l < kLayers; ++l) {
         Conv& k = N->conv[l];
-        NET_CUDA(N, unpack_grad(k.dWT, k.cout, k.K27, k.gW, st));
+        NET_CUDA(N, unpack_grad(k.dWT, k.cout, k.cin, k.cs, k.gW, st));
     }
     return LBM_OK;
 }
@@ -349,7 +356,7 @@ int update(lbm_net* N) {
         const int64_t w = (int64_t)k.cout * k.K27;
         NET_CUDA(N, adam(k.W, k.gW, k.mW, k.vW, w, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
         NET_CUDA(N, adam(k.b, k.gb, k.mb, k.vb, k.cout, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
-        NET_CUDA(N, pack_weights(k.W, k.cin, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, st));
+        NET_CUDA(N, pack_weights(k.W, k.cin, k.cs, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, st));
     }
     NET_CUDA(N, adam(N->Wh, N->gWh, N->mWh, N->vWh, 4 * c.c1, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
     NET_CUDA(N, adam(N->bh, N->gbh, N->mbh, N->vbh, 4, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
@@ -454,7 +461,8 @@ extern "C" int lbm_net_create(const lbm_net_config* cfg, lbm_net** out) {
         k.cout = cout[l];
         k.level = level[l];
         k.K27 = 27 * cin[l];
-        k.Kp = pad64(k.K27);
+        k.cs = l == 0 ? kX0 : cin[l];
+        k.Kp = pad64(27 * k.cs);
         k.Kpf = pad64(27 * cout[l]);
     }
     if (cudaGetDevice(&N->device) != cudaSuccess ||
@@ -487,7 +495,7 @@ extern "C" int lbm_net_create(const lbm_net_config* cfg, lbm_net** out) {
         for (auto& w : host) w = (float)(sd * rng.normal());
         if (cudaMemcpy(k.W, host.data(), host.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
             rc = nfail(N, LBM_ECUDA, "weight upload failed%s");
-        else if (pack_weights(k.W, k.cin, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, N->stream) != cudaSuccess)
+        else if (pack_weights(k.W, k.cin, k.cs, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, N->stream) != cudaSuccess)
             rc = nfail(N, LBM_ECUDA, "weight packing failed%s");
     }
     if (rc == LBM_OK) {
@@ -542,7 +550,7 @@ extern "C" int lbm_net_set_params(lbm_net* N, const float* host, int64_t count) 
     NET_CUDA(N, e);
     for (int l = 0; l < kLayers; ++l) {
         Conv& k = N->conv[l];
-        NET_CUDA(N, pack_weights(k.W, k.cin, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, N->stream));
+        NET_CUDA(N, pack_weights(k.W, k.cin, k.cs, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, N->stream));
     }
     return wait_net(N);
 }
@@ -594,9 +602,9 @@ extern "C" const char* lbm_net_last_error(const lbm_net* N) {
 extern "C" int lbm_net_tensor(lbm_net* N, int which, int batch, void* host, int64_t count) {
     if (!N || !host || batch < 1 || batch > N->B) return nfail(N, LBM_EINVAL, "NULL argument or batch outside 1..max_batch%s");
     const int c1 = N->cfg.c1, c2 = N->cfg.c2, c3 = N->cfg.c3;
-    struct T { const void* p; int level, channels, bytes; };
+    struct T { const void* p; int level, channels, bytes, ld; };
     const T t[LBM_NET_TENSORS] = {
-        {N->X0, 0, 4, 2}, {N->A0, 0, c1, 2}, {N->S1, 0, c1, 2}, {N->P1, 1, c1, 2},
+        {N->X0, 0, 4, 2, kX0}, {N->A0, 0, c1, 2}, {N->S1, 0, c1, 2}, {N->P1, 1, c1, 2},
         {N->A2, 1, c2, 2}, {N->S2, 1, c2, 2}, {N->P2, 2, c2, 2}, {N->A4, 2, c3, 2},
         {N->A5, 2, c3, 2}, {N->A6, 2, c3, 2}, {N->C2, 1, c3 + c2, 2}, {N->A7, 1, c2, 2},
         {N->A8, 1, c2, 2}, {N->C1, 0, c2 + c1, 2}, {N->A9, 0, c1, 2}, {N->A10, 0, c1, 2},
@@ -612,6 +620,11 @@ extern "C" int lbm_net_tensor(lbm_net* N, int which, int batch, void* host, int6
     if (count != elems) return nfail(N, LBM_EINVAL, "count differs from batch * voxels * channels%s");
     int rc = wait_net(N);  // bounded, before the copy into caller memory
     if (rc != LBM_OK) return rc;
-    NET_CUDA(N, cudaMemcpy(host, d.p, (size_t)elems * d.bytes, cudaMemcpyDeviceToHost));
+    if (d.ld > d.channels)  // a padded row: its first `channels` values
+        NET_CUDA(N, cudaMemcpy2D(host, (size_t)d.channels * d.bytes, d.p, (size_t)d.ld * d.bytes,
+                                 (size_t)d.channels * d.bytes, (size_t)(elems / d.channels),
+                                 cudaMemcpyDeviceToHost));
+    else
+        NET_CUDA(N, cudaMemcpy(host, d.p, (size_t)elems * d.bytes, cudaMemcpyDeviceToHost));
     return LBM_OK;
 }

@@ -56,18 +56,15 @@ bool im2colT_supported(int n, int cin, int64_t M);
 cudaError_t im2colT(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_bfloat16* XcolT,
                     cudaStream_t st);
 // dWT [Kp][cout] += the weight gradient of a 3x3x3 convolution of X [B n^3][cin] with output
-// gradient dZT [cout][B n^3] (transposed), as an implicit GEMM (conv.cu): n >= 64 a power of
-// two, cin a multiple of 32; xt is scratch of 3 cin B n^3 values (the x-shifted transposes),
-// ws of splits Kp cout floats (the split partials, added to dWT in split order).
+// gradient dZ [B n^3][cout], as an implicit GEMM on both in place (conv.cu): n a power of two
+// in 2..256, cin a multiple of 32, cout a multiple of 8 up to 256; ws holds splits Kp cout
+// floats (the split partials, added to dWT in split order).
 bool conv_wgrad_implicit_supported(int B, int n, int cin, int cout);
-cudaError_t conv_wgrad_implicit(const __nv_bfloat16* X, int B, int n, int cin, const __nv_bfloat16* dZT, int cout,
-                                int Kp, __nv_bfloat16* xt, float* ws, size_t ws_floats, int splits, float* dWT,
-                                int* err, cudaStream_t st);
+cudaError_t conv_wgrad_implicit(const __nv_bfloat16* X, int B, int n, int cin, const __nv_bfloat16* dZ, int cout,
+                                int Kp, float* ws, size_t ws_floats, int splits, float* dWT, int* err,
+                                cudaStream_t st);
 // C[r][c] += ws[0][r][c] + ws[1][r][c] + ... in split order (slices of M ldc floats).
 cudaError_t add_splits(const float* ws, int splits, int M, int N, long long ldc, float* C, cudaStream_t st);
-// XT[s][c][v] = X[v + (s - 1) e_x][c] for s = 0, 1, 2 (zero where the shift leaves the
-// grid): the x-shifted transposes the implicit weight gradient reads (3 cin M values).
-cudaError_t transpose_shift_x(const __nv_bfloat16* X, int B, int n, int cin, __nv_bfloat16* XT, cudaStream_t st);
 cudaError_t transpose(const __nv_bfloat16* in, int64_t R, int64_t C, int64_t ld_in,
                       __nv_bfloat16* out, int64_t ld_out, cudaStream_t st);
 cudaError_t bias_relu(const float* Y, const float* bias, int64_t M, int C, __nv_bfloat16* A,
@@ -98,10 +95,12 @@ cudaError_t mse(const float* out, const float* target, int64_t count, float* dOu
                 double* part, cudaStream_t st);
 cudaError_t adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
                  float b2, float eps, int step, cudaStream_t st);
-cudaError_t pack_weights(const float* W, int cin, int cout, int Kp, int Kpf, __nv_bfloat16* Wb,
+// Weights [cout][27 cin] for an input stored with cs >= cin channels: K index tap * cs + ci.
+cudaError_t pack_weights(const float* W, int cin, int cs, int cout, int Kp, int Kpf, __nv_bfloat16* Wb,
                          __nv_bfloat16* Wf, cudaStream_t st);
-cudaError_t unpack_grad(const float* dWT, int cout, int K27, float* gW, cudaStream_t st);
-cudaError_t features(int B, int n, const float* scalars, __nv_bfloat16* X, cudaStream_t st);
+cudaError_t unpack_grad(const float* dWT, int cout, int cin, int cs, float* gW, cudaStream_t st);
+// The 4 input channels in rows of ldx (a multiple of 8; channels 4 .. ldx - 1 written zero).
+cudaError_t features(int B, int n, const float* scalars, __nv_bfloat16* X, int ldx, cudaStream_t st);
 
 }  // namespace nn
 }  // namespace lbm

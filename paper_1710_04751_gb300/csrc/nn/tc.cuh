@@ -160,12 +160,29 @@ __host__ __device__ constexpr uint64_t sdesc_k_sw64(uint32_t saddr) {
            ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 
+// Descriptor of an MN-major operand tile (the M, resp. N, index contiguous in memory):
+// swizzle atoms of 8 K rows, each row 32 values (64 bytes, `layout` 4 = 64-byte swizzle)
+// or 64 values (128 bytes, `layout` 2 = 128-byte swizzle); atoms along M/N `lbo` bytes
+// apart (leading-dimension byte offset), along K `sbo` bytes apart.  This is the layout a
+// TMA box with the M/N index innermost leaves in shared memory.
+__host__ __device__ constexpr uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo,
+                                                uint32_t layout) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) |
+           ((uint64_t)layout << 61);
+}
+
 // Instruction descriptor of kind::f16: D format F32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22),
 // M >> 4 (bits 24-28).
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with both operands MN-major (the transpose bits 15 and 16 set).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
+    return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
 }
 
 }  // namespace nn

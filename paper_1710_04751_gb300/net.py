@@ -62,7 +62,7 @@ def _lib():
     L.lbm_nn_gemm_timeout_probe.argtypes = [vp]
     L.lbm_net_tensor.argtypes = [vp, i32, i32, vp, i64]
     L.lbm_nn_conv3d_bf16.argtypes = [vp, i32, i32, i32, vp, i64, i32, vp, vp, i32, vp]
-    L.lbm_nn_conv3d_wgrad_bf16.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, vp, i64, i32, vp, vp]
+    L.lbm_nn_conv3d_wgrad_bf16.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, i64, i32, vp, vp]
     _bound = True
     return L
 
@@ -100,18 +100,18 @@ def conv3d_bf16(X, n, W, out, mode=CONV_BIAS_RELU_BF16, bias=None):
                                      int(mode), _stream(out)))
 
 
-def conv3d_wgrad_bf16(X, n, dZT, dWT, splits=8):
+def conv3d_wgrad_bf16(X, n, dZ, dWT, splits=8):
     """dWT [Kp, cout] (float32) += the weight gradient of conv3d_bf16 as an implicit GEMM
-    (lbm_nn_conv3d_wgrad_bf16).  X: bfloat16 CUDA [batch, n^3, cin]; dZT: bfloat16
-    [cout, batch n^3] (the output gradient, transposed).  Scratch is allocated here."""
+    (lbm_nn_conv3d_wgrad_bf16), both operands read in place.  X: bfloat16 CUDA
+    [batch, n^3, cin]; dZ: bfloat16 [batch n^3, cout] (the output gradient).  The split
+    workspace is allocated here."""
     import torch
     batch, vox, cin = X.shape
-    cout, Kp = dZT.shape[0], dWT.shape[0]
-    if vox != n ** 3 or dZT.shape[1] != batch * vox or dWT.shape[1] != cout:
-        raise ValueError("shapes: X [batch, n^3, cin], dZT [cout, batch n^3], dWT [Kp, cout]")
-    xt = torch.empty(3 * cin * batch * vox, dtype=torch.bfloat16, device=X.device)
+    cout, Kp = dZ.shape[1], dWT.shape[0]
+    if vox != n ** 3 or dZ.shape[0] != batch * vox or dWT.shape[1] != cout:
+        raise ValueError("shapes: X [batch, n^3, cin], dZ [batch n^3, cout], dWT [Kp, cout]")
     ws = torch.empty(splits * Kp * cout, dtype=torch.float32, device=X.device)
-    _check(_lib().lbm_nn_conv3d_wgrad_bf16(X.data_ptr(), batch, n, cin, dZT.data_ptr(), cout, Kp, xt.data_ptr(),
+    _check(_lib().lbm_nn_conv3d_wgrad_bf16(X.data_ptr(), batch, n, cin, dZ.data_ptr(), cout, Kp,
                                            ws.data_ptr(), ws.numel(), splits, dWT.data_ptr(), _stream(dWT)))
 
 

@@ -355,12 +355,15 @@ def test_implicit_convolution_against_fp64(B, n, cin, cout):
 # dW^T[tap cin + ci][co] = sum over voxels v of X[v + shift(tap)][ci] dZ[v][co] (zero outside
 # the grid): every element within (K_split + splits) 2^-24 sum |x dz| -- the first-order bound
 # of FP32 summation of the split's K products and of the split partials -- after adding to
-# an initial 1 (it accumulates); the padding rows 27 cin .. Kp - 1 stay at 1.  Grids 64^3 and
-# 128^3 (the A tiles are 64-voxel x-row segments), one and two samples, cin 32 / 96,
-# cout 32 / 96 (a 128-wide tile over 96 columns) / 64, uneven splits.
+# an initial 1 (it accumulates); the padding rows 27 cin .. Kp - 1 stay at 1.  Grids from 2^3
+# (one K block spans eight samples, most of them past the batch) to 128^3 (x-row segments),
+# one to three samples, cin 32 / 64 / 96, cout 8 / 32 / 64 / 96 (a 128-wide tile over 96
+# columns, two B boxes) / 256 (four B boxes), uneven splits.
 # ------------------------------------------------------------------------------------
 
-WGRAD_CASES = [(1, 64, 32, 32, 8), (2, 64, 96, 32, 5), (1, 64, 32, 96, 3), (1, 128, 32, 64, 16)]
+WGRAD_CASES = [(1, 64, 32, 32, 8), (2, 64, 96, 32, 5), (1, 64, 32, 96, 3), (1, 128, 32, 64, 16),
+               (2, 32, 64, 96, 7), (3, 16, 32, 256, 2), (1, 8, 96, 8, 1), (2, 4, 32, 32, 1),
+               (1, 2, 32, 64, 1)]
 
 
 @pytest.mark.parametrize("B,n,cin,cout,splits", WGRAD_CASES,
@@ -383,12 +386,12 @@ def test_implicit_weight_gradient_against_fp64(B, n, cin, cout, splits):
         xs = xp[:, kz:kz + n, ky:ky + n, kx:kx + n, :].reshape(M, cin)
         ref[tap * cin:(tap + 1) * cin] = xs.T @ dz
         mag[tap * cin:(tap + 1) * cin] = np.abs(xs).T @ np.abs(dz)
-    kblocks = M // 64
+    kblocks = -(-M // 64)
     per = -(-kblocks // splits)
     # plus the FP32 rounding of 1 + sum (the accumulation test) and of the subtraction
     bound = (per * 64 + splits) * 2.0 ** -24 * mag + 2.0 ** -23 * np.maximum(1.0, np.abs(ref)) + 1e-30
     dWT = torch.ones((Kp, cout), dtype=torch.float32, device="cuda")
-    net.conv3d_wgrad_bf16(X.cuda(), n, dZ.t().contiguous().cuda(), dWT, splits=splits)
+    net.conv3d_wgrad_bf16(X.cuda(), n, dZ.cuda(), dWT, splits=splits)
     got = dWT.cpu().double().numpy() - 1.0
     r = np.abs(got[:27 * cin] - ref) / bound
     assert r.max() <= 1.0, (np.unravel_index(r.argmax(), r.shape), r.max())
