@@ -99,7 +99,7 @@ extern "C" int lbm_nn_conv3d_wgrad_bf16(const void* X, int batch, int n, int cin
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const cudaError_t e = nn::conv_wgrad_implicit(static_cast<const __nv_bfloat16*>(X), batch, n, cin,
                                                   static_cast<const __nv_bfloat16*>(dZ), cout, Kp, ws,
-                                                  (size_t)ws_floats, splits, dWT, err, st);
+                                                  (size_t)ws_floats, splits, dWT, 1, err, st);
     if (e == cudaErrorInvalidValue)
         return record_error(nullptr, LBM_EINVAL, "invalid weight-gradient shape, workspace or alignment%s");
     if (e != cudaSuccess)

@@ -727,8 +727,8 @@ bool conv_wgrad_implicit_supported(int B, int n, int cin, int cout) {
 }
 
 cudaError_t conv_wgrad_implicit(const __nv_bfloat16* X, int B, int n, int cin, const __nv_bfloat16* dZ, int cout,
-                                int Kp, float* ws, size_t ws_floats, int splits, float* dWT, int* err,
-                                cudaStream_t st) {
+                                int Kp, float* ws, size_t ws_floats, int splits, float* dWT, int accumulate,
+                                int* err, cudaStream_t st) {
     if (!conv_wgrad_implicit_supported(B, n, cin, cout) || Kp < 27 * cin || splits < 1 || ((uintptr_t)X & 15) ||
         ((uintptr_t)dZ & 15))
         return cudaErrorInvalidValue;
@@ -760,7 +760,7 @@ cudaError_t conv_wgrad_implicit(const __nv_bfloat16* X, int B, int n, int cin, c
     default: e = launch_wgrad<256>(tx, tb, a, mtiles, used, st); break;
     }
     if (e != cudaSuccess) return e;
-    return add_splits(ws, used, Kp, cout, cout, dWT, st);
+    return add_splits(ws, used, Kp, cout, cout, dWT, accumulate, st);
 }
 
 }  // namespace nn

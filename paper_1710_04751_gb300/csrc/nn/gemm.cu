@@ -304,22 +304,23 @@ cudaError_t gemm_timeout_probe(const __nv_bfloat16* operand, float* C, int* err,
 
 // C[r][c] += ws[0][r][c] + ws[1][r][c] + ... in split order (slices of M * ldc floats).
 __global__ void add_splits_kernel(const float* __restrict__ ws, int splits, int M, int N, long long ldc,
-                                  float* __restrict__ C) {
+                                  float* __restrict__ C, int accumulate) {
     const int64_t total = (int64_t)M * N;
     const int64_t slice = (int64_t)M * ldc;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = (q / N) * ldc + q % N;
-        float s = C[o];
+        float s = accumulate ? C[o] : 0.f;
         for (int z = 0; z < splits; ++z) s += ws[z * slice + o];
         C[o] = s;
     }
 }
 
-cudaError_t add_splits(const float* ws, int splits, int M, int N, long long ldc, float* C, cudaStream_t st) {
+cudaError_t add_splits(const float* ws, int splits, int M, int N, long long ldc, float* C, int accumulate,
+                       cudaStream_t st) {
     const int64_t total = (int64_t)M * N;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
-    add_splits_kernel<<<blocks, 256, 0, st>>>(ws, splits, M, N, ldc, C);
+    add_splits_kernel<<<blocks, 256, 0, st>>>(ws, splits, M, N, ldc, C, accumulate);
     return cudaGetLastError();
 }
 
@@ -334,7 +335,7 @@ cudaError_t gemm_bf16_add_splitk(const __nv_bfloat16* A, long long lda, const __
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)M * N;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
-    add_splits_kernel<<<blocks, 256, 0, st>>>(ws, used, M, N, ldc, C);
+    add_splits_kernel<<<blocks, 256, 0, st>>>(ws, used, M, N, ldc, C, 1);
     return cudaGetLastError();
 }
 

@@ -241,7 +241,7 @@ cudaError_t bias_relu(const float* Y, const float* bias, int64_t M, int C, __nv_
 // then the threads of a block, then the blocks in a fixed tree (sum_partials_kernel) -- so
 // that training gives the same result on every run.
 
-// out[i] += sum over b of part[b ld + first + i], one block of 256 threads per i: thread t
+// out[i] = sum over b of part[b ld + first + i], one block of 256 threads per i: thread t
 // adds the partials t, t + 256, ... in order, then the 256 sums are added pairwise in a
 // fixed tree (the same order on every run, independent of timing).
 __global__ void __launch_bounds__(256) sum_partials_kernel(const float* __restrict__ part, int nblocks, int ld,
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) sum_partials_kernel(const float* __restri
         if (t < w) red[t] += red[t + w];
         __syncthreads();
     }
-    if (t == 0) out[i] += red[0];
+    if (t == 0) out[i] = red[0];
 }
 
 static void sum_partials(const float* part, int nblocks, int ld, int first, int count, float* out,
@@ -810,7 +810,7 @@ __global__ void mse_kernel(const float* __restrict__ out, const float* __restric
     }
 }
 
-// *loss += the block partials, in the fixed order of sum_partials_kernel (FP64).
+// *loss = the sum of the block partials, in the fixed order of sum_partials_kernel (FP64).
 __global__ void __launch_bounds__(256) sum_loss_kernel(const double* __restrict__ part, int nblocks,
                                                        double* __restrict__ loss) {
     __shared__ double red[256];
@@ -823,7 +823,7 @@ __global__ void __launch_bounds__(256) sum_loss_kernel(const double* __restrict_
         if (t < w) red[t] += red[t + w];
         __syncthreads();
     }
-    if (t == 0) *loss += red[0];
+    if (t == 0) *loss = red[0];
 }
 
 cudaError_t mse(const float* out, const float* target, int64_t count, float* dOut, double* loss,
@@ -836,10 +836,15 @@ cudaError_t mse(const float* out, const float* target, int64_t count, float* dOu
 }
 
 // ---- Adam (Kingma & Ba 2015) on FP32 master values ------------------------------------------
-__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+// One launch for every parameter tensor: blockIdx.y selects the tensor.
+__global__ void adam_kernel(const __grid_constant__ AdamTable t, float lr, float b1, float b2, float eps,
                             float c1, float c2) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+    const AdamSeg& sg = t.seg[blockIdx.y];
+    float* __restrict__ p = sg.p;
+    const float* __restrict__ g = sg.g;
+    float* __restrict__ m = sg.m;
+    float* __restrict__ v = sg.v;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sg.n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -850,10 +855,18 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
     }
 }
 
-cudaError_t adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
-                 float eps, int step, cudaStream_t st) {
+// Blocks per tensor: every tensor's elements in at most 4 grid-stride passes.
+static unsigned blocks_per_seg(int64_t max_n) {
+    const int64_t b = (max_n + 4 * 256 - 1) / (4 * 256);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 4096));
+}
+
+cudaError_t adam(const AdamTable& t, float lr, float b1, float b2, float eps, int step, cudaStream_t st) {
+    if (t.count < 1 || t.count > kMaxSegs) return cudaErrorInvalidValue;
+    int64_t max_n = 0;
+    for (int i = 0; i < t.count; ++i) max_n = std::max(max_n, t.seg[i].n);
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
-    adam_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    adam_kernel<<<dim3(blocks_per_seg(max_n), t.count), 256, 0, st>>>(t, lr, b1, b2, eps, c1, c2);
     return cudaGetLastError();
 }
 
@@ -862,52 +875,62 @@ cudaError_t adam(float* p, const float* g, float* m, float* v, int64_t n, float 
 // with cs >= cin channels (zero for ci >= cin and in the K padding), the forward operand, and
 // Wf [cin][Kpf] BF16 with Wf[ci][t * cout + co] = W[co][(26 - t) * cin + ci]: the weights of
 // the convolution that maps the output gradient to the input gradient (every tap
-// mirrored, input and output channels exchanged; zero padding to Kpf).
-__global__ void pack_weights_kernel(const float* __restrict__ W, int cin, int cs, int cout, int Kp,
-                                    int Kpf, __nv_bfloat16* __restrict__ Wb,
-                                    __nv_bfloat16* __restrict__ Wf) {
+// mirrored, input and output channels exchanged; zero padding to Kpf).  One launch for
+// every layer: blockIdx.y selects the layer.
+__global__ void pack_weights_kernel(const __grid_constant__ PackTable t) {
+    const PackSeg& sg = t.seg[blockIdx.y];
+    const float* __restrict__ W = sg.W;
+    const int cin = sg.cin, cs = sg.cs, cout = sg.cout, Kp = sg.Kp, Kpf = sg.Kpf;
     const int K27 = 27 * cin;
-    const int64_t n1 = (int64_t)cout * Kp, n2 = (int64_t)cin * Kpf;
+    const int64_t n1 = (int64_t)cout * Kp, n2 = sg.Wf ? (int64_t)cin * Kpf : 0;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n1 + n2;
          q += (int64_t)gridDim.x * blockDim.x) {
         if (q < n1) {
             const int co = (int)(q / Kp), k = (int)(q % Kp);
             const int tap = k / cs, ci = k - tap * cs;
-            Wb[q] = __float2bfloat16_rn(tap < 27 && ci < cin ? W[(int64_t)co * K27 + tap * cin + ci] : 0.f);
-        } else if (Wf) {
+            sg.Wb[q] = __float2bfloat16_rn(tap < 27 && ci < cin ? W[(int64_t)co * K27 + tap * cin + ci] : 0.f);
+        } else {
             const int64_t r = q - n1;
             const int ci = (int)(r / Kpf), k = (int)(r % Kpf);
             float w = 0.f;
             if (k < 27 * cout) {
-                const int t = k / cout, co = k % cout;
-                w = W[(int64_t)co * K27 + (26 - t) * cin + ci];
+                const int tt = k / cout, co = k % cout;
+                w = W[(int64_t)co * K27 + (26 - tt) * cin + ci];
             }
-            Wf[r] = __float2bfloat16_rn(w);
+            sg.Wf[r] = __float2bfloat16_rn(w);
         }
     }
 }
-cudaError_t pack_weights(const float* W, int cin, int cs, int cout, int Kp, int Kpf, __nv_bfloat16* Wb,
-                         __nv_bfloat16* Wf, cudaStream_t st) {
-    if (cs < cin || Kp < 27 * cs) return cudaErrorInvalidValue;
-    const int64_t total = (int64_t)cout * Kp + (int64_t)cin * Kpf;
-    pack_weights_kernel<<<blocks_for(total, 256), 256, 0, st>>>(W, cin, cs, cout, Kp, Kpf, Wb, Wf);
+cudaError_t pack_weights(const PackTable& t, cudaStream_t st) {
+    if (t.count < 1 || t.count > kMaxSegs) return cudaErrorInvalidValue;
+    int64_t max_n = 0;
+    for (int i = 0; i < t.count; ++i) {
+        const PackSeg& sg = t.seg[i];
+        if (sg.cs < sg.cin || sg.Kp < 27 * sg.cs || (sg.Wf && sg.Kpf < 27 * sg.cout)) return cudaErrorInvalidValue;
+        max_n = std::max(max_n, (int64_t)sg.cout * sg.Kp + (sg.Wf ? (int64_t)sg.cin * sg.Kpf : 0));
+    }
+    pack_weights_kernel<<<dim3(blocks_per_seg(max_n), t.count), 256, 0, st>>>(t);
     return cudaGetLastError();
 }
 
-// dWT [Kp][cout] (K index tap * cs + ci) -> gW [cout][27 cin]
-__global__ void unpack_grad_kernel(const float* __restrict__ dWT, int cout, int cin, int cs,
-                                   float* __restrict__ gW) {
+// dWT [Kp][cout] (K index tap * cs + ci) -> gW [cout][27 cin], every layer in one launch.
+__global__ void unpack_grad_kernel(const __grid_constant__ UnpackTable t) {
+    const UnpackSeg& sg = t.seg[blockIdx.y];
+    const int cout = sg.cout, cin = sg.cin, cs = sg.cs;
     const int K27 = 27 * cin;
     const int64_t total = (int64_t)cout * K27;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int co = (int)(q / K27), k = (int)(q % K27);
         const int tap = k / cin, ci = k - tap * cin;
-        gW[q] = dWT[(int64_t)(tap * cs + ci) * cout + co];
+        sg.gW[q] = sg.dWT[(int64_t)(tap * cs + ci) * cout + co];
     }
 }
-cudaError_t unpack_grad(const float* dWT, int cout, int cin, int cs, float* gW, cudaStream_t st) {
-    unpack_grad_kernel<<<blocks_for((int64_t)cout * 27 * cin, 256), 256, 0, st>>>(dWT, cout, cin, cs, gW);
+cudaError_t unpack_grad(const UnpackTable& t, cudaStream_t st) {
+    if (t.count < 1 || t.count > kMaxSegs) return cudaErrorInvalidValue;
+    int64_t max_n = 0;
+    for (int i = 0; i < t.count; ++i) max_n = std::max(max_n, (int64_t)t.seg[i].cout * 27 * t.seg[i].cin);
+    unpack_grad_kernel<<<dim3(blocks_per_seg(max_n), t.count), 256, 0, st>>>(t);
     return cudaGetLastError();
 }
 

@@ -37,6 +37,7 @@ constexpr int kLayers = 11;
 // The 4 input channels are stored in rows of 32 (the rest zero), so that the first
 // convolution reads its input like every other layer: implicit GEMMs with 32-channel boxes.
 constexpr int kX0 = 32;
+static_assert(2 * kLayers + 2 <= kMaxSegs, "one Adam table holds every parameter tensor");
 
 struct Conv {
     int cin, cout, level, K27, Kp, Kpf;  // Kpf: padded 27 cout (input-gradient GEMM)
@@ -136,6 +137,17 @@ int wgrad_splits(const lbm_net* N, const Conv& k, int64_t M) {
     const int tiles = (k.Kp + 127) / 128;
     const int kb = (int)((M + 63) / 64);
     return std::max(1, std::min(2 * N->sm_count / tiles, kb));
+}
+
+// Every layer's packing of its FP32 weights into the BF16 operands (one launch).
+PackTable pack_table(const lbm_net* N) {
+    PackTable t{};
+    for (int l = 0; l < kLayers; ++l) {
+        const Conv& k = N->conv[l];
+        t.seg[l] = PackSeg{k.W, k.cin, k.cs, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf};
+    }
+    t.count = kLayers;
+    return t;
 }
 
 // Lays out (base == nullptr: only sizes) every buffer of the network.
@@ -251,8 +263,9 @@ int conv_bwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, const __nv_bfloat
     if (N->implicit && conv_wgrad_implicit_supported(B, n, k.cs, k.cout)) {
         // no im2col matrix and no transpose: both operands read in place
         NET_CUDA(N, conv_wgrad_implicit(X, B, n, k.cs, N->dZ, k.cout, k.Kp, N->ws, N->ws_floats,
-                                        wgrad_splits(N, k, M), k.dWT, N->err, st));
+                                        wgrad_splits(N, k, M), k.dWT, 0, N->err, st));
     } else {
+        NET_CUDA(N, cudaMemsetAsync(k.dWT, 0, (size_t)k.Kp * k.cout * 4, st));  // the GEMM adds
         NET_CUDA(N, transpose(N->dZ, M, k.cout, k.cout, N->dZT, M, st));
         if (im2colT_supported(n, k.cs, M)) {  // written transposed: no im2col matrix in between
             NET_CUDA(N, im2colT(X, B, n, k.cs, k.Kp, N->xcolT, st));
@@ -313,14 +326,7 @@ int backward(lbm_net* N, int B, const float* target) {
     cudaStream_t st = N->stream;
     const int n = N->n, c1 = N->cfg.c1, c2 = N->cfg.c2, c3 = N->cfg.c3;
     const int64_t M0 = (int64_t)B * N->V[0], M1 = (int64_t)B * N->V[1];
-    for (int l = 0; l < kLayers; ++l) {
-        Conv& k = N->conv[l];
-        NET_CUDA(N, cudaMemsetAsync(k.dWT, 0, (size_t)k.Kp * k.cout * 4, st));
-        NET_CUDA(N, cudaMemsetAsync(k.gb, 0, (size_t)k.cout * 4, st));
-    }
-    NET_CUDA(N, cudaMemsetAsync(N->gWh, 0, (size_t)4 * c1 * 4, st));
-    NET_CUDA(N, cudaMemsetAsync(N->gbh, 0, 16, st));
-    NET_CUDA(N, cudaMemsetAsync(N->loss, 0, 8, st));
+    // every gradient below is stored (not added) by its one producer: no zeroing pass
     NET_CUDA(N, mse(N->out, target, M0 * 4, N->dOut, N->loss, N->partd, st));
     NET_CUDA(N, head_bwd(N->dOut, N->A10, M0, c1, N->Wh, N->dA10, N->gWh, N->gbh, N->part, st));
     NET_RC(conv_bwd(N, 10, N->A9, B, N->A10, N->dA10, N->dA9));
@@ -340,10 +346,13 @@ int backward(lbm_net* N, int B, const float* target) {
     NET_CUDA(N, avgpool_bwd(N->dP1, B, n, c1, N->dS1, 1, st));
     NET_RC(conv_bwd(N, 1, N->A0, B, N->S1, N->dS1, N->dA0));
     NET_RC(conv_bwd(N, 0, N->X0, B, N->A0, N->dA0, nullptr));
+    UnpackTable t{};
     for (int l = 0; l < kLayers; ++l) {
-        Conv& k = N->conv[l];
-        NET_CUDA(N, unpack_grad(k.dWT, k.cout, k.cin, k.cs, k.gW, st));
+        const Conv& k = N->conv[l];
+        t.seg[l] = UnpackSeg{k.dWT, k.cout, k.cin, k.cs, k.gW};
     }
+    t.count = kLayers;
+    NET_CUDA(N, unpack_grad(t, st));
     return LBM_OK;
 }
 
@@ -351,15 +360,18 @@ int update(lbm_net* N) {
     cudaStream_t st = N->stream;
     const lbm_net_config& c = N->cfg;
     N->step += 1;
+    AdamTable t{};
+    int i = 0;
     for (int l = 0; l < kLayers; ++l) {
         Conv& k = N->conv[l];
-        const int64_t w = (int64_t)k.cout * k.K27;
-        NET_CUDA(N, adam(k.W, k.gW, k.mW, k.vW, w, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
-        NET_CUDA(N, adam(k.b, k.gb, k.mb, k.vb, k.cout, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
-        NET_CUDA(N, pack_weights(k.W, k.cin, k.cs, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, st));
+        t.seg[i++] = AdamSeg{k.W, k.gW, k.mW, k.vW, (int64_t)k.cout * k.K27};
+        t.seg[i++] = AdamSeg{k.b, k.gb, k.mb, k.vb, (int64_t)k.cout};
     }
-    NET_CUDA(N, adam(N->Wh, N->gWh, N->mWh, N->vWh, 4 * c.c1, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
-    NET_CUDA(N, adam(N->bh, N->gbh, N->mbh, N->vbh, 4, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
+    t.seg[i++] = AdamSeg{N->Wh, N->gWh, N->mWh, N->vWh, (int64_t)4 * c.c1};
+    t.seg[i++] = AdamSeg{N->bh, N->gbh, N->mbh, N->vbh, 4};
+    t.count = i;
+    NET_CUDA(N, adam(t, c.lr, c.beta1, c.beta2, c.eps, N->step, st));
+    NET_CUDA(N, pack_weights(pack_table(N), st));
     return LBM_OK;
 }
 
@@ -495,9 +507,9 @@ extern "C" int lbm_net_create(const lbm_net_config* cfg, lbm_net** out) {
         for (auto& w : host) w = (float)(sd * rng.normal());
         if (cudaMemcpy(k.W, host.data(), host.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
             rc = nfail(N, LBM_ECUDA, "weight upload failed%s");
-        else if (pack_weights(k.W, k.cin, k.cs, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, N->stream) != cudaSuccess)
-            rc = nfail(N, LBM_ECUDA, "weight packing failed%s");
     }
+    if (rc == LBM_OK && pack_weights(pack_table(N), N->stream) != cudaSuccess)
+        rc = nfail(N, LBM_ECUDA, "weight packing failed%s");
     if (rc == LBM_OK) {
         host.resize((size_t)4 * c.c1);
         const double sd = 0.25 * sqrt(1.0 / c.c1);
@@ -548,10 +560,7 @@ extern "C" int lbm_net_set_params(lbm_net* N, const float* host, int64_t count) 
         off += n;
     });
     NET_CUDA(N, e);
-    for (int l = 0; l < kLayers; ++l) {
-        Conv& k = N->conv[l];
-        NET_CUDA(N, pack_weights(k.W, k.cin, k.cs, k.cout, k.Kp, k.Kpf, k.Wb, l == 0 ? nullptr : k.Wf, N->stream));
-    }
+    NET_CUDA(N, pack_weights(pack_table(N), N->stream));
     return wait_net(N);
 }
 

@@ -58,19 +58,21 @@ cudaError_t im2colT(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_
 // dWT [Kp][cout] += the weight gradient of a 3x3x3 convolution of X [B n^3][cin] with output
 // gradient dZ [B n^3][cout], as an implicit GEMM on both in place (conv.cu): n a power of two
 // in 2..256, cin a multiple of 32, cout a multiple of 8 up to 256; ws holds splits Kp cout
-// floats (the split partials, added to dWT in split order).
+// floats (the split partials, added to dWT in split order; accumulate == 0: dWT = the sum).
 bool conv_wgrad_implicit_supported(int B, int n, int cin, int cout);
 cudaError_t conv_wgrad_implicit(const __nv_bfloat16* X, int B, int n, int cin, const __nv_bfloat16* dZ, int cout,
-                                int Kp, float* ws, size_t ws_floats, int splits, float* dWT, int* err,
-                                cudaStream_t st);
-// C[r][c] += ws[0][r][c] + ws[1][r][c] + ... in split order (slices of M ldc floats).
-cudaError_t add_splits(const float* ws, int splits, int M, int N, long long ldc, float* C, cudaStream_t st);
+                                int Kp, float* ws, size_t ws_floats, int splits, float* dWT, int accumulate,
+                                int* err, cudaStream_t st);
+// C[r][c] = (accumulate ? C[r][c] : 0) + ws[0][r][c] + ws[1][r][c] + ... in split order
+// (slices of M ldc floats).
+cudaError_t add_splits(const float* ws, int splits, int M, int N, long long ldc, float* C, int accumulate,
+                       cudaStream_t st);
 cudaError_t transpose(const __nv_bfloat16* in, int64_t R, int64_t C, int64_t ld_in,
                       __nv_bfloat16* out, int64_t ld_out, cudaStream_t st);
 cudaError_t bias_relu(const float* Y, const float* bias, int64_t M, int C, __nv_bfloat16* A,
                       int64_t ldA, int c_off, cudaStream_t st);
-// Gradient reductions over rows (relu_bwd's db, head_bwd's dW and db, mse's loss) add
-// per-block partial sums in block order: `part` holds kMaxPartialBlocks * C floats
+// Gradient reductions over rows (relu_bwd's db, head_bwd's dW and db, mse's loss) store
+// the sum of per-block partial sums, taken in a fixed order: `part` holds kMaxPartialBlocks * C floats
 // (relu_bwd), kMaxPartialBlocks * (4 C + 4) floats (head_bwd) or kMaxPartialBlocks
 // doubles (mse).
 constexpr int kMaxPartialBlocks = 1024;
@@ -93,12 +95,41 @@ cudaError_t head_bwd(const float* dOut, const __nv_bfloat16* A, int64_t M, int C
                      float* dA, float* dW, float* db, float* part, cudaStream_t st);
 cudaError_t mse(const float* out, const float* target, int64_t count, float* dOut, double* loss,
                 double* part, cudaStream_t st);
-cudaError_t adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
-                 float b2, float eps, int step, cudaStream_t st);
-// Weights [cout][27 cin] for an input stored with cs >= cin channels: K index tap * cs + ci.
-cudaError_t pack_weights(const float* W, int cin, int cs, int cout, int Kp, int Kpf, __nv_bfloat16* Wb,
-                         __nv_bfloat16* Wf, cudaStream_t st);
-cudaError_t unpack_grad(const float* dWT, int cout, int cin, int cs, float* gW, cudaStream_t st);
+// Tables of tensors for the one-launch Adam step, weight packing and gradient unpacking.
+constexpr int kMaxSegs = 32;
+struct AdamSeg {
+    float* p;
+    const float* g;
+    float *m, *v;
+    int64_t n;
+};
+struct AdamTable {
+    AdamSeg seg[kMaxSegs];
+    int count;
+};
+// Weights [cout][27 cin] for an input stored with cs >= cin channels: K index tap * cs + ci
+// (Wb [cout][Kp]); Wf [cin][Kpf] the mirrored input-gradient weights, or NULL.
+struct PackSeg {
+    const float* W;
+    int cin, cs, cout, Kp, Kpf;
+    __nv_bfloat16 *Wb, *Wf;
+};
+struct PackTable {
+    PackSeg seg[kMaxSegs];
+    int count;
+};
+struct UnpackSeg {
+    const float* dWT;
+    int cout, cin, cs;
+    float* gW;
+};
+struct UnpackTable {
+    UnpackSeg seg[kMaxSegs];
+    int count;
+};
+cudaError_t adam(const AdamTable& t, float lr, float b1, float b2, float eps, int step, cudaStream_t st);
+cudaError_t pack_weights(const PackTable& t, cudaStream_t st);
+cudaError_t unpack_grad(const UnpackTable& t, cudaStream_t st);
 // The 4 input channels in rows of ldx (a multiple of 8; channels 4 .. ldx - 1 written zero).
 cudaError_t features(int B, int n, const float* scalars, __nv_bfloat16* X, int ldx, cudaStream_t st);
 
