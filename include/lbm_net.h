@@ -7,9 +7,9 @@
  * warm-started solver still runs until its own convergence criterion holds.
  *
  * Arithmetic: BF16 operands on the tcgen05 tensor cores with FP32 accumulation (the
- * forward convolutions and the input gradients are implicit GEMMs that read their operand
- * tiles straight from the activations; the weight gradients GEMMs over an im2col matrix),
- * FP32 master weights and Adam moments.
+ * forward convolutions, the input gradients and the weight gradients are implicit GEMMs
+ * that read their operand tiles straight from the activations and output gradients: no
+ * im2col matrix), FP32 master weights and Adam moments.
  *
  * Errors follow include/lbm.h (LBM_OK or a negative LBM_E* code, the message in
  * lbm_last_error(NULL)).  Device pointers are caller-owned.
