@@ -1,13 +1,15 @@
-"""The warm-start network at its production channel widths (32, 64, 128) on a 16^3 grid,
-batch 2, checked element by element: every stored activation, the outputs, every
-activation gradient and every parameter gradient.
+"""The warm-start network at its production channel widths (32, 64, 128) on a 16^3 and a
+24^3 grid, batch 2, checked element by element: every stored activation, the outputs,
+every activation gradient and every parameter gradient.
 
 Each layer is recomputed in FP64 (torch CPU, the definitions the oracle uses: zero-padded
 3x3x3 convolution, bias, ReLU, 2x average pooling, nearest upsampling, concatenation,
 the 1x1 head, the mean squared error) from the GPU's OWN stored inputs of that layer
 (lbm_net_tensor), so that a difference in one layer cannot hide behind, or spread into,
-another.  At 16^3 and batch 2 the GEMMs take the tile widths (BN = 32 ... 128) and the
-split-K weight-gradient path (14 splits) of the 64^3 training.
+another.  At 16^3 every convolution takes the implicit kernels of the 64^3 training (tile
+widths BN = 32 ... 128, the row-reuse form, split-K weight gradients); 24^3 is not a power
+of two, so there every convolution takes the explicit im2col matrix and the GEMM, the
+fallback, with the first layer's input in its padded 32-channel rows.
 
 Per-element bounds, from the arithmetic: a product sum of K BF16 x BF16 terms accumulated
 in FP32 on the tensor cores differs from the FP64 sum by at most 1e-6 K sum |a b| (as in
@@ -20,7 +22,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-N_GRID, BATCH, CH = 16, 2, (32, 64, 128)
+GRIDS, BATCH, CH = (16, 24), 2, (32, 64, 128)
 U8 = 2.0 ** -8   # relative rounding of a BF16 store (8 significant bits, round to nearest)
 U24 = 2.0 ** -24
 
@@ -49,8 +51,9 @@ def _assert_within(got, ref, bound, what):
     return r.max()
 
 
-@pytest.fixture(scope="module")
-def run():
+@pytest.fixture(scope="module", params=GRIDS, ids=[f"n{g}" for g in GRIDS])
+def run(request):
+    N_GRID = request.param
     torch = _torch()
     from oracle import nn_oracle as nno
     from paper_1710_04751_gb300 import net
@@ -72,7 +75,7 @@ def run():
     layers, head = nno.unflatten(params, c1, c2, c3)
     glayers, ghead = nno.unflatten(grads, c1, c2, c3)
     return dict(t=t, layers=layers, head=head, glayers=glayers, ghead=ghead, scal=scal, tgt=tgt,
-                loss=loss)
+                loss=loss, n=N_GRID)
 
 
 # layer l: (input tensor, output tensor, grid level)
@@ -86,8 +89,8 @@ DX = ["", "D_A0", "D_P1", "D_A2", "D_P2", "D_A4", "D_A5", "D_C2", "D_A7", "D_C1"
 def test_input_features_exact(run):
     torch = _torch()
     from oracle import nn_oracle as nno
-    ref = _q(nno.features(N_GRID, run["scal"].astype(np.float64)))
-    got = _grid(run["t"]["X0"], N_GRID)
+    ref = _q(nno.features(run["n"], run["scal"].astype(np.float64)))
+    got = _grid(run["t"]["X0"], run["n"])
     assert torch.equal(got, ref)
 
 
@@ -96,7 +99,7 @@ def test_convolution_outputs(run, l):
     torch = _torch()
     F = torch.nn.functional
     src, dst, level = CONVS[l]
-    m = N_GRID >> level
+    m = run["n"] >> level
     X = _grid(run["t"][src], m)
     A = _grid(run["t"][dst], m)
     w, b = run["layers"][l]
@@ -114,7 +117,7 @@ def test_convolution_outputs(run, l):
 def test_pooling(run, src, dst, level):
     torch = _torch()
     F = torch.nn.functional
-    m = N_GRID >> level
+    m = run["n"] >> level
     S = _grid(run["t"][src], m)
     P = _grid(run["t"][dst], m // 2)
     ref = F.avg_pool3d(S, 2)
@@ -128,12 +131,12 @@ def test_concatenations_exact(run):
     t = run["t"]
     c1, c2, c3 = CH
     up = lambda a: F.interpolate(a, scale_factor=2, mode="nearest")  # noqa: E731
-    C2 = _grid(t["C2"], N_GRID // 2)
-    assert torch.equal(C2[:, :c3], up(_grid(t["A6"], N_GRID // 4)))
-    assert torch.equal(C2[:, c3:], _grid(t["S2"], N_GRID // 2))
-    C1 = _grid(t["C1"], N_GRID)
-    assert torch.equal(C1[:, :c2], up(_grid(t["A8"], N_GRID // 2)))
-    assert torch.equal(C1[:, c2:], _grid(t["S1"], N_GRID))
+    C2 = _grid(t["C2"], run["n"] // 2)
+    assert torch.equal(C2[:, :c3], up(_grid(t["A6"], run["n"] // 4)))
+    assert torch.equal(C2[:, c3:], _grid(t["S2"], run["n"] // 2))
+    C1 = _grid(t["C1"], run["n"])
+    assert torch.equal(C1[:, :c2], up(_grid(t["A8"], run["n"] // 2)))
+    assert torch.equal(C1[:, c2:], _grid(t["S1"], run["n"]))
 
 
 def test_head_loss_and_their_gradients(run):
@@ -165,7 +168,7 @@ def test_convolution_gradients(run, l):
     tg = torch.nn.grad
     t = run["t"]
     src, dst, level = CONVS[l]
-    m = N_GRID >> level
+    m = run["n"] >> level
     X = _grid(t[src], m)
     A = _grid(t[dst], m)
     dA = _grid(t["D_" + dst], m)
@@ -195,7 +198,7 @@ def test_upsampling_and_skip_gradients(run, cat, up_from, skip, split, level):
     torch = _torch()
     F = torch.nn.functional
     t = run["t"]
-    m = N_GRID >> level
+    m = run["n"] >> level
     dC = _grid(t[cat], m)
     # nearest upsampling: the coarse gradient sums its 8 fine children (FP32)
     ref = 8 * F.avg_pool3d(dC[:, :split], 2)
