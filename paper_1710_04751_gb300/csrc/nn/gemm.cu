@@ -311,6 +311,8 @@ __global__ void add_splits_kernel(const float* __restrict__ ws, int splits, int 
          q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = (q / N) * ldc + q % N;
         float s = accumulate ? C[o] : 0.f;
+        // unrolled so that the slices' loads are in flight together; added in split order
+#pragma unroll 8
         for (int z = 0; z < splits; ++z) s += ws[z * slice + o];
         C[o] = s;
     }

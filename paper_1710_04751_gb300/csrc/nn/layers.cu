@@ -652,6 +652,35 @@ __global__ void head_kernel(const __nv_bfloat16* __restrict__ A, int64_t M, int 
     }
 }
 
+// The same with the row read in 16-byte chunks of 8 channels and W, b from shared memory
+// (C a multiple of 8, at most 64); the channels are added in the same order.
+__global__ void head8_kernel(const __nv_bfloat16* __restrict__ A, int M, int C,
+                             const float* __restrict__ W, const float* __restrict__ b,
+                             float* __restrict__ out) {
+    __shared__ float w[4 * 64 + 4];
+    for (int i = threadIdx.x; i < 4 * C; i += blockDim.x) w[i] = W[i];
+    if (threadIdx.x < 4) w[4 * C + threadIdx.x] = b[threadIdx.x];
+    __syncthreads();
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        float o[4] = {w[4 * C], w[4 * C + 1], w[4 * C + 2], w[4 * C + 3]};
+        const uint4* row = reinterpret_cast<const uint4*>(A + (int64_t)m * C);
+        for (int g = 0; g < C / 8; ++g) {
+            const uint4 v = row[g];
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 a = __bfloat1622float2(h[k]);
+                const int c = 8 * g + 2 * k;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) o[j] += w[j * C + c] * a.x;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) o[j] += w[j * C + c + 1] * a.y;
+            }
+        }
+        reinterpret_cast<float4*>(out)[m] = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
 // dA[m][c] = sum_j dOut[m][j] W[j][c] (one thread per row).
 __global__ void head_dA_kernel(const float* __restrict__ dOut, int64_t M, int C,
                                const float* __restrict__ W, float* __restrict__ dA) {
@@ -685,6 +714,10 @@ __global__ void head_dW_kernel(const float* __restrict__ dOut, const __nv_bfloat
 
 cudaError_t head_fwd(const __nv_bfloat16* A, int64_t M, int C, const float* W, const float* b,
                      float* out, cudaStream_t st) {
+    if (C % 8 == 0 && C <= 64 && M < (int64_t(1) << 30) && ((uintptr_t)A & 15) == 0 && ((uintptr_t)out & 15) == 0) {
+        head8_kernel<<<blocks_for(M, 256), 256, 0, st>>>(A, (int)M, C, W, b, out);
+        return cudaGetLastError();
+    }
     head_kernel<<<blocks_for(M, 256), 256, 0, st>>>(A, M, C, W, b, out);
     return cudaGetLastError();
 }
