@@ -68,37 +68,10 @@ __global__ void im2col1_kernel(const __nv_bfloat16* __restrict__ X, int B, int n
     }
 }
 
-// cin a multiple of 4 (the network's 4-channel input layer): 4 channels (8 bytes) per thread.
-__global__ void im2col4_kernel(const __nv_bfloat16* __restrict__ X, int n, int cin, int Kp, int total,
-                               __nv_bfloat16* __restrict__ Xcol) {
-    const int kq = Kp / 4;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-        const int m = q / kq;
-        const int k = (q - m * kq) * 4;
-        uint2 v = make_uint2(0, 0);
-        if (k < 27 * cin) {
-            const int tap = k / cin, ci = k - tap * cin;
-            const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
-            int r = m / n;
-            const int x = m - r * n;
-            const int y = r % n;
-            r /= n;
-            const int z = r % n, b = r / n;
-            const int sz = z + kz - 1, sy = y + ky - 1, sx = x + kx - 1;
-            if ((unsigned)sz < (unsigned)n && (unsigned)sy < (unsigned)n && (unsigned)sx < (unsigned)n)
-                v = *reinterpret_cast<const uint2*>(X + (int64_t)(((b * n + sz) * n + sy) * n + sx) * cin + ci);
-        }
-        *reinterpret_cast<uint2*>(Xcol + (int64_t)m * Kp + k) = v;
-    }
-}
-
 cudaError_t im2col(const __nv_bfloat16* X, int B, int n, int cin, int Kp, __nv_bfloat16* Xcol,
                    cudaStream_t st) {
     const int64_t M = (int64_t)B * n * n * n;
-    if (cin % 4 == 0 && cin % 8 != 0 && Kp % 4 == 0 && ((uintptr_t)X & 7) == 0 && ((uintptr_t)Xcol & 7) == 0 &&
-        M * (Kp / 4) < (int64_t(1) << 31))
-        im2col4_kernel<<<blocks_for(M * (Kp / 4), 256), 256, 0, st>>>(X, n, cin, Kp, (int)(M * (Kp / 4)), Xcol);
-    else if (cin % 8 == 0)
+    if (cin % 8 == 0)
         im2col8_kernel<<<blocks_for(M * (Kp / 8), 256), 256, 0, st>>>(X, B, n, cin, Kp, Xcol);
     else
         im2col1_kernel<<<blocks_for(M * Kp, 256), 256, 0, st>>>(X, B, n, cin, Kp, Xcol);
