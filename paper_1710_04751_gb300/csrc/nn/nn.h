@@ -127,6 +127,9 @@ struct UnpackTable {
     UnpackSeg seg[kMaxSegs];
     int count;
 };
+// The tables travel as kernel parameters (__grid_constant__): within the classic 4 KB.
+static_assert(sizeof(AdamTable) + 6 * sizeof(float) <= 4096, "Adam table exceeds the parameter space");
+static_assert(sizeof(PackTable) <= 4096 && sizeof(UnpackTable) <= 4096, "table exceeds the parameter space");
 cudaError_t adam(const AdamTable& t, float lr, float b1, float b2, float eps, int step, cudaStream_t st);
 cudaError_t pack_weights(const PackTable& t, cudaStream_t st);
 cudaError_t unpack_grad(const UnpackTable& t, cudaStream_t st);
