@@ -61,6 +61,8 @@ struct lbm_net {
     // scratch
     __nv_bfloat16 *xcol, *xcolT, *dZ, *dZT;
     float* y;
+    // capacities (elements) of the explicit fallback's scratch: xcol, xcolT, y, dZT
+    int64_t xcol_cap, xcolT_cap, y_cap, dzt_cap;
     float* ws;          // split-K partial results of the weight-gradient GEMMs
     size_t ws_floats;
     float* part;        // per-block partial sums of the bias / head gradients
@@ -150,18 +152,41 @@ PackTable pack_table(const lbm_net* N) {
     return t;
 }
 
+// Whether layer k takes the explicit fallback (an im2col matrix and the GEMM) for its
+// forward pass, its weight gradient at batch B, its input gradient: the tests conv_fwd and
+// conv_bwd make.  The fallback's scratch is sized from these alone.
+bool fwd_fallback(const lbm_net* N, const Conv& k) {
+    return !(N->implicit && conv_implicit_supported(N->n >> k.level, k.cs, k.cout));
+}
+bool wgrad_fallback(const lbm_net* N, const Conv& k, int64_t B) {
+    return !(N->implicit && conv_wgrad_implicit_supported((int)B, N->n >> k.level, k.cs, k.cout));
+}
+bool dgrad_fallback(const lbm_net* N, const Conv& k) {
+    return !(N->implicit && conv_implicit_supported(N->n >> k.level, k.cout, k.cin));
+}
+
 // Lays out (base == nullptr: only sizes) every buffer of the network.
 size_t carve(lbm_net* N, char* base) {
     Carver c{base};
     const int64_t B = N->B, V0 = N->V[0], V1 = N->V[1], V2 = N->V[2];
     const int c1 = N->cfg.c1, c2 = N->cfg.c2, c3 = N->cfg.c3;
-    int64_t max_xcol = 0, max_y = 0, max_cout = 0;
+    int64_t max_y = 0, max_cout = 0;
+    int64_t xcol = 0, xcolT = 0, y = 0, dzt = 0;  // the fallback's scratch, where a layer takes it
     size_t ws = 0;
     for (int l = 0; l < kLayers; ++l) {
         Conv& k = N->conv[l];
         const int64_t M = B * N->V[k.level];
-        max_xcol = std::max(max_xcol, M * std::max(k.Kp, k.Kpf));
         max_y = std::max(max_y, M * k.cout);
+        if (fwd_fallback(N, k)) {
+            xcol = std::max(xcol, M * k.Kp);
+            y = std::max(y, M * k.cout);
+        }
+        if (wgrad_fallback(N, k, B)) {  // a smaller batch falls back only if this one does
+            xcol = std::max(xcol, M * k.Kp);
+            xcolT = std::max(xcolT, M * k.Kp);
+            dzt = std::max(dzt, M * k.cout);
+        }
+        if (l > 0 && dgrad_fallback(N, k)) xcol = std::max(xcol, M * k.Kpf);
         max_cout = std::max<int64_t>(max_cout, k.cout);
         // the largest batch asks for the most splits (wgrad_splits grows with M)
         ws = std::max(ws, gemm_splitk_floats(k.Kp, k.cout, (int)M, wgrad_splits(N, k, M)));
@@ -221,11 +246,12 @@ size_t carve(lbm_net* N, char* base) {
     N->out = c.take<float>(B * V0 * 4);
     N->dOut = c.take<float>(B * V0 * 4);
     N->scal = c.take<float>(2 * B);
-    N->xcol = c.take<bf>(max_xcol);
-    N->xcolT = c.take<bf>(max_xcol);
+    N->xcol = c.take<bf>(xcol);
+    N->xcolT = c.take<bf>(xcolT);
     N->dZ = c.take<bf>(max_y);
-    N->dZT = c.take<bf>(max_y);
-    N->y = c.take<float>(max_y);
+    N->dZT = c.take<bf>(dzt);
+    N->y = c.take<float>(y);
+    N->xcol_cap = xcol, N->xcolT_cap = xcolT, N->y_cap = y, N->dzt_cap = dzt;
     N->ws = c.take<float>((int64_t)ws);
     N->ws_floats = ws;
     N->part = c.take<float>((int64_t)kMaxPartialBlocks * std::max<int64_t>(max_cout, 4 * c1 + 4));
@@ -244,6 +270,8 @@ int conv_fwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, __nv_bfloat16* A)
                                   N->err, st));
         return LBM_OK;
     }
+    if (M * k.Kp > N->xcol_cap || M * k.cout > N->y_cap)
+        return nfail(N, LBM_EINVAL, "internal: the fallback scratch is smaller than the forward pass needs%s");
     NET_CUDA(N, im2col(X, B, n, k.cs, k.Kp, N->xcol, st));
     NET_CUDA(N, gemm_bf16(N->xcol, k.Kp, k.Wb, k.Kp, N->y, k.cout, (int)M, k.cout, k.Kp, GEMM_F32, 1,
                           N->err, st));
@@ -265,6 +293,8 @@ int conv_bwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, const __nv_bfloat
         NET_CUDA(N, conv_wgrad_implicit(X, B, n, k.cs, N->dZ, k.cout, k.Kp, N->ws, N->ws_floats,
                                         wgrad_splits(N, k, M), k.dWT, 0, N->err, st));
     } else {
+        if (M * k.Kp > N->xcol_cap || M * k.Kp > N->xcolT_cap || M * k.cout > N->dzt_cap)
+            return nfail(N, LBM_EINVAL, "internal: the fallback scratch is smaller than the weight gradient needs%s");
         NET_CUDA(N, cudaMemsetAsync(k.dWT, 0, (size_t)k.Kp * k.cout * 4, st));  // the GEMM adds
         NET_CUDA(N, transpose(N->dZ, M, k.cout, k.cout, N->dZT, M, st));
         if (im2colT_supported(n, k.cs, M)) {  // written transposed: no im2col matrix in between
@@ -281,6 +311,8 @@ int conv_bwd(lbm_net* N, int l, const __nv_bfloat16* X, int B, const __nv_bfloat
             NET_CUDA(N, conv_implicit(N->dZ, B, n, k.cout, k.Wf, k.Kpf, k.cin, nullptr, dX, CONV_F32,
                                       N->err, st));
         } else {  // the xcol scratch is free again
+            if (M * k.Kpf > N->xcol_cap)
+                return nfail(N, LBM_EINVAL, "internal: the fallback scratch is smaller than the input gradient needs%s");
             NET_CUDA(N, im2col(N->dZ, B, n, k.cout, k.Kpf, N->xcol, st));
             NET_CUDA(N, gemm_bf16(N->xcol, k.Kpf, k.Wf, k.Kpf, dX, k.cin, (int)M, k.cin, k.Kpf,
                                   GEMM_F32, 1, N->err, st));
